@@ -1,0 +1,261 @@
+"""Pins of the CPU oracle against facts fixed outside it (no GPU).
+
+Each test ties the oracle to something other than itself: brute force on the
+non-recombining tree, closed-form European sums, the Black-Scholes limit, the
+American-call-without-dividends identity, the paper's weight identities and
+its structural lemmas on the red/green divider.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from tests import closed_forms as cf
+from paper_2303_02317_gb300 import workloads as wl
+
+RNG = np.random.default_rng(7)
+
+
+def _rand_req(model, T, rng, q_zero=False, tri_form=0):
+    S0 = rng.uniform(50, 150)
+    K = rng.uniform(50, 150)
+    sigma = rng.uniform(0.1, 0.6)
+    r = rng.uniform(0.0, 0.08)
+    q = 0.0 if (q_zero or model == 2) else rng.uniform(0.005, 0.06)
+    E = rng.uniform(0.1, 3.0)
+    lam = math.sqrt(3) if (model == 1 and tri_form == 0) else 0.0
+    return dict(model=model, S0=S0, K=K, r=r, q=q, sigma=sigma, expiry=E, T=T, lam=lam,
+                tri_form=tri_form)
+
+
+# ---------------------------------------------------------------- brute force
+@pytest.mark.parametrize("seed", range(6))
+def test_bopm_matches_nonrecombining_tree(oracle_lib, seed):
+    """Fig. 1 lattice == every path of the binomial tree (Sec. 3.1)."""
+    rng = np.random.default_rng(100 + seed)
+    for T in (1, 2, 5, 11):
+        req = _rand_req(0, T, rng)
+        P = oracle_lib.params(req)
+        u, p, m = P["u"], P["p"], P["m"]
+        steps = [(m * p, +1), (m * (1 - p), -1)]
+        ex = lambda lvl, x: req["S0"] * u ** x - req["K"]
+        bf = cf.brute_force_tree(T, steps, ex, 0)
+        got = oracle_lib.price_american(req)
+        assert got == pytest.approx(bf, rel=1e-13, abs=1e-13)
+
+
+@pytest.mark.parametrize("tri_form", [0, 1])
+def test_topm_matches_nonrecombining_tree(oracle_lib, tri_form):
+    """Trinomial lattice (Sec. 4) == every path of the trinomial tree."""
+    rng = np.random.default_rng(200 + tri_form)
+    for T in (1, 3, 7):
+        req = _rand_req(1, T, rng, tri_form=tri_form)
+        P = oracle_lib.params(req)
+        u, m = P["u"], P["m"]
+        steps = [(m * P["pu"], +1), (m * P["po"], 0), (m * P["pd"], -1)]
+        ex = lambda lvl, x: req["S0"] * u ** x - req["K"]
+        bf = cf.brute_force_tree(T, steps, ex, 0)
+        assert oracle_lib.price_american(req) == pytest.approx(bf, rel=1e-13, abs=1e-13)
+
+
+def test_bsm_matches_nonrecombining_walk(oracle_lib):
+    """The explicit scheme (Sec. 5, bsmG) is a trinomial walk with weights
+    (b, c, a) on (k-1, k, k+1); enumerate every path."""
+    rng = np.random.default_rng(300)
+    for T in (1, 4, 7):
+        req = _rand_req(2, T, rng)
+        P = oracle_lib.params(req)
+        b, c, a = P["w"]
+        ds = P["ds"]
+        steps = [(a, +1), (c, 0), (b, -1)]
+        s0 = math.log(req["S0"] / req["K"])
+        ex = lambda lvl, k: 1.0 - math.exp(s0 + k * ds)
+        bf = req["K"] * cf.brute_force_tree(T, steps, ex, 0)
+        assert oracle_lib.price_american(req) == pytest.approx(bf, rel=1e-13, abs=1e-13)
+
+
+# -------------------------------------------------------------- closed forms
+def test_weight_identities(oracle_lib):
+    """Sec. 3 (proof of Lemma 2.2): s0/u + s1 u = e^{-Y dt}; the same
+    martingale identity m (p_d/u + p_o + p_u u) = e^{-Y dt} for both
+    trinomial forms; BSM: c = 1 - a - b - omega dtau with a + b = 2/3."""
+    rng = np.random.default_rng(11)
+    for _ in range(20):
+        req = _rand_req(0, int(rng.integers(10, 5000)), rng)
+        P = oracle_lib.params(req)
+        sd, su = P["w"]
+        assert sd / P["u"] + su * P["u"] == pytest.approx(math.exp(-req["q"] * P["dt"]), rel=1e-14)
+        for form in (0, 1):
+            t = _rand_req(1, int(rng.integers(10, 5000)), rng, tri_form=form)
+            Q = oracle_lib.params(t)
+            wd, wo, wu = Q["w"]
+            lhs = wd / Q["u"] + wo + wu * Q["u"]
+            assert lhs == pytest.approx(math.exp(-t["q"] * Q["dt"]), rel=1e-13)
+            if form == 0:   # Boyle: second moment matched too
+                m2 = (wd / Q["u"] ** 2 + wo + wu * Q["u"] ** 2) / Q["m"]
+                assert m2 == pytest.approx(math.exp((2 * (t["r"] - t["q"]) + t["sigma"] ** 2) * Q["dt"]), rel=1e-12)
+            else:           # paper form: two binomial half steps, p_u = p^2, p_d = (1-p)^2
+                p = math.sqrt(Q["pu"])
+                assert Q["pd"] == pytest.approx((1 - p) ** 2, rel=1e-12)
+        s = _rand_req(2, int(rng.integers(10, 5000)), rng)
+        B = oracle_lib.params(s)
+        b, c, a = B["w"]
+        assert a + b == pytest.approx(2.0 / 3.0, rel=1e-14)
+        assert c == pytest.approx(1.0 / 3.0 - B["omega"] * B["dtau"], rel=1e-12)
+
+
+@pytest.mark.parametrize("T", [16, 301, 2048])
+def test_binomial_call_without_yield_is_european_sum(oracle_lib, T):
+    """With Y=0 Lemma 2.3's bound is infinite: no interior green cell, so the
+    American call equals the European binomial sum."""
+    rng = np.random.default_rng(T)
+    for _ in range(3):
+        req = _rand_req(0, T, rng, q_zero=True)
+        P = oracle_lib.params(req)
+        ref = cf.binomial_european_call(req["S0"], req["K"], T, P["u"], P["p"], P["m"])
+        assert oracle_lib.price_american(req) == pytest.approx(ref, rel=1e-11, abs=1e-12)
+        assert oracle_lib.price_european(req) == pytest.approx(ref, rel=1e-11, abs=1e-12)
+
+
+@pytest.mark.parametrize("tri_form", [0, 1])
+def test_trinomial_call_without_yield_is_european_sum(oracle_lib, tri_form):
+    rng = np.random.default_rng(41 + tri_form)
+    for T in (9, 120):
+        req = _rand_req(1, T, rng, q_zero=True, tri_form=tri_form)
+        P = oracle_lib.params(req)
+        ref = cf.trinomial_european_call(req["S0"], req["K"], T, P["u"], P["pu"], P["po"], P["pd"], P["m"])
+        assert oracle_lib.price_american(req) == pytest.approx(ref, rel=1e-11, abs=1e-12)
+
+
+def test_european_lattices_converge_to_black_scholes(oracle_lib):
+    """European values on the three lattices approach the Black-Scholes
+    closed form as T grows (error O(1/T))."""
+    rng = np.random.default_rng(5)
+    for _ in range(3):
+        req = _rand_req(0, 4096, rng)
+        ref = cf.bs_call(req["S0"], req["K"], req["r"], req["q"], req["sigma"], req["expiry"])
+        assert abs(oracle_lib.price_european(req) - ref) < 2e-3 * req["K"] / 100 + 1e-3
+        for form in (0, 1):
+            t = dict(req, model=1, tri_form=form, lam=math.sqrt(3) if form == 0 else 0.0)
+            assert abs(oracle_lib.price_european(t) - ref) < 2e-3 * req["K"] / 100 + 1e-3
+        p = dict(req, model=2, q=0.0)
+        refp = cf.bs_put(p["S0"], p["K"], p["r"], 0.0, p["sigma"], p["expiry"])
+        assert abs(oracle_lib.price_european(p) - refp) < 2e-3 * req["K"] / 100 + 1e-3
+
+
+def test_bsm_put_without_rate_has_no_early_exercise(oracle_lib):
+    """r = 0 (omega = 0): the explicit scheme keeps the continuation above
+    the payoff, so American == European, and both approach Black-Scholes."""
+    rng = np.random.default_rng(9)
+    for T in (64, 1000):
+        req = _rand_req(2, T, rng)
+        req["r"] = 0.0
+        am = oracle_lib.price_american(req)
+        eu = oracle_lib.price_european(req)
+        assert am == pytest.approx(eu, rel=1e-13, abs=1e-14)
+    req = _rand_req(2, 4096, rng)
+    req["r"] = 0.0
+    ref = cf.bs_put(req["S0"], req["K"], 0.0, 0.0, req["sigma"], req["expiry"])
+    assert abs(oracle_lib.price_american(req) - ref) < 2e-3
+
+
+def test_american_bounds(oracle_lib):
+    """max(European on the same lattice, intrinsic) <= American;
+    call <= S0; put <= K (the north-star 'between' reading)."""
+    for req in wl.random_small(30, seed=3, T_range=(5, 400)):
+        d = req.as_dict()
+        am = oracle_lib.price_american(d)
+        eu = oracle_lib.price_european(d)
+        if req.model == 2:
+            intr = max(req.K - req.S0, 0.0)
+            assert am <= req.K + 1e-12
+        else:
+            intr = max(req.S0 - req.K, 0.0)
+            assert am <= req.S0 + 1e-12
+        assert am >= eu - 1e-12 * max(1.0, eu)
+        assert am >= intr - 1e-12 * max(1.0, intr)
+
+
+# ----------------------------------------------------------- divider lemmas
+def _call_checks(oracle_lib, req):
+    g, bnd = oracle_lib.grid(req)
+    P = oracle_lib.params(req)
+    T, D = req["T"], P["D"]
+    S, K = req["S0"], req["K"]
+    u = P["u"]
+    for i in range(T - 1):
+        # Cor. 2.7 / its trinomial analogue: the divider moves <= 1 cell left,
+        # except that a fully red row is clipped at the row end (D i).
+        assert min(bnd[i + 1] - 1, D * i) <= bnd[i] <= bnd[i + 1], (i, bnd[i], bnd[i + 1])
+    for i in range(T + 1):
+        row = g[i, : D * i + 1]
+        # hidden lemma of Sec. 3.2 (trinomial: row monotone): non-decreasing rows
+        assert np.all(np.diff(row) >= -1e-12 * max(1.0, np.max(np.abs(row))))
+        # red cells left of the divider, green (== exercise) right of it
+        k = np.arange(D * i + 1)
+        ex = S * u ** ((2 * k - i) if D == 1 else (k - i)) - K
+        green = k > bnd[i]
+        assert np.allclose(row[green], np.maximum(ex[green], 0.0 if i == T else ex[green]), rtol=1e-13, atol=1e-13)
+    if D == 1:
+        # Lemma timedecay: G[i][j] >= G[i+2][j+1]
+        for i in range(T - 1):
+            for j in range(i):
+                assert g[i, j] >= g[i + 2, j + 1] - 1e-12
+        # Lemma 2.3: a green cell of row i < T sits at or right of the bound
+        if req["q"] > 0 and req["r"] > 0:
+            dt = P["dt"]
+            shift = math.log((K / S) * (1 - math.exp(-req["r"] * dt)) / (1 - math.exp(-req["q"] * dt)))
+            for i in range(T):
+                if bnd[i] < i:
+                    assert bnd[i] + 1 >= i / 2 + shift / (2 * req["sigma"] * math.sqrt(dt)) - 1e-9
+    else:
+        # trinomial diagonal lemma: G[i+1][j+1] <= G[i][j]
+        for i in range(T - 1):
+            for j in range(2 * i + 1):
+                assert g[i + 1, j + 1] <= g[i, j] + 1e-12
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_call_divider_lemmas(oracle_lib, seed):
+    rng = np.random.default_rng(500 + seed)
+    for model, form in ((0, 0), (1, 0), (1, 1)):
+        req = _rand_req(model, int(rng.integers(20, 160)), rng, tri_form=form)
+        _call_checks(oracle_lib, req)
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_bsm_divider_theorem(oracle_lib, seed):
+    """BSM boundary theorem: 0 <= k_n - k_{n+1} <= 1, green left of the
+    divider holds the payoff, red right of it holds the continuation."""
+    rng = np.random.default_rng(600 + seed)
+    req = _rand_req(2, int(rng.integers(20, 200)), rng)
+    g, bnd = oracle_lib.grid(req)
+    T = req["T"]
+    P = oracle_lib.params(req)
+    s0 = math.log(req["S0"] / req["K"])
+    NONE = oracle_lib.INT32_MIN
+    for n in range(T):
+        if bnd[n] == NONE:
+            continue
+        if bnd[n + 1] != NONE:
+            assert 0 <= bnd[n] - bnd[n + 1] <= 1, (n, bnd[n], bnd[n + 1])
+        else:
+            # the divider left the shrinking triangle on its left edge
+            assert bnd[n] - 1 < -(T - n - 1)
+    for n in range(T + 1):
+        R = T - n
+        k = np.arange(-R, R + 1)
+        row = g[n, k + T]
+        ex = 1 - np.exp(s0 + k * P["ds"])
+        green = k <= (bnd[n] if bnd[n] != NONE else -R - 1)
+        assert np.allclose(row[green], ex[green], rtol=1e-13, atol=1e-13)
+        assert np.all(row >= np.maximum(ex, 0.0) - 1e-13)
+
+
+def test_invalid_inputs_rejected(oracle_lib):
+    base = wl.fixed_call(0, 64).as_dict()
+    for bad in (dict(S0=0.0), dict(K=-1.0), dict(sigma=0.0), dict(expiry=0.0), dict(T=0)):
+        assert oracle_lib.status_of(dict(base, **bad)) == 1
+    assert oracle_lib.status_of(dict(wl.fixed_bsm_put(64).as_dict(), q=0.01)) == 1
+    # r - q so large at tiny sigma that p > 1
+    assert oracle_lib.status_of(dict(base, sigma=0.001, r=0.5, T=4)) == 2
