@@ -55,6 +55,7 @@ class _Params(ctypes.Structure):
         ("o_min", ctypes.c_int32),
         ("nw", ctypes.c_int32),
         ("u", ctypes.c_double),
+        ("logu", ctypes.c_double),
         ("dt", ctypes.c_double),
         ("dtau", ctypes.c_double),
         ("ds", ctypes.c_double),
@@ -136,7 +137,7 @@ def params(req) -> dict:
     if st:
         raise ValueError("oracle rejected request (status %d)" % st)
     return {"model": P.model, "D": P.D, "w": [P.w[i] for i in range(P.nw)],
-            "o_min": P.o_min, "u": P.u, "dt": P.dt, "dtau": P.dtau, "ds": P.ds,
+            "o_min": P.o_min, "u": P.u, "logu": P.logu, "dt": P.dt, "dtau": P.dtau, "ds": P.ds,
             "omega": P.omega, "p": P.p, "pu": P.pu, "po": P.po, "pd": P.pd, "m": P.m}
 
 

@@ -75,6 +75,7 @@ typedef struct {
     int32_t o_min;      /* 0 for the calls, -1 for BSM */
     int32_t nw;         /* 2 or 3 */
     double u;           /* price factor per column (calls) or e^{ds} (BSM) */
+    double logu;        /* exact log of u as defined (V sqrt(dt), ...) */
     double dt, dtau, ds, omega, p, pu, po, pd, m;
 } or_params;
 
@@ -95,15 +96,16 @@ int or_params_compute(const or_req *q, or_params *P)
         P->D = 1; P->nw = 2; P->o_min = 0;
         P->w[0] = m * (1.0 - p);   /* down child G[i+1][j]  */
         P->w[1] = m * p;           /* up child   G[i+1][j+1] */
-        P->u = u; P->dt = dt; P->p = p; P->m = m;
+        P->u = u; P->logu = q->V * sqrt(dt); P->dt = dt; P->p = p; P->m = m;
         return OR_OK;
     }
     if (q->model == OR_TOPM) {
         double dt = q->E / T;
         double m = exp(-q->R * dt);
-        double u, pu, pd, po;
+        double u, logu, pu, pd, po;
         if (q->tri_form == 1) {
-            u = exp(q->V * sqrt(2.0 * dt));
+            logu = q->V * sqrt(2.0 * dt);
+            u = exp(logu);
             double su = exp(q->V * sqrt(dt / 2.0));
             double sd = 1.0 / su;
             double e = exp((q->R - q->Y) * dt / 2.0);
@@ -112,7 +114,8 @@ int or_params_compute(const or_req *q, or_params *P)
             po = 1.0 - pu - pd;
         } else {
             double lam = q->lambda > 0 ? q->lambda : sqrt(3.0);
-            u = exp(lam * q->V * sqrt(dt));
+            logu = lam * q->V * sqrt(dt);
+            u = exp(logu);
             /* Solve the 3x3 moment system by Gaussian elimination on the
                unknowns (pu, po, pd); rows: sum, first moment, second moment.
                Right-hand sides are taken relative to 1 (expm1) so that the
@@ -130,7 +133,7 @@ int or_params_compute(const or_req *q, or_params *P)
         if (!(pu >= 0 && pd >= 0 && po >= 0)) return OR_EUNSTABLE;
         P->D = 2; P->nw = 3; P->o_min = 0;
         P->w[0] = m * pd; P->w[1] = m * po; P->w[2] = m * pu;
-        P->u = u; P->dt = dt; P->pu = pu; P->po = po; P->pd = pd; P->m = m;
+        P->u = u; P->logu = logu; P->dt = dt; P->pu = pu; P->po = po; P->pd = pd; P->m = m;
         return OR_OK;
     }
     if (q->model == OR_BSM) {
@@ -145,14 +148,16 @@ int or_params_compute(const or_req *q, or_params *P)
         if (!(a >= 0 && b >= 0 && c >= 0)) return OR_EUNSTABLE;
         P->D = 2; P->nw = 3; P->o_min = -1;
         P->w[0] = b; P->w[1] = c; P->w[2] = a;   /* on k-1, k, k+1 */
-        P->u = exp(ds); P->dtau = dtau; P->ds = ds; P->omega = omega;
+        P->u = exp(ds); P->logu = ds; P->dtau = dtau; P->ds = ds; P->omega = omega;
         return OR_OK;
     }
     return OR_EINVAL;
 }
 
 /* exercise value table ex[k + T] for k in [-T, T]:
-   calls: S u^k - K ; put: 1 - e^{ln(S/K) + k ds} (units of K) */
+   calls: S u^k - K with u^k evaluated as e^{k log u} from the exact log u of
+   the model (Sec. 3.1: node price S u^{N_u - N_d}); put: 1 - e^{ln(S/K) + k ds}
+   (units of K). */
 static double *exercise_table(const or_req *q, const or_params *P)
 {
     int64_t T = q->T;
@@ -162,7 +167,7 @@ static double *exercise_table(const or_req *q, const or_params *P)
         if (P->model == OR_BSM)
             ex[k + T] = 1.0 - exp(log(q->S / q->K) + (double)k * P->ds);
         else
-            ex[k + T] = q->S * pow(P->u, (double)k) - q->K;
+            ex[k + T] = q->S * exp((double)k * P->logu) - q->K;
     }
     return ex;
 }

@@ -193,7 +193,7 @@ def _call_checks(oracle_lib, req):
         assert np.all(np.diff(row) >= -1e-12 * max(1.0, np.max(np.abs(row))))
         # red cells left of the divider, green (== exercise) right of it
         k = np.arange(D * i + 1)
-        ex = S * u ** ((2 * k - i) if D == 1 else (k - i)) - K
+        ex = S * np.exp(P["logu"] * ((2 * k - i) if D == 1 else (k - i))) - K
         green = k > bnd[i]
         assert np.allclose(row[green], np.maximum(ex[green], 0.0 if i == T else ex[green]), rtol=1e-13, atol=1e-13)
     if D == 1:
