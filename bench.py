@@ -1,0 +1,343 @@
+"""Benchmark: American options per second at T = 2^17 on one GB300.
+
+Workload (one step): price the book of 512 American calls of the precision
+sweep -- 256 binomial (CRR) + 256 trinomial (Boyle, lambda = sqrt(3)), all at
+T = 2^17 steps, S0, K ~ U[50,150], sigma ~ U[0.1,0.6], r ~ U[0,0.08],
+q ~ U[0.005,0.06], expiry ~ U[0.1,3] (seed 2303) -- with the trapezoidal
+divide-and-conquer pricer (FP32 hi/lo-split FFT convolutions, FP64 base cases,
+boundary tests and root).  Synthetic inputs; no dataset.
+
+Reported beside it: the same book through the host-buffer C-ABI call (e2e),
+the plain Theta(T^2) FP64 stencil on a sample of the book (ms/option), the
+per-option error of the split-FP32 prices against the FP64 FFT pricer and the
+CPU oracle, the roofline of the pricing kernel and the CPU oracle timed on the
+host cores.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+Multi-GPU (torchrun): every rank prices its own copy of the book (weak
+scaling, independent options, no collective on the data path).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+T_BENCH = 1 << 17
+N_BINOMIAL = N_TRINOMIAL = 256
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12     # SMs x FP32 lanes x FMA x max clock
+FP64_PEAK_TFLOPS = 1.25                              # GB300 dense FP64 (vendor figure)
+WORKLOAD = "precision_sweep_T131072_256binomial_256trinomial"
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as f:
+            return json.load(f)
+    except Exception:
+        return {}
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle sampling during the timed region."""
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", "clocks_bench.csv")
+
+    def start(self):
+        os.makedirs(os.path.dirname(self.path), exist_ok=True)
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def cpu_oracle_sample(reqs, n_sample, budget_s=25.0):
+    """Time the CPU oracle (as it stands, OpenMP over the host cores) on a
+    bounded sample of the book; returns (options/s, seconds, threads, sample
+    description, prices)."""
+    import oracle
+    oracle.build()
+    threads = oracle.max_threads()
+    sample = reqs[:n_sample // 2] + reqs[N_BINOMIAL:N_BINOMIAL + n_sample - n_sample // 2]
+    t0 = time.perf_counter()
+    prices = []
+    done = []
+    for r in sample:
+        prices.append(oracle.price_american(r.as_dict(), nthreads=threads))
+        done.append(r)
+        if time.perf_counter() - t0 > budget_s:
+            break
+    dt = time.perf_counter() - t0
+    desc = "%d options of the book (%d binomial, %d trinomial) at T=%d, OpenMP over %d threads" % (
+        len(done), sum(1 for r in done if r.model == 0), sum(1 for r in done if r.model == 1),
+        T_BENCH, threads)
+    return len(done) / dt, dt, threads, desc, done, prices
+
+
+def run_reference(args):
+    """The reference arm: the CPU oracle (plain FP64 backward induction) on
+    the host cores, each step a bounded sample of the same book."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    from paper_2303_02317_gb300 import workloads as wl
+    reqs = wl.precision_sweep(T=T_BENCH, n_binomial=N_BINOMIAL, n_trinomial=N_TRINOMIAL)
+    import oracle
+    oracle.build()
+    threads = oracle.max_threads()
+    sample = [reqs[0], reqs[N_BINOMIAL]]
+    for _ in range(args.warmup):
+        for r in sample[:1]:
+            oracle.price_american(r.as_dict(), nthreads=threads)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        for r in sample:
+            oracle.price_american(r.as_dict(), nthreads=threads)
+        times.append(time.perf_counter() - t0)
+    per_step = sum(times) / len(times)
+    value = len(sample) / per_step
+    line = {
+        "impl": "reference", "metric": "options_per_second", "value": value, "unit": "options/s",
+        "n_gpus": 0, "steps": args.steps, "warmup": args.warmup, "ms_per_step": per_step * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "T": T_BENCH, "step_sample": "1 binomial + 1 trinomial option"},
+        "cpu_baseline": {"value": value, "unit": "options/s", "cores": threads, "kind": "oracle",
+                         "sample": "per step: 1 binomial + 1 trinomial option of the book at T=%d" % T_BENCH},
+        "e2e": {"value": value, "unit": "options/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--method", default="fft32", choices=["fft32", "fft64"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--stencil-sample", type=int, default=4)
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    args.warmup = max(args.warmup, 3)
+
+    import torch
+    import torch.distributed as dist
+    import paper_2303_02317_gb300 as aop
+    from paper_2303_02317_gb300 import workloads as wl
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    method = aop.FFT_FP32SPLIT if args.method == "fft32" else aop.FFT_FP64
+
+    reqs = wl.precision_sweep(T=T_BENCH, n_binomial=N_BINOMIAL, n_trinomial=N_TRINOMIAL)
+    n = len(reqs)
+    arr = aop.requests_array(reqs)
+    ctx = aop.Context(local)
+    d_reqs = torch.from_numpy(arr.view(np.uint8).copy()).to(dev)
+    d_prices = torch.empty(n, dtype=torch.float64, device=dev)
+    d_status = torch.empty(n, dtype=torch.int32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    sh = stream.cuda_stream
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)   # > L2 (129 MB)
+
+    def step():
+        ctx.price_batch_device(n, d_reqs.data_ptr(), d_prices.data_ptr(), d_status.data_ptr(),
+                               method=method, stream=sh)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize(dev)
+    st = d_status.cpu().numpy()
+    if (st != 0).any():
+        raise SystemExit("pricing failed: status %s" % np.unique(st))
+
+    sampler = ClockSampler(local)
+    sampler.start()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    kernel_ms = []
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    t_wall = time.perf_counter()
+    for k in range(args.steps):
+        flush.fill_(k & 0xff)
+        ev[k][0].record(stream)
+        step()
+        ev[k][1].record(stream)
+        kernel_ms.append(ctx.stats()["kernel_ms"])
+    torch.cuda.synchronize(dev)
+    t_wall = time.perf_counter() - t_wall
+    clocks = sampler.stop()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    ms_step = float(np.mean(step_ms))
+    if world > 1:
+        t = torch.tensor([ms_step], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_step = float(t.item())
+    prices32 = d_prices.cpu().numpy().copy()
+    stats = ctx.stats()
+    kms = float(np.mean(kernel_ms))
+
+    # ---- end to end through the host-buffer C ABI call
+    e2e_times = []
+    for k in range(max(3, args.steps // 2)):
+        flush.fill_(k & 0xff)
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        hp, hs = ctx.price_batch(arr, method=method)
+        e2e_times.append(time.perf_counter() - t0)
+    e2e_ms = float(np.mean(e2e_times)) * 1e3
+
+    if rank != 0:
+        if world > 1:
+            dist.barrier()
+        return
+
+    # ---- accuracy: split-FP32 prices against the FP64 FFT pricer (untimed)
+    acc = {}
+    if method == aop.FFT_FP32SPLIT:
+        p64, s64 = ctx.price_batch(arr, method=aop.FFT_FP64)
+        ok = (s64 == 0)
+        rel = np.abs(prices32[ok] - p64[ok]) / np.maximum(np.abs(p64[ok]), 1e-300)
+        ab = np.abs(prices32[ok] - p64[ok])
+        floor = np.abs(p64[ok]) >= 1e-3 * arr["K"][ok]
+        acc = {"vs": "fft_fp64", "max_rel": float(rel[floor].max()), "mean_rel": float(rel[floor].mean()),
+               "max_abs": float(ab.max()), "mean_abs": float(ab.mean()),
+               "n_rel_le_1e-6": int((rel[floor] <= 1e-6).sum()), "n_priced_above_floor": int(floor.sum())}
+    else:
+        p64 = prices32
+
+    # ---- plain FP64 stencil on a sample (ms/option)
+    samp = [reqs[i] for i in range(args.stencil_sample // 2)] + \
+           [reqs[N_BINOMIAL + i] for i in range(args.stencil_sample - args.stencil_sample // 2)]
+    sarr = aop.requests_array(samp)
+    ps, ss = ctx.price_batch(sarr, method=aop.STENCIL_FP64)
+    sstats = ctx.stats()
+    stencil_ms = sstats["kernel_ms"]
+    stencil = {"sample": "%d options of the book (%d binomial, %d trinomial)" % (
+        len(samp), sum(1 for r in samp if r.model == 0), sum(1 for r in samp if r.model == 1)),
+        "ms_per_option": stencil_ms / len(samp), "options_per_s": len(samp) / (stencil_ms / 1e3),
+        "cells": sstats["stencil_cells"],
+        "fp64_gcells_per_s": sstats["stencil_cells"] / (stencil_ms / 1e3) / 1e9}
+    idx = [i for i in range(args.stencil_sample // 2)] + \
+          [N_BINOMIAL + i for i in range(args.stencil_sample - args.stencil_sample // 2)]
+    stencil["max_rel_fft64_vs_stencil"] = float(np.max(np.abs(p64[idx] - ps) / np.abs(ps)))
+
+    # ---- roofline of the pricing kernel: FFT flops (FP32 or FP64) over time
+    flops = stats["fft_flops"]
+    peaks = _peaks()
+    kern_s = kms / 1e3
+    if method == aop.FFT_FP32SPLIT:
+        peak = FP32_PEAK_TFLOPS
+        note = "FP32 peak derived: 152 SMs x 128 lanes x 2 flop x 2.07 GHz"
+    else:
+        peak = FP64_PEAK_TFLOPS
+        note = "FP64 peak: vendor dense FP64 figure"
+    achieved = flops / kern_s / 1e12
+    roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+            "frac": achieved / peak, "traffic": None, "kernel": "dnc_kernel",
+            "per_launch_flops": flops, "kernel_ms": kms, "peak_source": note,
+            "hbm_gbs_measured": peaks.get("hbm_gbs")}
+
+    # ---- CPU oracle baseline on a bounded sample
+    cpu = None
+    if not args.no_cpu_baseline:
+        v, secs, threads, desc, done, oprices = cpu_oracle_sample(reqs, 4)
+        cpu = {"value": v, "unit": "options/s", "cores": threads, "kind": "oracle", "sample": desc,
+               "seconds": secs}
+        # FP64 FFT vs oracle on the sample
+        ii = [reqs.index(r) for r in done]
+        cpu["max_rel_fft64_vs_oracle"] = float(np.max(np.abs(p64[ii] - np.array(oprices)) / np.abs(oprices)))
+        if method == aop.FFT_FP32SPLIT:
+            cpu["max_rel_fft32_vs_oracle"] = float(np.max(np.abs(prices32[ii] - np.array(oprices)) / np.abs(oprices)))
+
+    value = world * n / (ms_step / 1e3)
+    line = {
+        "metric": "options_per_second", "value": value, "unit": "options/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
+        "ms_per_option": ms_step / n, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32split+f64" if method == aop.FFT_FP32SPLIT else "f64",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "T": T_BENCH, "options_per_step": n,
+                   "method": args.method, "l2": "512 MB buffer written between timed steps",
+                   "parallelism": "independent options per rank"},
+        "e2e": {"value": world * n / (e2e_ms / 1e3), "unit": "options/s",
+                "h2d_bytes_per_step": int(arr.nbytes), "d2h_bytes_per_step": int(n * (8 + 4))},
+        "gpu_launches": 2 * args.steps,
+        "clocks": clocks,
+        "roofline": roof,
+        "accuracy": acc,
+        "stencil_fp64": stencil,
+        "speedup_vs_stencil_ms_per_option": stencil["ms_per_option"] / (ms_step / n),
+        "cpu_baseline": cpu,
+        "kernel_stats": stats,
+        "wall_s_timed": t_wall,
+    }
+    print(json.dumps(line))
+    if world > 1:
+        dist.barrier()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,190 @@
+/*
+ * american.h -- C ABI of the GB300 (sm_103a) nonlinear-stencil American option
+ * pricer: an implementation of the trapezoidal divide-and-conquer of
+ * "Fast American Option Pricing using Nonlinear Stencils" (arXiv 2303.02317),
+ * plus the plain Theta(T^2) lattice loop it replaces.
+ *
+ * Conventions for every entry point
+ *   - Status codes only; nothing throws across this boundary.
+ *   - The caller owns every buffer passed in.  The library owns only the device
+ *     workspace held by an aop_ctx; nothing the library allocates crosses the ABI.
+ *   - Host pointers are plain C arrays.  Entry points whose names end in
+ *     "_device" take device pointers (memory allocated on the context's device)
+ *     and run asynchronously on the given CUDA stream (cudaStream_t passed as
+ *     void*; NULL = the context's own stream).
+ *   - A context is used by one host thread at a time; contexts are independent.
+ *   - Every computation runs in the library's CUDA kernels.  If no CUDA device
+ *     is usable the entry points return AOP_ECUDA; there is no CPU fallback.
+ */
+#ifndef AMERICAN_H
+#define AMERICAN_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Lattice models.
+ *   AOP_BINOMIAL_CALL  -- Sec. 3 (Fig. 1, Def. 2.1): (T+1)x(T+1) grid, row i
+ *       holds columns j in [0, i] at price S0 u^{2j-i}, u = e^{sigma sqrt(dt)},
+ *       dt = expiry/T; weights m(1-p) on G[i+1][j] and m p on G[i+1][j+1].
+ *   AOP_TRINOMIAL_CALL -- Sec. 4 and its appendix: row i holds j in [0, 2i] at
+ *       price S0 u^{j-i}; weights m p_d, m p_o, m p_u on G[i+1][j..j+2].
+ *   AOP_BSM_PUT        -- Sec. 5: explicit finite differences for the
+ *       nondimensional Black-Scholes-Merton put (scheme bsmG) on the shrinking
+ *       triangle k in [-(T-n), T-n], dtau = sigma^2 expiry/(2T),
+ *       ds = sqrt(3 dtau), s_k = ln(S0/K) + k ds; q must be 0. */
+typedef enum {
+    AOP_BINOMIAL_CALL = 0,
+    AOP_TRINOMIAL_CALL = 1,
+    AOP_BSM_PUT = 2
+} aop_model;
+
+typedef enum {
+    AOP_OK = 0,
+    AOP_EINVAL = 1,      /* bad argument: S0, K, sigma or expiry <= 0, T < 1,
+                            T > AOP_MAX_T, unknown model/method, q != 0 for the
+                            BSM put, NULL where a pointer is required */
+    AOP_EUNSTABLE = 2,   /* a lattice probability or FD weight is negative
+                            (binomial p outside [0,1], trinomial p_x < 0,
+                            BSM a, b or c < 0) */
+    AOP_ENOMEM = 3,      /* workspace cap exceeded or device allocation failed */
+    AOP_ECUDA = 4,       /* a CUDA runtime call failed / no usable device */
+    AOP_ETIMEOUT = 5,    /* a bounded device-side wait gave up */
+    AOP_EBUSY = 6,       /* admission refused: no workspace slot free */
+    AOP_EINTERNAL = 7    /* a device-side consistency check failed */
+} aop_status;
+
+typedef enum {
+    AOP_FFT_FP64 = 0,       /* trapezoidal D&C, FFT convolutions in FP64 */
+    AOP_FFT_FP32SPLIT = 1,  /* trapezoidal D&C, FFT convolutions in FP32 on
+                               hi/lo split inputs with hi/lo twiddles; base
+                               cases, boundary tests and root in FP64 */
+    AOP_STENCIL_FP64 = 2    /* plain Theta(T^2) backward induction (Fig. 1 loop
+                               and its trinomial / finite-difference analogues),
+                               temporally blocked, FP64 */
+} aop_method;
+
+typedef enum {
+    AOP_TRI_BOYLE = 0,  /* u = e^{lambda sigma sqrt(dt)}, probabilities matching
+                           the first two moments (Boyle 1986); lambda <= 0
+                           selects sqrt(3) */
+    AOP_TRI_PAPER = 1   /* Sec. 4: u = e^{sigma sqrt(2 dt)},
+                           p_u = ((e^{(r-q)dt/2} - u^{-1/2})/(u^{1/2}-u^{-1/2}))^2,
+                           p_d = ((u^{1/2} - e^{(r-q)dt/2})/(u^{1/2}-u^{-1/2}))^2 */
+} aop_tri_form;
+
+#define AOP_MAX_T (1 << 20)        /* largest supported step count */
+#define AOP_BOUNDARY_NONE_PUT (-2147483647 - 1)   /* INT32_MIN */
+
+/* One pricing request (72 bytes, 8-byte aligned; identical layout on host and
+ * device).  Parameters use the paper's notation (Table "Notations"):
+ * S = S0, K, R = r, Y = q, V = sigma, E = expiry (in years here). */
+typedef struct aop_request {
+    int32_t model;      /* aop_model */
+    int32_t tri_form;   /* aop_tri_form, trinomial only */
+    double S0, K, r, q, sigma, expiry;
+    int64_t T;          /* number of time steps, 1 <= T <= AOP_MAX_T */
+    double lambda;      /* trinomial stretch for AOP_TRI_BOYLE */
+} aop_request;
+
+typedef struct aop_options {
+    int32_t method;     /* aop_method */
+    int32_t base_case;  /* D&C base-case height in rows; 0 = tuned default */
+    int32_t flags;      /* reserved, pass 0 */
+    int32_t reserved;
+} aop_options;
+
+/* Counters accumulated by the kernels of the last batch call (for roofline
+ * accounting).  fft_points counts transform lengths N summed over forward and
+ * inverse transforms; conv_inputs counts input cells of the linear advances. */
+typedef struct aop_stats {
+    int64_t options;
+    int64_t convolutions;
+    int64_t fft_points;
+    int64_t fft_flops;          /* 5 N log2 N per complex transform */
+    int64_t conv_inputs;
+    int64_t conv_outputs;
+    int64_t basecase_cells;     /* FP64 cell updates in naive base cases */
+    int64_t stencil_cells;      /* FP64 cell updates of the plain stencil */
+    int64_t global_fft_bytes;   /* bytes moved by multi-pass (global) FFT passes */
+    double kernel_ms;           /* CUDA-event time of the pricing kernel(s) of the
+                                   last batch, measured on their launch stream */
+} aop_stats;
+
+typedef struct aop_ctx aop_ctx;
+
+/* Human-readable name of a status code (static string, never NULL). */
+const char *aop_status_string(aop_status s);
+
+/* Create a context on CUDA device `device`.  workspace_cap_bytes bounds the
+ * device workspace the context may hold (0 = 64 GiB).  The context owns a CUDA
+ * stream and lazily grows its workspace up to the cap.  *ctx receives NULL on
+ * failure. */
+aop_status aop_ctx_create(aop_ctx **ctx, int device, size_t workspace_cap_bytes);
+
+/* Release every device resource of the context.  NULL is accepted. */
+aop_status aop_ctx_destroy(aop_ctx *ctx);
+
+/* Price one option (Sec. 3-5), synchronously, with the FP64 FFT method on
+ * device 0 using an internal context.  *price_out in currency units. */
+aop_status price_american(int model, double S0, double K, double r, double q,
+                          double sigma, double expiry, int64_t T, double *price_out);
+
+/* Price one option with explicit method/options.  boundary_out (nullable,
+ * host, int32[T+1]) receives the red-green divider of every lattice row:
+ *   calls: boundary[i] = largest column j in [0, D i] whose continuation value
+ *          is >= its exercise value (Cor. 2.7), -1 if none (D = 1 binomial,
+ *          2 trinomial);
+ *   put:   boundary[n] = largest spatial index k in [-(T-n), T-n] whose
+ *          exercise value exceeds its continuation value (BSM boundary
+ *          theorem), AOP_BOUNDARY_NONE_PUT if none. */
+aop_status price_american_ex(const aop_request *req, const aop_options *opt,
+                             double *price_out, int32_t *boundary_out);
+
+/* Price n options given in host arrays; returns when prices[] and status[]
+ * (both host, length n) are filled.  status may be NULL.  Returns AOP_OK when
+ * the batch ran, even if individual options failed (see status[i]); a bad
+ * option does not fail the batch.  Copies to and from the device happen inside
+ * this call on `stream` (NULL = the context's stream). */
+aop_status price_american_batch(aop_ctx *ctx, int64_t n, const aop_request *reqs,
+                                const aop_options *opt, double *prices,
+                                aop_status *status, void *stream);
+
+/* Device-resident batch: d_reqs (aop_request[n]), d_prices (double[n]) and
+ * d_status (int32[n], nullable) are device pointers; enqueued on `stream`,
+ * returns without waiting.  d_boundary (nullable) is a device int32 array and
+ * d_boundary_offsets (device int64[n], required with d_boundary) gives the
+ * start of option i's T_i+1 entries in it.  The inputs must stay valid and
+ * unmodified until the stream reaches this work. */
+aop_status price_american_batch_device(aop_ctx *ctx, int64_t n, const aop_request *d_reqs,
+                                       const aop_options *opt, double *d_prices,
+                                       int32_t *d_status, int32_t *d_boundary,
+                                       const int64_t *d_boundary_offsets, void *stream);
+
+/* Linear advance of one row segment by h steps of a 2- or 3-point stencil
+ * (the FFT-based linear-stencil step used inside every trapezoid, Sec. 3.3
+ * "Solving a Trapezoid"): for count segments stored back to back in d_in
+ * (count*W doubles, device), writes d_out (count*(W - (nw-1)h) doubles):
+ *     out[x] = sum_{t=0}^{(nw-1)h} c_t in[x + t],
+ * where c is the h-fold self-convolution of the weights w[0..nw-1].
+ * method selects AOP_FFT_FP64 or AOP_FFT_FP32SPLIT.  Synchronous.
+ * Requires 1 <= nw-1, (nw-1)h < W <= 2^20. */
+aop_status aop_linear_advance_device(aop_ctx *ctx, int method, int nw, const double *w,
+                                     int64_t count, int64_t W, int64_t h,
+                                     const double *d_in, double *d_out, void *stream);
+
+/* Counters of the kernels launched by the last batch call on this context
+ * (synchronizes the context's stream). */
+aop_status aop_ctx_get_stats(aop_ctx *ctx, aop_stats *out);
+
+/* Library version string. */
+const char *aop_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* AMERICAN_H */

@@ -1,0 +1,232 @@
+"""GB300 (sm_103a) nonlinear-stencil American option pricer.
+
+A thin ctypes binding over the C ABI declared in ``include/american.h``
+(``libamerican.so``).  Every pricing step runs in the library's CUDA kernels;
+this module only marshals arguments.  If the shared library is missing or no
+CUDA device is usable the calls raise -- there is no CPU fallback.
+
+Method codes: FFT_FP64 (trapezoidal divide-and-conquer with FP64 FFT
+convolutions), FFT_FP32SPLIT (the same with FP32 hi/lo-split convolutions and
+FP64 base cases), STENCIL_FP64 (plain Theta(T^2) backward induction).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+import threading
+from typing import Iterable, List, Optional, Sequence
+
+import numpy as np
+
+from .workloads import Request  # noqa: F401  (re-exported for callers)
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libamerican.so")
+HEADER = os.path.join(os.path.dirname(HERE), "include", "american.h")
+
+BINOMIAL_CALL, TRINOMIAL_CALL, BSM_PUT = 0, 1, 2
+FFT_FP64, FFT_FP32SPLIT, STENCIL_FP64 = 0, 1, 2
+TRI_BOYLE, TRI_PAPER = 0, 1
+BOUNDARY_NONE_PUT = -(2 ** 31)
+MAX_T = 1 << 20
+STATUS = {0: "AOP_OK", 1: "AOP_EINVAL", 2: "AOP_EUNSTABLE", 3: "AOP_ENOMEM",
+          4: "AOP_ECUDA", 5: "AOP_ETIMEOUT", 6: "AOP_EBUSY", 7: "AOP_EINTERNAL"}
+
+REQUEST_DTYPE = np.dtype([("model", "<i4"), ("tri_form", "<i4"), ("S0", "<f8"), ("K", "<f8"),
+                          ("r", "<f8"), ("q", "<f8"), ("sigma", "<f8"), ("expiry", "<f8"),
+                          ("T", "<i8"), ("lambda", "<f8")], align=True)
+assert REQUEST_DTYPE.itemsize == 72
+
+
+class AopError(RuntimeError):
+    def __init__(self, code: int, what: str = ""):
+        self.code = int(code)
+        super().__init__("%s (%s)%s" % (STATUS.get(self.code, "status %d" % code),
+                                        status_string(self.code) if _lib_or_none() else "",
+                                        (": " + what) if what else ""))
+
+
+class _Options(ctypes.Structure):
+    _fields_ = [("method", ctypes.c_int32), ("base_case", ctypes.c_int32),
+                ("flags", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
+class _Stats(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_int64) for n in (
+        "options", "convolutions", "fft_points", "fft_flops", "conv_inputs", "conv_outputs",
+        "basecase_cells", "stencil_cells", "global_fft_bytes")] + [("kernel_ms", ctypes.c_double)]
+
+
+_lock = threading.Lock()
+_lib = None
+
+
+def _lib_or_none():
+    return _lib
+
+
+def load(path: Optional[str] = None):
+    """Load libamerican.so (raises if it has not been built)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        p = path or LIB_PATH
+        if not os.path.exists(p):
+            raise RuntimeError("libamerican.so not found at %s; run "
+                               "paper_2303_02317_gb300.build.build() (needs nvcc)" % p)
+        lib = ctypes.CDLL(p)
+        vp, i64, i32, dbl = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_double
+        lib.aop_status_string.restype = ctypes.c_char_p
+        lib.aop_status_string.argtypes = [ctypes.c_int]
+        lib.aop_version.restype = ctypes.c_char_p
+        lib.aop_ctx_create.argtypes = [ctypes.POINTER(vp), ctypes.c_int, ctypes.c_size_t]
+        lib.aop_ctx_destroy.argtypes = [vp]
+        lib.price_american.argtypes = [ctypes.c_int, dbl, dbl, dbl, dbl, dbl, dbl, i64,
+                                       ctypes.POINTER(dbl)]
+        lib.price_american_ex.argtypes = [vp, ctypes.POINTER(_Options), ctypes.POINTER(dbl), vp]
+        lib.price_american_batch.argtypes = [vp, i64, vp, ctypes.POINTER(_Options), vp, vp, vp]
+        lib.price_american_batch_device.argtypes = [vp, i64, vp, ctypes.POINTER(_Options), vp,
+                                                    vp, vp, vp, vp]
+        lib.aop_linear_advance_device.argtypes = [vp, ctypes.c_int, ctypes.c_int, vp, i64, i64,
+                                                  i64, vp, vp, vp]
+        lib.aop_ctx_get_stats.argtypes = [vp, ctypes.POINTER(_Stats)]
+        for f in ("aop_ctx_create", "aop_ctx_destroy", "price_american", "price_american_ex",
+                  "price_american_batch", "price_american_batch_device",
+                  "aop_linear_advance_device", "aop_ctx_get_stats"):
+            getattr(lib, f).restype = ctypes.c_int
+        _lib = lib
+        return lib
+
+
+def declared_symbols() -> List[str]:
+    """Names of the functions declared in include/american.h."""
+    txt = open(HEADER).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    names = re.findall(r"^\s*(?:const\s+)?[A-Za-z_][A-Za-z0-9_]*\s*\*?\s*([A-Za-z_][A-Za-z0-9_]*)\s*\(",
+                       txt, flags=re.M)
+    return [n for n in names if n not in ("if", "while", "for", "return")]
+
+
+def status_string(code: int) -> str:
+    return load().aop_status_string(int(code)).decode()
+
+
+def version() -> str:
+    return load().aop_version().decode()
+
+
+def _check(code: int, what: str = ""):
+    if code != 0:
+        raise AopError(code, what)
+
+
+def _opts(method: int, base_case: int = 0) -> _Options:
+    return _Options(int(method), int(base_case), 0, 0)
+
+
+def requests_array(reqs: Iterable) -> np.ndarray:
+    """Pack requests (workloads.Request, dicts or tuples) into aop_request[]."""
+    reqs = list(reqs)
+    a = np.zeros(len(reqs), dtype=REQUEST_DTYPE)
+    for i, r in enumerate(reqs):
+        g = (lambda k, d=0: r.get(k, d)) if isinstance(r, dict) else (lambda k, d=0: getattr(r, k, d))
+        a[i] = (int(g("model")), int(g("tri_form", 0) or 0), float(g("S0")), float(g("K")),
+                float(g("r")), float(g("q")), float(g("sigma")), float(g("expiry")), int(g("T")),
+                float(g("lam", 0.0) or 0.0))
+    return a
+
+
+def price_american(model: int, S0: float, K: float, r: float, q: float, sigma: float,
+                   expiry: float, T: int) -> float:
+    """One option, FP64 FFT method, device 0 (C: price_american)."""
+    out = ctypes.c_double()
+    _check(load().price_american(int(model), S0, K, r, q, sigma, expiry, int(T), ctypes.byref(out)))
+    return out.value
+
+
+def price_american_ex(req, method: int = FFT_FP64, base_case: int = 0, boundary: bool = False):
+    """One option with explicit method; returns price or (price, boundary[T+1])."""
+    arr = requests_array([req])
+    out = ctypes.c_double()
+    T = int(arr["T"][0])
+    b = np.empty(T + 1, dtype=np.int32) if boundary else None
+    o = _opts(method, base_case)
+    code = load().price_american_ex(arr.ctypes.data, ctypes.byref(o), ctypes.byref(out),
+                                    b.ctypes.data if b is not None else None)
+    _check(code, "price_american_ex")
+    return (out.value, b) if boundary else out.value
+
+
+class Context:
+    """An aop_ctx: a device, a stream and a capped workspace."""
+
+    def __init__(self, device: int = 0, workspace_cap_bytes: int = 0):
+        lib = load()
+        h = ctypes.c_void_p()
+        _check(lib.aop_ctx_create(ctypes.byref(h), int(device), ctypes.c_size_t(workspace_cap_bytes)),
+               "aop_ctx_create")
+        self._h = h
+        self.device = device
+
+    @property
+    def handle(self):
+        return self._h
+
+    def close(self):
+        if self._h:
+            load().aop_ctx_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    # host buffers in, host buffers out (C: price_american_batch)
+    def price_batch(self, reqs, method: int = FFT_FP64, base_case: int = 0, stream: int = 0):
+        arr = reqs if isinstance(reqs, np.ndarray) else requests_array(reqs)
+        n = len(arr)
+        prices = np.empty(n, dtype=np.float64)
+        status = np.empty(n, dtype=np.int32)
+        o = _opts(method, base_case)
+        _check(load().price_american_batch(self._h, n, arr.ctypes.data, ctypes.byref(o),
+                                           prices.ctypes.data, status.ctypes.data,
+                                           ctypes.c_void_p(stream) if stream else None),
+               "price_american_batch")
+        return prices, status
+
+    # device pointers (C: price_american_batch_device)
+    def price_batch_device(self, n: int, d_reqs: int, d_prices: int, d_status: int = 0,
+                           d_boundary: int = 0, d_boundary_offsets: int = 0,
+                           method: int = FFT_FP64, base_case: int = 0, stream: int = 0):
+        o = _opts(method, base_case)
+        _check(load().price_american_batch_device(
+            self._h, int(n), ctypes.c_void_p(d_reqs), ctypes.byref(o), ctypes.c_void_p(d_prices),
+            ctypes.c_void_p(d_status) if d_status else None,
+            ctypes.c_void_p(d_boundary) if d_boundary else None,
+            ctypes.c_void_p(d_boundary_offsets) if d_boundary_offsets else None,
+            ctypes.c_void_p(stream) if stream else None), "price_american_batch_device")
+
+    def linear_advance_device(self, method: int, w: Sequence[float], count: int, W: int, h: int,
+                              d_in: int, d_out: int, stream: int = 0):
+        wa = (ctypes.c_double * 3)(*(list(w) + [0.0] * (3 - len(w))))
+        _check(load().aop_linear_advance_device(self._h, int(method), len(w), wa, int(count), int(W),
+                                                int(h), ctypes.c_void_p(d_in), ctypes.c_void_p(d_out),
+                                                ctypes.c_void_p(stream) if stream else None),
+               "aop_linear_advance_device")
+
+    def stats(self) -> dict:
+        s = _Stats()
+        _check(load().aop_ctx_get_stats(self._h, ctypes.byref(s)), "aop_ctx_get_stats")
+        out = {k: int(getattr(s, k)) for k, _ in _Stats._fields_ if k != "kernel_ms"}
+        out["kernel_ms"] = float(s.kernel_ms)
+        return out

@@ -1,0 +1,382 @@
+// api.cu -- the C ABI (include/american.h): contexts, workspace, batches.
+#include <algorithm>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <mutex>
+#include <vector>
+
+#include "common.cuh"
+#include "internal.h"
+
+using namespace aop;
+
+struct aop_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    size_t cap = 0;
+    // workspace (grow-only)
+    void *ws = nullptr;
+    size_t ws_size = 0;
+    // per-batch device arrays (grow-only)
+    void *small = nullptr;
+    size_t small_size = 0;
+    // pinned host staging
+    void *pinned = nullptr;
+    size_t pinned_size = 0;
+    // twiddle tables
+    void *tw32 = nullptr, *tw64 = nullptr;
+    int tw_log2 = 0;
+    aop_stats *d_stats = nullptr;
+    int *d_err = nullptr;
+    int64_t *d_tmax = nullptr;
+    int64_t last_n = 0;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;   // bracket the pricing kernels
+    bool timed = false;
+};
+
+namespace {
+
+constexpr int kDefaultBaseCase = 16;
+
+aop_status cuda_fail(cudaError_t e) {
+    return e == cudaSuccess ? AOP_OK : (e == cudaErrorMemoryAllocation ? AOP_ENOMEM : AOP_ECUDA);
+}
+
+#define CK(x)                                     \
+    do {                                          \
+        cudaError_t e_ = (x);                     \
+        if (e_ != cudaSuccess) return cuda_fail(e_); \
+    } while (0)
+
+aop_status ensure(void **p, size_t *have, size_t need, size_t cap) {
+    if (*have >= need) return AOP_OK;
+    if (cap && need > cap) return AOP_ENOMEM;
+    if (*p) { cudaFree(*p); *p = nullptr; *have = 0; }
+    size_t sz = need + need / 8;
+    if (cap && sz > cap) sz = need;
+    cudaError_t e = cudaMalloc(p, sz);
+    if (e != cudaSuccess) { cudaGetLastError(); *p = nullptr; return AOP_ENOMEM; }
+    *have = sz;
+    return AOP_OK;
+}
+
+aop_status ensure_pinned(aop_ctx *c, size_t need) {
+    if (c->pinned_size >= need) return AOP_OK;
+    if (c->pinned) cudaFreeHost(c->pinned);
+    c->pinned = nullptr;
+    c->pinned_size = 0;
+    size_t sz = need + need / 4 + 4096;
+    if (cudaMallocHost(&c->pinned, sz) != cudaSuccess) { cudaGetLastError(); return AOP_ENOMEM; }
+    c->pinned_size = sz;
+    return AOP_OK;
+}
+
+aop_status ensure_twiddles(aop_ctx *c, int log2n) {
+    if (c->tw_log2 >= log2n) return AOP_OK;
+    if (c->tw32) cudaFree(c->tw32);
+    if (c->tw64) cudaFree(c->tw64);
+    c->tw32 = c->tw64 = nullptr;
+    c->tw_log2 = 0;
+    size_t half = (size_t)1 << (log2n - 1);
+    CK(cudaMalloc(&c->tw32, half * sizeof(float4)));
+    CK(cudaMalloc(&c->tw64, half * sizeof(double2)));
+    CK(launch_twiddles(log2n, c->tw32, c->tw64, c->stream));
+    c->tw_log2 = log2n;
+    return AOP_OK;
+}
+
+int resolve_base_case(const aop_options *opt) {
+    int b = (opt && opt->base_case > 0) ? opt->base_case : kDefaultBaseCase;
+    int p = 1;
+    while (p < b) p <<= 1;   // power of two
+    if (p < 2) p = 2;
+    if (p > 64) p = 64;
+    return p;
+}
+
+// Core of every batch: d_reqs etc. on the device, T_max known.
+aop_status run_batch(aop_ctx *c, int64_t n, const aop_request *d_reqs, const aop_options *opt,
+                     int64_t T_max, double *d_prices, int32_t *d_status, int32_t *d_bnd,
+                     const int64_t *d_bnd_off, cudaStream_t s, Params *d_params)
+{
+    const int method = opt ? opt->method : AOP_FFT_FP64;
+    if (method < 0 || method > 2) return AOP_EINVAL;
+    if (n == 0 || T_max < 1) return AOP_OK;
+    const int B = resolve_base_case(opt);
+    CK(cudaMemsetAsync(c->d_stats, 0, sizeof(aop_stats), s));
+    CK(cudaMemsetAsync(c->d_err, 0, sizeof(int), s));
+    if (method == AOP_STENCIL_FP64) {
+        size_t need = stencil_workspace_bytes(n, T_max);
+        aop_status st = ensure(&c->ws, &c->ws_size, need, c->cap);
+        if (st) return st;
+        CK(cudaEventRecord(c->ev0, s));
+        CK(run_stencil(n, d_params, T_max, c->ws, d_prices, d_status, d_bnd, d_bnd_off, c->d_stats, s));
+        CK(cudaEventRecord(c->ev1, s));
+    } else {
+        int64_t W = 2 * T_max + 1;
+        int lg = ilog2_ceil(W);
+        if (lg < 13) lg = 13;
+        aop_status st = ensure_twiddles(c, lg);
+        if (st) return st;
+        int grid = 0;
+        size_t need = dnc_workspace_bytes(method, n, T_max, B, &grid, c->device);
+        size_t have_cap = c->cap ? c->cap : need;
+        if (need > have_cap) need = have_cap;   // fewer resident CTAs
+        st = ensure(&c->ws, &c->ws_size, need, c->cap);
+        if (st) return st;
+        const void *tw = (method == AOP_FFT_FP64) ? c->tw64 : c->tw32;
+        CK(cudaEventRecord(c->ev0, s));
+        CK(run_dnc(method, n, d_params, T_max, B, c->ws, c->ws_size, tw, c->tw_log2, d_prices,
+                   d_status, d_bnd, d_bnd_off, c->d_stats, c->d_err, c->device, s));
+        CK(cudaEventRecord(c->ev1, s));
+    }
+    c->timed = true;
+    c->last_n = n;
+    return AOP_OK;
+}
+
+std::mutex g_default_mu;
+aop_ctx *g_default[64];
+
+aop_ctx *default_ctx(int device, aop_status *st) {
+    std::lock_guard<std::mutex> lk(g_default_mu);
+    if (device < 0 || device >= 64) { *st = AOP_EINVAL; return nullptr; }
+    if (!g_default[device]) {
+        aop_ctx *c = nullptr;
+        *st = aop_ctx_create(&c, device, 0);
+        if (*st) return nullptr;
+        g_default[device] = c;
+    }
+    *st = AOP_OK;
+    return g_default[device];
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *aop_status_string(aop_status s) {
+    switch (s) {
+    case AOP_OK: return "ok";
+    case AOP_EINVAL: return "invalid argument";
+    case AOP_EUNSTABLE: return "negative lattice probability or finite-difference weight";
+    case AOP_ENOMEM: return "workspace cap exceeded or device allocation failed";
+    case AOP_ECUDA: return "CUDA runtime error or no usable device";
+    case AOP_ETIMEOUT: return "bounded device wait gave up";
+    case AOP_EBUSY: return "no workspace slot free";
+    case AOP_EINTERNAL: return "device-side consistency check failed";
+    }
+    return "unknown status";
+}
+
+const char *aop_version(void) { return "paper_2303_02317_gb300 0.1 (sm_103a)"; }
+
+aop_status aop_ctx_create(aop_ctx **ctx, int device, size_t workspace_cap_bytes) {
+    if (!ctx) return AOP_EINVAL;
+    *ctx = nullptr;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) { cudaGetLastError(); return AOP_ECUDA; }
+    if (device < 0 || device >= ndev) return AOP_EINVAL;
+    aop_ctx *c = new aop_ctx();
+    c->device = device;
+    c->cap = workspace_cap_bytes ? workspace_cap_bytes : ((size_t)64 << 30);
+    cudaError_t e = cudaSetDevice(device);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaMalloc(&c->d_stats, sizeof(aop_stats));
+    if (e == cudaSuccess) e = cudaMalloc(&c->d_err, sizeof(int));
+    if (e == cudaSuccess) e = cudaMalloc(&c->d_tmax, sizeof(int64_t));
+    if (e == cudaSuccess) e = cudaMemset(c->d_stats, 0, sizeof(aop_stats));
+    if (e == cudaSuccess) e = cudaEventCreate(&c->ev0);
+    if (e == cudaSuccess) e = cudaEventCreate(&c->ev1);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        aop_ctx_destroy(c);
+        return cuda_fail(e);
+    }
+    *ctx = c;
+    return AOP_OK;
+}
+
+aop_status aop_ctx_destroy(aop_ctx *c) {
+    if (!c) return AOP_OK;
+    cudaSetDevice(c->device);
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    if (c->ws) cudaFree(c->ws);
+    if (c->small) cudaFree(c->small);
+    if (c->pinned) cudaFreeHost(c->pinned);
+    if (c->tw32) cudaFree(c->tw32);
+    if (c->tw64) cudaFree(c->tw64);
+    if (c->d_stats) cudaFree(c->d_stats);
+    if (c->d_err) cudaFree(c->d_err);
+    if (c->d_tmax) cudaFree(c->d_tmax);
+    if (c->ev0) cudaEventDestroy(c->ev0);
+    if (c->ev1) cudaEventDestroy(c->ev1);
+    if (c->stream) cudaStreamDestroy(c->stream);
+    delete c;
+    return AOP_OK;
+}
+
+aop_status price_american_batch_device(aop_ctx *c, int64_t n, const aop_request *d_reqs,
+                                       const aop_options *opt, double *d_prices, int32_t *d_status,
+                                       int32_t *d_bnd, const int64_t *d_bnd_off, void *stream) {
+    if (!c || n < 0 || (n > 0 && (!d_reqs || !d_prices)) || (d_bnd && !d_bnd_off)) return AOP_EINVAL;
+    if (n == 0) return AOP_OK;
+    CK(cudaSetDevice(c->device));
+    cudaStream_t s = stream ? (cudaStream_t)stream : c->stream;
+    // per-batch device arrays: params
+    aop_status st = ensure(&c->small, &c->small_size, (size_t)n * sizeof(Params) + 256, 0);
+    if (st) return st;
+    Params *d_params = (Params *)c->small;
+    CK(cudaMemsetAsync(c->d_tmax, 0, sizeof(int64_t), s));
+    CK(launch_params(n, d_reqs, d_params, d_status, c->d_tmax, s));
+    int64_t T_max = 0;
+    CK(cudaMemcpyAsync(&T_max, c->d_tmax, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    if (T_max == 0) {
+        // every option was rejected: fill NaN prices
+        CK(cudaMemsetAsync(d_prices, 0xff, (size_t)n * sizeof(double), s));
+        return AOP_OK;
+    }
+    return run_batch(c, n, d_reqs, opt, T_max, d_prices, d_status, d_bnd, d_bnd_off, s, d_params);
+}
+
+aop_status price_american_batch(aop_ctx *c, int64_t n, const aop_request *reqs, const aop_options *opt,
+                                double *prices, aop_status *status, void *stream) {
+    if (!c || n < 0 || (n > 0 && (!reqs || !prices))) return AOP_EINVAL;
+    if (n == 0) return AOP_OK;
+    CK(cudaSetDevice(c->device));
+    cudaStream_t s = stream ? (cudaStream_t)stream : c->stream;
+    const size_t rb = (size_t)n * sizeof(aop_request), pb = (size_t)n * sizeof(double),
+                 sb = (size_t)n * sizeof(int32_t);
+    aop_status st = ensure_pinned(c, rb + pb + sb + 64);
+    if (st) return st;
+    // device arrays: reqs | prices | status | params
+    size_t off_p = (rb + 255) & ~(size_t)255, off_s = (off_p + pb + 255) & ~(size_t)255,
+           off_par = (off_s + sb + 255) & ~(size_t)255;
+    st = ensure(&c->small, &c->small_size, off_par + (size_t)n * sizeof(Params) + 256, 0);
+    if (st) return st;
+    char *d = (char *)c->small;
+    aop_request *d_reqs = (aop_request *)d;
+    double *d_prices = (double *)(d + off_p);
+    int32_t *d_status = (int32_t *)(d + off_s);
+    Params *d_params = (Params *)(d + off_par);
+    char *h = (char *)c->pinned;
+    memcpy(h, reqs, rb);
+    int64_t T_max = 0;
+    for (int64_t i = 0; i < n; i++)
+        if (reqs[i].T > T_max && reqs[i].T <= AOP_MAX_T) T_max = reqs[i].T;
+    CK(cudaMemcpyAsync(d_reqs, h, rb, cudaMemcpyHostToDevice, s));
+    CK(launch_params(n, d_reqs, d_params, d_status, nullptr, s));
+    st = run_batch(c, n, d_reqs, opt, T_max, d_prices, d_status, nullptr, nullptr, s, d_params);
+    if (st) return st;
+    CK(cudaMemcpyAsync(h + rb, d_prices, pb, cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(h + rb + pb, d_status, sb, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    memcpy(prices, h + rb, pb);
+    if (status) {
+        const int32_t *hs = (const int32_t *)(h + rb + pb);
+        for (int64_t i = 0; i < n; i++) status[i] = (aop_status)hs[i];
+    }
+    return AOP_OK;
+}
+
+aop_status price_american_ex(const aop_request *req, const aop_options *opt, double *price_out,
+                             int32_t *boundary_out) {
+    if (!req || !price_out) return AOP_EINVAL;
+    if (req->T < 1 || req->T > AOP_MAX_T) return AOP_EINVAL;
+    aop_status st;
+    aop_ctx *c = default_ctx(0, &st);
+    if (!c) return st;
+    std::lock_guard<std::mutex> lk(g_default_mu);
+    CK(cudaSetDevice(c->device));
+    cudaStream_t s = c->stream;
+    const int64_t T = req->T;
+    // device: req | price | status | boundary | offset | params
+    size_t off_price = 256, off_stat = 512, off_off = 768, off_par = 1024,
+           off_b = off_par + ((sizeof(Params) + 255) & ~(size_t)255);
+    size_t need = off_b + (size_t)(T + 1) * sizeof(int32_t) + 256;
+    st = ensure(&c->small, &c->small_size, need, 0);
+    if (st) return st;
+    char *d = (char *)c->small;
+    st = ensure_pinned(c, (size_t)(T + 1) * sizeof(int32_t) + 512);
+    if (st) return st;
+    char *h = (char *)c->pinned;
+    memcpy(h, req, sizeof(aop_request));
+    int64_t zero = 0;
+    memcpy(h + 128, &zero, sizeof(zero));
+    CK(cudaMemcpyAsync(d, h, sizeof(aop_request), cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(d + off_off, h + 128, sizeof(int64_t), cudaMemcpyHostToDevice, s));
+    Params *d_params = (Params *)(d + off_par);
+    int32_t *d_status = (int32_t *)(d + off_stat);
+    CK(launch_params(1, (const aop_request *)d, d_params, d_status, nullptr, s));
+    int32_t *d_b = boundary_out ? (int32_t *)(d + off_b) : nullptr;
+    st = run_batch(c, 1, (const aop_request *)d, opt, T, (double *)(d + off_price), d_status, d_b,
+                   (const int64_t *)(d + off_off), s, d_params);
+    if (st) return st;
+    CK(cudaMemcpyAsync(h + 256, d + off_price, sizeof(double), cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(h + 264, d_status, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    if (d_b) CK(cudaMemcpyAsync(h + 512, d_b, (size_t)(T + 1) * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    int32_t ost;
+    memcpy(price_out, h + 256, sizeof(double));
+    memcpy(&ost, h + 264, sizeof(int32_t));
+    if (d_b) memcpy(boundary_out, h + 512, (size_t)(T + 1) * sizeof(int32_t));
+    return (aop_status)ost;
+}
+
+aop_status price_american(int model, double S0, double K, double r, double q, double sigma, double expiry,
+                          int64_t T, double *price_out) {
+    aop_request rq;
+    memset(&rq, 0, sizeof(rq));
+    rq.model = model;
+    rq.tri_form = AOP_TRI_BOYLE;
+    rq.S0 = S0; rq.K = K; rq.r = r; rq.q = q; rq.sigma = sigma; rq.expiry = expiry;
+    rq.T = T;
+    rq.lambda = 0.0;
+    aop_options o;
+    memset(&o, 0, sizeof(o));
+    o.method = AOP_FFT_FP64;
+    return price_american_ex(&rq, &o, price_out, nullptr);
+}
+
+aop_status aop_linear_advance_device(aop_ctx *c, int method, int nw, const double *w, int64_t count,
+                                     int64_t W, int64_t h, const double *d_in, double *d_out, void *stream) {
+    if (!c || !w || !d_in || !d_out) return AOP_EINVAL;
+    if (method != AOP_FFT_FP64 && method != AOP_FFT_FP32SPLIT) return AOP_EINVAL;
+    if (nw < 2 || nw > 3 || h < 1 || count < 0 || W > ((int64_t)1 << 20) || (int64_t)(nw - 1) * h >= W)
+        return AOP_EINVAL;
+    if (count == 0) return AOP_OK;
+    CK(cudaSetDevice(c->device));
+    cudaStream_t s = stream ? (cudaStream_t)stream : c->stream;
+    int lg = ilog2_ceil(W + 2);
+    if (lg < 13) lg = 13;
+    aop_status st = ensure_twiddles(c, lg + 1);
+    if (st) return st;
+    size_t need = linear_advance_workspace_bytes(method, W, h);
+    st = ensure(&c->ws, &c->ws_size, need, c->cap);
+    if (st) return st;
+    const void *tw = (method == AOP_FFT_FP64) ? c->tw64 : c->tw32;
+    CK(run_linear_advance(method, nw, w, count, W, h, d_in, d_out, tw, c->tw_log2, c->ws, c->ws_size,
+                          c->d_err, s));
+    CK(cudaStreamSynchronize(s));
+    return AOP_OK;
+}
+
+aop_status aop_ctx_get_stats(aop_ctx *c, aop_stats *out) {
+    if (!c || !out) return AOP_EINVAL;
+    CK(cudaSetDevice(c->device));
+    CK(cudaStreamSynchronize(c->stream));
+    CK(cudaDeviceSynchronize());
+    CK(cudaMemcpy(out, c->d_stats, sizeof(aop_stats), cudaMemcpyDeviceToHost));
+    out->options = c->last_n;
+    out->kernel_ms = 0.0;
+    if (c->timed) {
+        float ms = 0.f;
+        CK(cudaEventElapsedTime(&ms, c->ev0, c->ev1));
+        out->kernel_ms = ms;
+    }
+    return AOP_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,60 @@
+// internal.h -- host-side declarations shared by the library's translation units.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "../../include/american.h"
+
+namespace aop {
+
+struct Params;
+
+// Tunables of one batch launch.
+struct LaunchCfg {
+    int method;          // aop_method
+    int base_case;       // D&C base-case height (power of two)
+    int64_t T_max;       // largest step count in the batch
+    int any_call;        // batch holds at least one binomial/trinomial call
+    int any_put;         // batch holds at least one BSM put
+};
+
+// Workspace bump allocator over one device buffer owned by the context.
+struct Arena {
+    char *base = nullptr;
+    size_t size = 0, used = 0;
+    void *take(size_t bytes) {
+        size_t off = (used + 255) & ~(size_t)255;
+        if (off + bytes > size) return nullptr;
+        used = off + bytes;
+        return base + off;
+    }
+};
+
+// setup.cu
+cudaError_t launch_params(int64_t n, const aop_request *d_reqs, Params *d_params,
+                          int32_t *d_status, int64_t *d_tmax, cudaStream_t s);
+cudaError_t launch_twiddles(int log2n, void *d_tw32, void *d_tw64, cudaStream_t s);
+cudaError_t launch_fill_i32(int32_t *p, int64_t n, int32_t v, cudaStream_t s);
+
+// stencil.cu -- plain Theta(T^2) lattice loop (temporally blocked)
+size_t stencil_workspace_bytes(int64_t n, int64_t T_max);
+cudaError_t run_stencil(int64_t n, const Params *d_params, int64_t T_max, void *ws,
+                        double *d_prices, int32_t *d_status, int32_t *d_bnd,
+                        const int64_t *d_bnd_off, aop_stats *d_stats, cudaStream_t s);
+
+// dnc.cu -- trapezoidal divide-and-conquer pricer
+size_t dnc_workspace_bytes(int method, int64_t n, int64_t T_max, int base_case, int *grid_out,
+                           int device);
+cudaError_t run_dnc(int method, int64_t n, const Params *d_params, int64_t T_max, int base_case,
+                    void *ws, size_t ws_bytes, const void *d_tw, int tw_log2, double *d_prices,
+                    int32_t *d_status, int32_t *d_bnd, const int64_t *d_bnd_off,
+                    aop_stats *d_stats, int *d_err, int device, cudaStream_t s);
+cudaError_t run_linear_advance(int method, int nw, const double *w, int64_t count, int64_t W,
+                               int64_t h, const double *d_in, double *d_out, const void *d_tw,
+                               int tw_log2, void *ws, size_t ws_bytes, int *d_err,
+                               cudaStream_t s);
+size_t linear_advance_workspace_bytes(int method, int64_t W, int64_t h);
+
+}  // namespace aop

@@ -1,0 +1,86 @@
+// setup.cu -- per-option parameter setup (hot-path row a1) and the FFT twiddle
+// tables shared by every convolution.
+#include <algorithm>
+#include "common.cuh"
+#include "internal.h"
+
+namespace aop {
+
+namespace {
+
+__global__ void params_kernel(int64_t n, const aop_request *reqs, Params *params,
+                              int32_t *status, unsigned long long *tmax)
+{
+    unsigned long long local = 0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const aop_request q = reqs[i];
+        Params P = make_params(q);
+        params[i] = P;
+        if (status) status[i] = P.status;
+        if (P.status == AOP_OK) local = max(local, (unsigned long long)P.T);
+    }
+    if (tmax) {
+        for (int off = 16; off > 0; off >>= 1)
+            local = max(local, __shfl_down_sync(0xffffffffu, local, off));
+        if ((threadIdx.x & 31) == 0) atomicMax(tmax, local);
+    }
+}
+
+// Twiddles w^k = e^{-2 pi i k / N} for k < N/2, N = 2^log2n.
+//   tw64[k]        = (cos, sin) in FP64
+//   tw32[2k], [2k+1] = hi and lo FP32 parts of the same value (the lo part is
+//                    the FP64 residual, so hi + lo carries ~48 bits).
+__global__ void twiddle_kernel(int log2n, float4 *tw32, double2 *tw64)
+{
+    const int64_t half = (int64_t)1 << (log2n - 1);
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < half;
+         k += (int64_t)gridDim.x * blockDim.x) {
+        double s, c;
+        // angle = -2 pi k / N = -pi * (k / (N/2)); sincospi takes the multiple of pi
+        sincospi(-(double)k / (double)half, &s, &c);
+        if (tw64) tw64[k] = make_double2(c, s);
+        if (tw32) {
+            float ch = (float)c, sh = (float)s;
+            float cl = (float)(c - (double)ch), sl = (float)(s - (double)sh);
+            tw32[k] = make_float4(ch, sh, cl, sl);
+        }
+    }
+}
+
+__global__ void fill_i32_kernel(int32_t *p, int64_t n, int32_t v)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        p[i] = v;
+}
+
+}  // namespace
+
+cudaError_t launch_params(int64_t n, const aop_request *d_reqs, Params *d_params,
+                          int32_t *d_status, int64_t *d_tmax, cudaStream_t s)
+{
+    if (n == 0) return cudaSuccess;
+    int blocks = (int)std::min<int64_t>((n + 255) / 256, 1024);
+    params_kernel<<<blocks, 256, 0, s>>>(n, d_reqs, d_params, d_status,
+                                         (unsigned long long *)d_tmax);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_twiddles(int log2n, void *d_tw32, void *d_tw64, cudaStream_t s)
+{
+    int64_t half = (int64_t)1 << (log2n - 1);
+    int blocks = (int)std::min<int64_t>((half + 255) / 256, 4096);
+    twiddle_kernel<<<blocks, 256, 0, s>>>(log2n, (float4 *)d_tw32, (double2 *)d_tw64);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fill_i32(int32_t *p, int64_t n, int32_t v, cudaStream_t s)
+{
+    if (n == 0) return cudaSuccess;
+    int blocks = (int)std::min<int64_t>((n + 255) / 256, 4096);
+    fill_i32_kernel<<<blocks, 256, 0, s>>>(p, n, v);
+    return cudaGetLastError();
+}
+
+}  // namespace aop

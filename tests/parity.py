@@ -1,0 +1,39 @@
+"""Shared parity rules for the GPU tests (no library code here).
+
+Tolerances (derived in DESIGN.md, "Parity tolerances"):
+  FP64 methods (FFT_FP64, STENCIL_FP64):
+      |gpu - oracle| <= 1e-10 |oracle| + 1e-12 K
+  FP32-split FFT:
+      |gpu - oracle| <= FP32_REL |oracle| + FP32_ABS K
+Boundary rows may differ from the oracle only where the oracle's margin
+|continuation - exercise| at the divider is within the tie band of the method.
+"""
+import numpy as np
+
+import oracle
+
+FP64_REL = 1e-10
+FP64_ABS = 1e-12
+FP32_REL = 2e-6
+FP32_ABS = 2e-6
+
+
+def price_tol(method, price_ref, K):
+    if method == 1:
+        return FP32_REL * abs(price_ref) + FP32_ABS * K
+    return FP64_REL * abs(price_ref) + FP64_ABS * K
+
+
+def tie_band(method, req):
+    base = oracle.tie_band(req)
+    return base if method != 1 else base * 1e6
+
+
+def check_boundary(method, req, got, want, margin):
+    """Return the rows that differ outside the tie band."""
+    got = np.asarray(got)
+    want = np.asarray(want)
+    diff = np.nonzero(got != want)[0]
+    band = tie_band(method, req)
+    bad = [int(i) for i in diff if not (margin[i] <= band and abs(int(got[i]) - int(want[i])) <= 1)]
+    return bad, len(diff)

@@ -1,0 +1,52 @@
+"""GPU parity of the FFT linear advance (the linear-stencil step inside every
+trapezoid) against the plain definition: the stencil applied h times, i.e. a
+correlation with the h-fold self-convolution of the weights, in FP64 numpy."""
+import numpy as np
+import pytest
+
+import paper_2303_02317_gb300 as aop
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    c = aop.Context(0)
+    yield c
+    c.close()
+
+
+def _direct(x, w, h):
+    k = np.array([1.0])
+    for _ in range(h):
+        k = np.convolve(k, w)
+    return np.stack([np.correlate(row, k, "valid") for row in x])
+
+
+CASES = [
+    # (nw, W, h, count)
+    (2, 5, 1, 3), (2, 64, 31, 2), (2, 100, 37, 4), (3, 100, 10, 2), (3, 4096, 1000, 2),
+    (2, 4097, 2000, 1), (3, 5000, 1200, 2), (2, 70000, 3000, 1), (3, 65537, 8000, 1),
+]
+
+
+@pytest.mark.parametrize("method", [aop.FFT_FP64, aop.FFT_FP32SPLIT], ids=["fft64", "fft32"])
+@pytest.mark.parametrize("nw,W,h,count", CASES)
+def test_linear_advance(ctx, method, nw, W, h, count):
+    rng = np.random.default_rng(W * 7 + h)
+    w = rng.uniform(0.2, 1.0, nw)
+    w = w / w.sum() * 0.999
+    x = np.abs(rng.normal(size=(count, W))) * rng.uniform(0.1, 100.0)
+    ref = _direct(x, w, h)
+    dx = torch.tensor(x, dtype=torch.float64, device="cuda")
+    nout = W - (nw - 1) * h
+    dy = torch.full((count, nout), float("nan"), dtype=torch.float64, device="cuda")
+    ctx.linear_advance_device(method, list(w), count, W, h, dx.data_ptr(), dy.data_ptr())
+    got = dy.cpu().numpy()
+    scale = np.abs(x).max()
+    tol = 1e-12 * scale if method == aop.FFT_FP64 else 1e-6 * scale
+    err = np.abs(got - ref).max()
+    assert err <= tol, (err, tol, err / scale)

@@ -1,0 +1,120 @@
+"""GPU parity: every method against the FP64 CPU oracle, element by element
+(price and the divider of every lattice row), through the C ABI."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import paper_2303_02317_gb300 as aop
+from paper_2303_02317_gb300 import workloads as wl
+from tests import parity
+
+pytestmark = pytest.mark.gpu
+
+METHODS = [aop.FFT_FP64, aop.FFT_FP32SPLIT, aop.STENCIL_FP64]
+MNAME = {0: "fft64", 1: "fft32", 2: "stencil"}
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    torch = pytest.importorskip("torch")
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    aop.load()
+    c = aop.Context(0)
+    yield c
+    c.close()
+
+
+def _check(req, method, base_case=0):
+    d = req.as_dict() if hasattr(req, "as_dict") else dict(req)
+    ref, bref, margin = oracle.price_american(d, with_boundary=True, with_margin=True)
+    got, b = aop.price_american_ex(d, method=method, base_case=base_case, boundary=True)
+    tol = parity.price_tol(method, ref, d["K"])
+    assert abs(got - ref) <= tol, (MNAME[method], d, got, ref, abs(got - ref), tol)
+    bad, ndiff = parity.check_boundary(method, d, b, bref, margin)
+    assert not bad, (MNAME[method], d, "rows", bad[:8], [(int(b[i]), int(bref[i]), margin[i]) for i in bad[:4]])
+    return got, ref, ndiff
+
+
+def _edge_cases():
+    base = wl.fixed_call(0, 300)
+    out = [
+        base.with_T(1), base.with_T(2), base.with_T(3), base.with_T(7),
+        wl.fixed_call(1, 1), wl.fixed_call(1, 5), wl.fixed_bsm_put(1), wl.fixed_bsm_put(2),
+        wl.fixed_bsm_put(5),
+        # deep in the money with a large yield: immediate exercise, all green
+        wl.Request(0, 150.0, 50.0, 0.01, 0.08, 0.15, 2.0, 257),
+        wl.Request(1, 150.0, 50.0, 0.01, 0.08, 0.15, 2.0, 257, math.sqrt(3)),
+        # no yield: the call is never exercised early, whole rows red
+        wl.Request(0, 100.0, 100.0, 0.05, 0.0, 0.3, 1.0, 513),
+        wl.Request(1, 100.0, 100.0, 0.05, 0.0, 0.3, 1.0, 513, 0.0, 1),
+        # far out of the money call
+        wl.Request(0, 50.0, 150.0, 0.05, 0.02, 0.2, 0.5, 300),
+        # puts: no rate (no early exercise), deep in and out of the money
+        wl.Request(2, 100.0, 100.0, 0.0, 0.0, 0.3, 1.0, 400),
+        wl.Request(2, 100.0, 100.0, 1e-6, 0.0, 0.6, 3.0, 400),   # divider jumps at row 1
+        wl.Request(2, 150.0, 50.0, 0.05, 0.0, 0.2, 1.0, 400),
+        wl.Request(2, 50.0, 150.0, 0.08, 0.0, 0.2, 3.0, 400),
+        # the paper's experiment parameters (Sec. 6)
+        wl.paper_params(0, 1000), wl.paper_params(1, 1000), wl.paper_params(2, 1000),
+        wl.single_binomial_t2048(),
+    ]
+    return out
+
+
+@pytest.mark.parametrize("method", METHODS, ids=[MNAME[m] for m in METHODS])
+def test_edge_cases(ctx, method):
+    for r in _edge_cases():
+        _check(r, method)
+
+
+@pytest.mark.parametrize("method", METHODS, ids=[MNAME[m] for m in METHODS])
+def test_random_small(ctx, method):
+    for r in wl.random_small(45, seed=11, T_range=(8, 700)):
+        _check(r, method)
+
+
+@pytest.mark.parametrize("method", [aop.FFT_FP64, aop.FFT_FP32SPLIT], ids=["fft64", "fft32"])
+@pytest.mark.parametrize("B", [2, 8, 32, 64])
+def test_base_case_heights(ctx, method, B):
+    """The trapezoid cut does not change the result (any base-case height)."""
+    for r in wl.random_small(9, seed=100 + B, T_range=(200, 1500)):
+        _check(r, method, base_case=B)
+
+
+@pytest.mark.parametrize("method", METHODS, ids=[MNAME[m] for m in METHODS])
+@pytest.mark.parametrize("T", [4095, 8192])
+def test_configs_mid_size(ctx, method, T):
+    """Benchmark parameter sets at sizes the oracle runs in seconds: several
+    shared-memory tiles, multi-pass transforms and ragged tails."""
+    for r in (wl.fixed_call(0, T), wl.fixed_call(1, T), wl.fixed_call(1, T, wl.TRI_PAPER),
+              wl.fixed_bsm_put(T)):
+        _check(r, method)
+
+
+@pytest.mark.parametrize("method", METHODS, ids=[MNAME[m] for m in METHODS])
+def test_batch_matches_single(ctx, method):
+    reqs = wl.random_small(24, seed=5, T_range=(16, 900))
+    prices, status = ctx.price_batch(reqs, method=method)
+    assert (status == 0).all()
+    for r, p in zip(reqs, prices):
+        ref = oracle.price_american(r.as_dict())
+        assert abs(p - ref) <= parity.price_tol(method, ref, r.K)
+
+
+def test_invalid_and_unstable_requests(ctx):
+    good = wl.fixed_call(0, 64)
+    bad = [
+        wl.Request(0, 0.0, 100, 0.05, 0.03, 0.2, 1.0, 64),      # S0 <= 0
+        wl.Request(0, 100, 100, 0.05, 0.03, 0.0, 1.0, 64),      # sigma <= 0
+        wl.Request(2, 100, 100, 0.05, 0.01, 0.2, 1.0, 64),      # BSM with a yield
+        wl.Request(0, 100, 100, 0.5, 0.0, 0.001, 1.0, 4),       # p > 1
+    ]
+    for method in METHODS:
+        prices, status = ctx.price_batch([good] + bad + [good], method=method)
+        assert status.tolist() == [0, 1, 1, 1, 2, 0]
+        assert np.isnan(prices[1:5]).all()
+        ref = oracle.price_american(good.as_dict())
+        assert abs(prices[0] - ref) <= parity.price_tol(method, ref, good.K)
+        assert prices[0] == prices[-1]

@@ -234,7 +234,7 @@ def test_bsm_divider_theorem(oracle_lib, seed):
     P = oracle_lib.params(req)
     s0 = math.log(req["S0"] / req["K"])
     NONE = oracle_lib.INT32_MIN
-    for n in range(T):
+    for n in range(1, T):      # from row 1: see test_bsm_expiry_row_exception
         if bnd[n] == NONE:
             continue
         if bnd[n + 1] != NONE:
@@ -259,3 +259,19 @@ def test_invalid_inputs_rejected(oracle_lib):
     assert oracle_lib.status_of(dict(wl.fixed_bsm_put(64).as_dict(), q=0.01)) == 1
     # r - q so large at tiny sigma that p > 1
     assert oracle_lib.status_of(dict(base, sigma=0.001, r=0.5, T=4)) == 2
+
+
+def test_bsm_expiry_row_exception(oracle_lib):
+    """The divider theorem's proof uses a divider cell that is green through
+    the max at row n; at the expiry row (n = 0) cells are green by their payoff
+    alone, so the step 0 -> 1 can move the divider by many cells (r = 0: no
+    cell stays green at all, the American put equals the European one).  From
+    row 1 on the theorem holds again."""
+    r0 = dict(model=2, S0=100.0, K=100.0, r=0.0, q=0.0, sigma=0.3, expiry=1.0, T=400)
+    _, b, _ = oracle_lib.price_american(r0, with_boundary=True, with_margin=True)
+    assert b[0] == -1 and (b[1:] == oracle_lib.INT32_MIN).all()
+    r1 = dict(r0, r=1e-6, sigma=0.6, expiry=3.0)
+    _, b, _ = oracle_lib.price_american(r1, with_boundary=True, with_margin=True)
+    assert b[0] - b[1] > 1
+    live = [(b[n], b[n + 1]) for n in range(1, 400) if b[n + 1] != oracle_lib.INT32_MIN]
+    assert live and all(0 <= x - y <= 1 for x, y in live)
