@@ -169,6 +169,8 @@ def main():
     ap.add_argument("--method", default="fft32", choices=["fft32", "fft64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--stencil-sample", type=int, default=4)
+    ap.add_argument("--small", action="store_true",
+                    help="reduced book (T=2^15, 152 options) for profiler captures")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -188,6 +190,11 @@ def main():
     dev = torch.device("cuda", local)
     method = aop.FFT_FP32SPLIT if args.method == "fft32" else aop.FFT_FP64
 
+    global T_BENCH, N_BINOMIAL, N_TRINOMIAL, WORKLOAD
+    if args.small:
+        # reduced book of the same kernel for profiler captures
+        T_BENCH, N_BINOMIAL, N_TRINOMIAL = 1 << 15, 76, 76
+        WORKLOAD = "precision_sweep_T32768_76binomial_76trinomial"
     reqs = wl.precision_sweep(T=T_BENCH, n_binomial=N_BINOMIAL, n_trinomial=N_TRINOMIAL)
     n = len(reqs)
     arr = aop.requests_array(reqs)
@@ -195,13 +202,14 @@ def main():
     d_reqs = torch.from_numpy(arr.view(np.uint8).copy()).to(dev)
     d_prices = torch.empty(n, dtype=torch.float64, device=dev)
     d_status = torch.empty(n, dtype=torch.int32, device=dev)
-    stream = torch.cuda.current_stream(dev)
+    stream = torch.cuda.Stream(dev)       # a real stream: its events see the library's kernels
+    torch.cuda.set_stream(stream)
     sh = stream.cuda_stream
     flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)   # > L2 (129 MB)
 
     def step():
         ctx.price_batch_device(n, d_reqs.data_ptr(), d_prices.data_ptr(), d_status.data_ptr(),
-                               method=method, stream=sh)
+                               method=method, stream=sh, flags=aop.FLAG_OPTION_TIMES)
 
     for _ in range(args.warmup):
         step()
@@ -219,13 +227,16 @@ def main():
         dist.barrier()
     torch.cuda.synchronize(dev)
     t_wall = time.perf_counter()
+    opt_ms = []
     for k in range(args.steps):
         flush.fill_(k & 0xff)
         ev[k][0].record(stream)
         step()
         ev[k][1].record(stream)
         kernel_ms.append(ctx.stats()["kernel_ms"])
+        opt_ms.append(ctx.option_times_ns(n) / 1e6)
     torch.cuda.synchronize(dev)
+    opt_ms = np.concatenate(opt_ms)
     t_wall = time.perf_counter() - t_wall
     clocks = sampler.stop()
     step_ms = [a.elapsed_time(b) for a, b in ev]
@@ -257,6 +268,9 @@ def main():
     acc = {}
     if method == aop.FFT_FP32SPLIT:
         p64, s64 = ctx.price_batch(arr, method=aop.FFT_FP64)
+        acc_nonfinite = int((~np.isfinite(prices32)).sum() + (~np.isfinite(p64)).sum())
+        if acc_nonfinite:
+            raise SystemExit("non-finite prices: %d" % acc_nonfinite)
         ok = (s64 == 0)
         rel = np.abs(prices32[ok] - p64[ok]) / np.maximum(np.abs(p64[ok]), 1e-300)
         ab = np.abs(prices32[ok] - p64[ok])
@@ -268,20 +282,22 @@ def main():
         p64 = prices32
 
     # ---- plain FP64 stencil on a sample (ms/option)
-    samp = [reqs[i] for i in range(args.stencil_sample // 2)] + \
-           [reqs[N_BINOMIAL + i] for i in range(args.stencil_sample - args.stencil_sample // 2)]
-    sarr = aop.requests_array(samp)
-    ps, ss = ctx.price_batch(sarr, method=aop.STENCIL_FP64)
-    sstats = ctx.stats()
-    stencil_ms = sstats["kernel_ms"]
-    stencil = {"sample": "%d options of the book (%d binomial, %d trinomial)" % (
-        len(samp), sum(1 for r in samp if r.model == 0), sum(1 for r in samp if r.model == 1)),
-        "ms_per_option": stencil_ms / len(samp), "options_per_s": len(samp) / (stencil_ms / 1e3),
-        "cells": sstats["stencil_cells"],
-        "fp64_gcells_per_s": sstats["stencil_cells"] / (stencil_ms / 1e3) / 1e9}
-    idx = [i for i in range(args.stencil_sample // 2)] + \
-          [N_BINOMIAL + i for i in range(args.stencil_sample - args.stencil_sample // 2)]
-    stencil["max_rel_fft64_vs_stencil"] = float(np.max(np.abs(p64[idx] - ps) / np.abs(ps)))
+    stencil = None
+    if args.stencil_sample > 0:
+        samp = [reqs[i] for i in range(args.stencil_sample // 2)] + \
+               [reqs[N_BINOMIAL + i] for i in range(args.stencil_sample - args.stencil_sample // 2)]
+        sarr = aop.requests_array(samp)
+        ps, ss = ctx.price_batch(sarr, method=aop.STENCIL_FP64)
+        sstats = ctx.stats()
+        stencil_ms = sstats["kernel_ms"]
+        stencil = {"sample": "%d options of the book (%d binomial, %d trinomial)" % (
+            len(samp), sum(1 for r in samp if r.model == 0), sum(1 for r in samp if r.model == 1)),
+            "ms_per_option": stencil_ms / len(samp), "options_per_s": len(samp) / (stencil_ms / 1e3),
+            "cells": sstats["stencil_cells"],
+            "fp64_gcells_per_s": sstats["stencil_cells"] / (stencil_ms / 1e3) / 1e9}
+        idx = [i for i in range(args.stencil_sample // 2)] + \
+              [N_BINOMIAL + i for i in range(args.stencil_sample - args.stencil_sample // 2)]
+        stencil["max_rel_fft64_vs_stencil"] = float(np.max(np.abs(p64[idx] - ps) / np.abs(ps)))
 
     # ---- roofline of the pricing kernel: FFT flops (FP32 or FP64) over time
     flops = stats["fft_flops"]
@@ -316,6 +332,10 @@ def main():
         "metric": "options_per_second", "value": value, "unit": "options/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
         "ms_per_option": ms_step / n, "higher_is_better": True, "scaling": "weak",
+        "option_device_ms": {"p50": float(np.percentile(opt_ms, 50)),
+                             "p99": float(np.percentile(opt_ms, 99)),
+                             "max": float(opt_ms.max()), "mean": float(opt_ms.mean()),
+                             "what": "per-option time inside the pricing kernel, all options of a step in flight together"},
         "vs_baseline": None,
         "dtype": "f32split+f64" if method == aop.FFT_FP32SPLIT else "f64",
         "data": "synthetic",
@@ -329,7 +349,7 @@ def main():
         "roofline": roof,
         "accuracy": acc,
         "stencil_fp64": stencil,
-        "speedup_vs_stencil_ms_per_option": stencil["ms_per_option"] / (ms_step / n),
+        "speedup_vs_stencil_ms_per_option": (stencil["ms_per_option"] / (ms_step / n)) if stencil else None,
         "cpu_baseline": cpu,
         "kernel_stats": stats,
         "wall_s_timed": t_wall,

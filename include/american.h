@@ -90,10 +90,12 @@ typedef struct aop_request {
     double lambda;      /* trinomial stretch for AOP_TRI_BOYLE */
 } aop_request;
 
+#define AOP_FLAG_OPTION_TIMES 1   /* record each option's device time (D&C methods) */
+
 typedef struct aop_options {
     int32_t method;     /* aop_method */
     int32_t base_case;  /* D&C base-case height in rows; 0 = tuned default */
-    int32_t flags;      /* reserved, pass 0 */
+    int32_t flags;      /* AOP_FLAG_* bits, 0 for none */
     int32_t reserved;
 } aop_options;
 
@@ -179,6 +181,12 @@ aop_status aop_linear_advance_device(aop_ctx *ctx, int method, int nw, const dou
 /* Counters of the kernels launched by the last batch call on this context
  * (synchronizes the context's stream). */
 aop_status aop_ctx_get_stats(aop_ctx *ctx, aop_stats *out);
+
+/* Per-option device time (ns, from the first to the last instruction the
+ * pricing kernel spent on the option) of the last D&C batch that was run with
+ * AOP_FLAG_OPTION_TIMES; ns_out is a host array of n <= batch size entries.
+ * Synchronizes the context.  AOP_EINVAL if the last batch did not record them. */
+aop_status aop_ctx_get_option_times(aop_ctx *ctx, int64_t n, int64_t *ns_out);
 
 /* Library version string. */
 const char *aop_version(void);

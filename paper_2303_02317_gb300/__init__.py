@@ -92,7 +92,8 @@ def load(path: Optional[str] = None):
         lib.aop_linear_advance_device.argtypes = [vp, ctypes.c_int, ctypes.c_int, vp, i64, i64,
                                                   i64, vp, vp, vp]
         lib.aop_ctx_get_stats.argtypes = [vp, ctypes.POINTER(_Stats)]
-        for f in ("aop_ctx_create", "aop_ctx_destroy", "price_american", "price_american_ex",
+        lib.aop_ctx_get_option_times.argtypes = [vp, i64, vp]
+        for f in ("aop_ctx_get_option_times", "aop_ctx_create", "aop_ctx_destroy", "price_american", "price_american_ex",
                   "price_american_batch", "price_american_batch_device",
                   "aop_linear_advance_device", "aop_ctx_get_stats"):
             getattr(lib, f).restype = ctypes.c_int
@@ -122,8 +123,11 @@ def _check(code: int, what: str = ""):
         raise AopError(code, what)
 
 
-def _opts(method: int, base_case: int = 0) -> _Options:
-    return _Options(int(method), int(base_case), 0, 0)
+FLAG_OPTION_TIMES = 1
+
+
+def _opts(method: int, base_case: int = 0, flags: int = 0) -> _Options:
+    return _Options(int(method), int(base_case), int(flags), 0)
 
 
 def requests_array(reqs: Iterable) -> np.ndarray:
@@ -192,12 +196,13 @@ class Context:
         self.close()
 
     # host buffers in, host buffers out (C: price_american_batch)
-    def price_batch(self, reqs, method: int = FFT_FP64, base_case: int = 0, stream: int = 0):
+    def price_batch(self, reqs, method: int = FFT_FP64, base_case: int = 0, stream: int = 0,
+                    flags: int = 0):
         arr = reqs if isinstance(reqs, np.ndarray) else requests_array(reqs)
         n = len(arr)
         prices = np.empty(n, dtype=np.float64)
         status = np.empty(n, dtype=np.int32)
-        o = _opts(method, base_case)
+        o = _opts(method, base_case, flags)
         _check(load().price_american_batch(self._h, n, arr.ctypes.data, ctypes.byref(o),
                                            prices.ctypes.data, status.ctypes.data,
                                            ctypes.c_void_p(stream) if stream else None),
@@ -207,8 +212,9 @@ class Context:
     # device pointers (C: price_american_batch_device)
     def price_batch_device(self, n: int, d_reqs: int, d_prices: int, d_status: int = 0,
                            d_boundary: int = 0, d_boundary_offsets: int = 0,
-                           method: int = FFT_FP64, base_case: int = 0, stream: int = 0):
-        o = _opts(method, base_case)
+                           method: int = FFT_FP64, base_case: int = 0, stream: int = 0,
+                           flags: int = 0):
+        o = _opts(method, base_case, flags)
         _check(load().price_american_batch_device(
             self._h, int(n), ctypes.c_void_p(d_reqs), ctypes.byref(o), ctypes.c_void_p(d_prices),
             ctypes.c_void_p(d_status) if d_status else None,
@@ -223,6 +229,12 @@ class Context:
                                                 int(h), ctypes.c_void_p(d_in), ctypes.c_void_p(d_out),
                                                 ctypes.c_void_p(stream) if stream else None),
                "aop_linear_advance_device")
+
+    def option_times_ns(self, n: int) -> np.ndarray:
+        out = np.empty(int(n), dtype=np.int64)
+        _check(load().aop_ctx_get_option_times(self._h, int(n), out.ctypes.data),
+               "aop_ctx_get_option_times")
+        return out
 
     def stats(self) -> dict:
         s = _Stats()

@@ -30,6 +30,9 @@ struct aop_ctx {
     aop_stats *d_stats = nullptr;
     int *d_err = nullptr;
     int64_t *d_tmax = nullptr;
+    int64_t *d_opt_ns = nullptr;     // per-option device time of the last D&C batch
+    size_t opt_ns_cap = 0;
+    bool opt_ns_valid = false;
     int64_t last_n = 0;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;   // bracket the pricing kernels
     bool timed = false;
@@ -126,9 +129,17 @@ aop_status run_batch(aop_ctx *c, int64_t n, const aop_request *d_reqs, const aop
         st = ensure(&c->ws, &c->ws_size, need, c->cap);
         if (st) return st;
         const void *tw = (method == AOP_FFT_FP64) ? c->tw64 : c->tw32;
+        int64_t *opt_ns = nullptr;
+        c->opt_ns_valid = false;
+        if (opt && (opt->flags & AOP_FLAG_OPTION_TIMES)) {
+            st = ensure((void **)&c->d_opt_ns, &c->opt_ns_cap, (size_t)n * sizeof(int64_t), 0);
+            if (st) return st;
+            opt_ns = c->d_opt_ns;
+            c->opt_ns_valid = true;
+        }
         CK(cudaEventRecord(c->ev0, s));
         CK(run_dnc(method, n, d_params, T_max, B, c->ws, c->ws_size, tw, c->tw_log2, d_prices,
-                   d_status, d_bnd, d_bnd_off, c->d_stats, c->d_err, c->device, s));
+                   d_status, d_bnd, d_bnd_off, c->d_stats, c->d_err, opt_ns, c->device, s));
         CK(cudaEventRecord(c->ev1, s));
     }
     c->timed = true;
@@ -210,6 +221,7 @@ aop_status aop_ctx_destroy(aop_ctx *c) {
     if (c->d_stats) cudaFree(c->d_stats);
     if (c->d_err) cudaFree(c->d_err);
     if (c->d_tmax) cudaFree(c->d_tmax);
+    if (c->d_opt_ns) cudaFree(c->d_opt_ns);
     if (c->ev0) cudaEventDestroy(c->ev0);
     if (c->ev1) cudaEventDestroy(c->ev1);
     if (c->stream) cudaStreamDestroy(c->stream);
@@ -360,6 +372,16 @@ aop_status aop_linear_advance_device(aop_ctx *c, int method, int nw, const doubl
     CK(run_linear_advance(method, nw, w, count, W, h, d_in, d_out, tw, c->tw_log2, c->ws, c->ws_size,
                           c->d_err, s));
     CK(cudaStreamSynchronize(s));
+    return AOP_OK;
+}
+
+aop_status aop_ctx_get_option_times(aop_ctx *c, int64_t n, int64_t *ns_out) {
+    if (!c || !ns_out || n < 0) return AOP_EINVAL;
+    if (!c->opt_ns_valid || n > c->last_n) return AOP_EINVAL;
+    CK(cudaSetDevice(c->device));
+    CK(cudaStreamSynchronize(c->stream));
+    CK(cudaDeviceSynchronize());
+    CK(cudaMemcpy(ns_out, c->d_opt_ns, (size_t)n * sizeof(int64_t), cudaMemcpyDeviceToHost));
     return AOP_OK;
 }
 

@@ -50,11 +50,13 @@ __host__ __device__ inline int64_t ex_index(const Params &P, int64_t row, int64_
     return col + P.T;
 }
 
-// e^{xbase + k' logu} from three 7-bit tables: e0 * t3[c] * t2[b] * t1[a] with
-// k' = a + 128 b + 16384 c.  Each table entry is one correctly rounded-ish exp,
-// so the product is within a few ulp of the exact node price.
+// e^{xbase + k' logu} from three 7-bit tables: t3[c] * t2[b] * t1[a] with
+// k' = a + 128 b + 16384 c, t3[c] = e^{xbase + 16384 c logu} (the base folded
+// into the coarse table so that no factor overflows when the node price itself
+// is representable: node prices reach e^{+-650} at T = 2^17 for sigma = 0.6 and
+// three years), t2[b] = e^{128 b logu}, t1[a] = e^{a logu}.  Each entry is one
+// exp, so the product is within a few ulp of the exact node price.
 struct ExpTables {
-    double e0;
     double t1[kExpTab], t2[kExpTab], t3[kExpTab];
 };
 
@@ -62,7 +64,7 @@ __device__ inline double exp_from_tables(const ExpTables &E, int64_t kp) {
     int a = (int)(kp & (kExpTab - 1));
     int b = (int)((kp >> kExpBits) & (kExpTab - 1));
     int c = (int)(kp >> (2 * kExpBits));
-    return E.e0 * E.t3[c] * E.t2[b] * E.t1[a];
+    return E.t3[c] * E.t2[b] * E.t1[a];
 }
 
 // Exercise value of the cell whose exponent index is kp.
@@ -74,17 +76,12 @@ __device__ inline double exercise(const Params &P, const ExpTables &E, int64_t k
 
 // Build the exponent tables cooperatively (all threads of the block call it).
 __device__ inline void build_exp_tables(const Params &P, ExpTables &E) {
-    for (int t = threadIdx.x; t < 3 * kExpTab + 1; t += blockDim.x) {
-        if (t == 3 * kExpTab) {
-            E.e0 = exp(P.xbase);
-        } else {
-            int tab = t / kExpTab, n = t % kExpTab;
-            double scale = (double)(1ll << (kExpBits * tab));
-            double v = exp((double)n * scale * P.logu);
-            if (tab == 0) E.t1[n] = v;
-            else if (tab == 1) E.t2[n] = v;
-            else E.t3[n] = v;
-        }
+    for (int t = threadIdx.x; t < 3 * kExpTab; t += blockDim.x) {
+        int tab = t / kExpTab, n = t % kExpTab;
+        double scale = (double)(1ll << (kExpBits * tab));
+        if (tab == 0) E.t1[n] = exp((double)n * P.logu);
+        else if (tab == 1) E.t2[n] = exp((double)n * scale * P.logu);
+        else E.t3[n] = exp(P.xbase + (double)n * scale * P.logu);
     }
 }
 

@@ -70,6 +70,7 @@ struct DncArgs {
     int *queue;
     int *err;
     aop_stats *stats;
+    int64_t *opt_ns;       // per-option device time (nullable)
 };
 
 // a row segment in memory: the value of column x lives at p[x - base]
@@ -154,7 +155,10 @@ struct Dnc {
                 im = (w2 - w0) * s1;
                 dl = 4.0 * ((w0 * w1 + w1 * w2) * sh * sh + w0 * w2 * s1 * s1) * inv2;
             }
-            double lm = gd * (lws + 0.5 * log1p(-dl));
+            // 1 - |s/s(0)|^2 lies in [0, 1]; rounding can step outside when
+            // |s(pi)| vanishes (e.g. p = 1/2), where the power is zero anyway
+            dl = fmin(fmax(dl, 0.0), 1.0);
+            double lm = (dl >= 1.0) ? -INFINITY : gd * (lws + 0.5 * log1p(-dl));
             double ph = gd * atan2(im, re);
             // reduce the phase to [-pi, pi] in units of pi
             double phpi = ph * 0.3183098861837907;
@@ -762,12 +766,18 @@ __global__ void __launch_bounds__(kThreadsD) dnc_kernel(const __grid_constant__ 
         }
         build_exp_tables(sP, E);
         __syncthreads();
+        uint64_t t_start = 0;
+        if (threadIdx.x == 0 && a.opt_ns) asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t_start));
         int32_t *bnd = a.bnd ? a.bnd + a.bnd_off[o] : nullptr;
         Dnc<MODE> d(a, sP, E, sm, slot, cache, &ncache, &arena_used, bnd, cnt);
         double price = (sP.model == AOP_BSM_PUT) ? d.price_put() : d.price_call();
         if (threadIdx.x == 0) {
             a.prices[o] = price;
-            cnt.convs += 0;
+            if (a.opt_ns) {
+                uint64_t t_end;
+                asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t_end));
+                a.opt_ns[o] = (int64_t)(t_end - t_start);
+            }
         }
         __syncthreads();
     }
@@ -846,7 +856,7 @@ size_t dnc_workspace_bytes(int method, int64_t n, int64_t T_max, int base_case, 
 cudaError_t run_dnc(int method, int64_t n, const Params *d_params, int64_t T_max, int base_case,
                     void *ws, size_t ws_bytes, const void *d_tw, int tw_log2, double *d_prices,
                     int32_t *d_status, int32_t *d_bnd, const int64_t *d_bnd_off,
-                    aop_stats *d_stats, int *d_err, int device, cudaStream_t s)
+                    aop_stats *d_stats, int *d_err, int64_t *d_opt_ns, int device, cudaStream_t s)
 {
     if (n == 0) return cudaSuccess;
     Layout L = make_layout(method, T_max, base_case);
@@ -884,6 +894,7 @@ cudaError_t run_dnc(int method, int64_t n, const Params *d_params, int64_t T_max
     a.queue = queue;
     a.err = d_err;
     a.stats = d_stats;
+    a.opt_ns = d_opt_ns;
     const size_t smem = (size_t)((method == AOP_FFT_FP64) ? 16 : 8) << L.lg_nsmem;
     if (method == AOP_FFT_FP64) {
         cudaFuncSetAttribute(dnc_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

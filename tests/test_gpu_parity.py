@@ -94,6 +94,26 @@ def test_configs_mid_size(ctx, method, T):
 
 
 @pytest.mark.parametrize("method", METHODS, ids=[MNAME[m] for m in METHODS])
+def test_extreme_parameters(ctx, method):
+    """Corners of the benchmark parameter box at T = 8192: the widest lattices
+    (sigma = 0.6, three years, node prices near e^{+-200}) and the most skewed
+    probabilities (sigma = 0.1, r = 0.08)."""
+    T = 8192
+    cases = [
+        wl.Request(0, 150.0, 50.0, 0.08, 0.005, 0.6, 3.0, T),
+        wl.Request(1, 150.0, 50.0, 0.08, 0.005, 0.6, 3.0, T, math.sqrt(3)),
+        wl.Request(1, 50.0, 150.0, 0.0, 0.06, 0.6, 3.0, T, math.sqrt(3)),
+        wl.Request(0, 100.0, 100.0, 0.08, 0.005, 0.1, 0.1, T),
+        wl.Request(1, 100.0, 100.0, 0.08, 0.005, 0.1, 3.0, T, 0.0, 1),
+        wl.Request(2, 50.0, 150.0, 0.08, 0.0, 0.6, 3.0, T),
+        wl.Request(2, 150.0, 50.0, 0.08, 0.0, 0.1, 3.0, T),
+        wl.Request(2, 100.0, 100.0, 0.001, 0.0, 0.6, 0.1, T),
+    ]
+    for r in cases:
+        _check(r, method)
+
+
+@pytest.mark.parametrize("method", METHODS, ids=[MNAME[m] for m in METHODS])
 def test_batch_matches_single(ctx, method):
     reqs = wl.random_small(24, seed=5, T_range=(16, 900))
     prices, status = ctx.price_batch(reqs, method=method)
