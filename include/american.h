@@ -182,6 +182,32 @@ aop_status aop_linear_advance_device(aop_ctx *ctx, int method, int nw, const dou
  * (synchronizes the context's stream). */
 aop_status aop_ctx_get_stats(aop_ctx *ctx, aop_stats *out);
 
+/* Allocation-free variant of aop_linear_advance_device (the paper has no
+ * counterpart; this is a deployment convenience).
+ *
+ * For callers that cannot allocate device memory when they call in: a serving
+ * thread held to a fixed memory budget, a host application whose own allocator
+ * owns the device memory, code that must not take the implicit device-wide
+ * synchronisation of cudaMalloc/cudaFree.  It needs no context: its scratch
+ * space (FFT work area, kernel-power band, twiddle tables) is one file-scope
+ * device array of 6.8 MB (6.5 MiB) that every GPU loading the library keeps until
+ * the process exits.  Inputs and outputs are the caller's device buffers, with
+ * the same layout and meaning as in aop_linear_advance_device; the call is
+ * asynchronous on `stream` (NULL = the legacy default stream) on the current
+ * device.
+ *
+ * Limits: 2 <= W <= AOP_NOALLOC_MAX_W, otherwise AOP_EINVAL (use
+ * aop_linear_advance_device for wider segments).  The first call on a device
+ * looks up the array's device address and fills its twiddle tables, and waits
+ * for that on `stream`; make that first call before any stream capture.  All
+ * calls share the one array: calls whose kernels overlap on the GPU (other
+ * streams, other host threads) race and must be serialised by the caller.
+ * Nothing is allocated or freed by this call. */
+#define AOP_NOALLOC_MAX_W 16384
+aop_status aop_linear_advance_noalloc(int method, int nw, const double *w, int64_t count,
+                                      int64_t W, int64_t h, const double *d_in, double *d_out,
+                                      void *stream);
+
 /* Per-option device time (ns, from the first to the last instruction the
  * pricing kernel spent on the option) of the last D&C batch that was run with
  * AOP_FLAG_OPTION_TIMES; ns_out is a host array of n <= batch size entries.

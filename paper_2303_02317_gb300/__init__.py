@@ -93,6 +93,9 @@ def load(path: Optional[str] = None):
                                                   i64, vp, vp, vp]
         lib.aop_ctx_get_stats.argtypes = [vp, ctypes.POINTER(_Stats)]
         lib.aop_ctx_get_option_times.argtypes = [vp, i64, vp]
+        lib.aop_linear_advance_noalloc.argtypes = [ctypes.c_int, ctypes.c_int, vp, i64, i64, i64,
+                                                   vp, vp, vp]
+        lib.aop_linear_advance_noalloc.restype = ctypes.c_int
         for f in ("aop_ctx_get_option_times", "aop_ctx_create", "aop_ctx_destroy", "price_american", "price_american_ex",
                   "price_american_batch", "price_american_batch_device",
                   "aop_linear_advance_device", "aop_ctx_get_stats"):
@@ -161,6 +164,24 @@ def price_american_ex(req, method: int = FFT_FP64, base_case: int = 0, boundary:
                                     b.ctypes.data if b is not None else None)
     _check(code, "price_american_ex")
     return (out.value, b) if boundary else out.value
+
+
+NOALLOC_MAX_W = 16384
+
+
+def linear_advance_noalloc(method: int, w: Sequence[float], count: int, W: int, h: int,
+                           d_in: int, d_out: int, stream: int = 0):
+    """C: aop_linear_advance_noalloc -- the linear advance without a context
+    and without any device allocation at call time, for callers that cannot
+    allocate (fixed memory budget, foreign allocator owning the device memory,
+    no implicit synchronisation allowed).  Its scratch is one static device
+    array shared by every call: overlapping calls race.  W <= NOALLOC_MAX_W.
+    Asynchronous on `stream` (0 = the legacy default stream)."""
+    wa = (ctypes.c_double * 3)(*(list(w) + [0.0] * (3 - len(w))))
+    _check(load().aop_linear_advance_noalloc(int(method), len(w), wa, int(count), int(W), int(h),
+                                             ctypes.c_void_p(d_in), ctypes.c_void_p(d_out),
+                                             ctypes.c_void_p(stream) if stream else None),
+           "aop_linear_advance_noalloc")
 
 
 class Context:

@@ -29,6 +29,8 @@
 // on the band where |s|^h exceeds 2^-60 of its peak and cached.
 #include <algorithm>
 #include <cstdio>
+#include <cstring>
+#include <mutex>
 
 #include "common.cuh"
 #include "fft.cuh"
@@ -983,4 +985,105 @@ cudaError_t run_linear_advance(int method, int nw, const double *w, int64_t coun
     return cudaGetLastError();
 }
 
+// ----------------------------------------------- allocation-free linear advance
+// For callers that must not allocate device memory at call time (a serving
+// thread that runs under a fixed memory budget, an embedding host whose
+// allocator owns all device memory, code that cannot afford the implicit
+// synchronisation of cudaMalloc/cudaFree).  The scratch space of the linear
+// advance lives in one file-scope device array instead of a context
+// workspace.  Every GPU that loads the library holds this array until the
+// process exits.
+namespace {
+
+constexpr int64_t kNoAllocMaxW = AOP_NOALLOC_MAX_W;     // widest segment accepted
+constexpr int64_t kNoAllocNmax = AOP_NOALLOC_MAX_W;     // largest transform length
+constexpr int kNoAllocCtas = 16;
+constexpr int kNoAllocTwLog2 = 15;                      // twiddles for N <= 2^15
+constexpr int64_t kNoAllocSpec = kNoAllocNmax / 2 + 2;  // one kernel power per call
+constexpr int64_t kNoAllocStride = kNoAllocNmax * 16 + kNoAllocSpec * 16;   // FP64 worst case
+constexpr int64_t kNoAllocTwEntries = (int64_t)1 << (kNoAllocTwLog2 - 1);
+constexpr int64_t kNoAllocTw32Off = kNoAllocCtas * kNoAllocStride;
+constexpr int64_t kNoAllocTw64Off = kNoAllocTw32Off + kNoAllocTwEntries * 16;
+constexpr int64_t kNoAllocBytes = kNoAllocTw64Off + kNoAllocTwEntries * 16;
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
+
+// device address of the array, looked up once per device (host code may not
+// use the array's name as a device pointer)
+struct NoAllocDevice {
+    bool ready;
+    char *base;
+};
+std::mutex g_noalloc_mu;
+NoAllocDevice g_noalloc_dev[64];
+
+}  // namespace
+
 }  // namespace aop
+
+extern "C" aop_status aop_linear_advance_noalloc(int method, int nw, const double *w, int64_t count,
+                                                 int64_t W, int64_t h, const double *d_in, double *d_out,
+                                                 void *stream)
+{
+    using namespace aop;
+    if (!w || (count > 0 && (!d_in || !d_out))) return AOP_EINVAL;
+    if (method != AOP_FFT_FP64 && method != AOP_FFT_FP32SPLIT) return AOP_EINVAL;
+    if (nw < 2 || nw > 3 || h < 1 || count < 0 || W < 2 || W > kNoAllocMaxW ||
+        (int64_t)(nw - 1) * h >= W)
+        return AOP_EINVAL;
+    if (count == 0) return AOP_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) { cudaGetLastError(); return AOP_ECUDA; }
+    char *base = nullptr;
+    {
+        std::lock_guard<std::mutex> lk(g_noalloc_mu);
+        NoAllocDevice &D = g_noalloc_dev[dev];
+        if (!D.ready) {
+            // one-time set-up on this device: find the array and fill the
+            // twiddle tables it holds (nothing is allocated)
+            void *ptr = nullptr;
+            cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+            if (e != cudaSuccess || !ptr) { cudaGetLastError(); return AOP_ECUDA; }
+            char *b = (char *)ptr;
+            e = launch_twiddles(kNoAllocTwLog2, b + kNoAllocTw32Off, b + kNoAllocTw64Off, s);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+            if (e != cudaSuccess) { cudaGetLastError(); return AOP_ECUDA; }
+            D.base = b;
+            D.ready = true;
+        }
+        base = D.base;
+    }
+    Params P;
+    memset(&P, 0, sizeof(P));
+    P.model = AOP_BINOMIAL_CALL;
+    P.nw = nw;
+    P.D = nw - 1;
+    P.o_min = 0;
+    P.w[0] = w[0]; P.w[1] = w[1]; P.w[2] = nw == 3 ? w[2] : 0.0;
+    P.wsum = P.w[0] + P.w[1] + P.w[2];
+    DncArgs a;
+    memset(&a, 0, sizeof(a));
+    a.B = 16;
+    a.lg_nsmem = (method == AOP_FFT_FP64) ? 11 : 12;
+    a.W_max = kNoAllocMaxW;
+    a.ws = base;
+    a.ws_stride = kNoAllocStride;
+    a.off_scr = 0;
+    a.off_spec = kNoAllocNmax * 16;
+    a.spec_cap = kNoAllocSpec;
+    a.tw = base + ((method == AOP_FFT_FP64) ? kNoAllocTw64Off : kNoAllocTw32Off);
+    a.tw_log2 = kNoAllocTwLog2;
+    a.err = nullptr;
+    const int64_t grid = std::min<int64_t>(count, kNoAllocCtas);
+    const size_t smem = (size_t)((method == AOP_FFT_FP64) ? 16 : 8) << a.lg_nsmem;
+    if (method == AOP_FFT_FP64) {
+        cudaFuncSetAttribute(advance_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        advance_kernel<0><<<(unsigned)grid, kThreadsD, smem, s>>>(a, P, count, W, h, d_in, d_out);
+    } else {
+        cudaFuncSetAttribute(advance_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        advance_kernel<1><<<(unsigned)grid, kThreadsD, smem, s>>>(a, P, count, W, h, d_in, d_out);
+    }
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? AOP_OK : AOP_ECUDA;
+}
