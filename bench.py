@@ -166,7 +166,7 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--method", default="fft32", choices=["fft32", "fft64"])
+    ap.add_argument("--method", default="fft32", choices=["fft32", "fft64", "df32"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--stencil-sample", type=int, default=4)
     ap.add_argument("--small", action="store_true",
@@ -188,7 +188,7 @@ def main():
         dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    method = aop.FFT_FP32SPLIT if args.method == "fft32" else aop.FFT_FP64
+    method = {"fft32": aop.FFT_FP32SPLIT, "fft64": aop.FFT_FP64, "df32": aop.FFT_DF32}[args.method]
 
     global T_BENCH, N_BINOMIAL, N_TRINOMIAL, WORKLOAD
     if args.small:
@@ -337,7 +337,7 @@ def main():
                              "max": float(opt_ms.max()), "mean": float(opt_ms.mean()),
                              "what": "per-option time inside the pricing kernel, all options of a step in flight together"},
         "vs_baseline": None,
-        "dtype": "f32split+f64" if method == aop.FFT_FP32SPLIT else "f64",
+        "dtype": {aop.FFT_FP32SPLIT: "f32split+f64", aop.FFT_DF32: "f32x2+f64"}.get(method, "f64"),
         "data": "synthetic",
         "config": {"workload": WORKLOAD, "T": T_BENCH, "options_per_step": n,
                    "method": args.method, "l2": "512 MB buffer written between timed steps",

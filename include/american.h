@@ -62,9 +62,13 @@ typedef enum {
     AOP_FFT_FP32SPLIT = 1,  /* trapezoidal D&C, FFT convolutions in FP32 on
                                hi/lo split inputs with hi/lo twiddles; base
                                cases, boundary tests and root in FP64 */
-    AOP_STENCIL_FP64 = 2    /* plain Theta(T^2) backward induction (Fig. 1 loop
+    AOP_STENCIL_FP64 = 2,   /* plain Theta(T^2) backward induction (Fig. 1 loop
                                and its trinomial / finite-difference analogues),
                                temporally blocked, FP64 */
+    AOP_FFT_DF32 = 3        /* trapezoidal D&C, FFT convolutions in double-float
+                               arithmetic (pairs of FP32 numbers, ~48-bit
+                               significands, on the FP32 pipe); base cases,
+                               boundary tests and root in FP64 */
 } aop_method;
 
 typedef enum {
@@ -114,6 +118,16 @@ typedef struct aop_stats {
     int64_t global_fft_bytes;   /* bytes moved by multi-pass (global) FFT passes */
     double kernel_ms;           /* CUDA-event time of the pricing kernel(s) of the
                                    last batch, measured on their launch stream */
+    int64_t walker_wait_ns;     /* D&C: time the recursion warps spent waiting for
+                                   linear advances, summed over options */
+    int64_t worker_busy_ns;     /* D&C: time the worker warps spent in linear
+                                   advances, summed over warps */
+    int64_t walker_base_ns;     /* D&C: time the recursion warps spent in the
+                                   naive base cases, summed over options */
+    int64_t basecase_calls;     /* D&C: naive base cases run */
+    int64_t basecase_rows;      /* D&C: rows stepped by the naive base cases */
+    int64_t walker_ns;          /* D&C: time from the first recursion step to the
+                                   root price, summed over options */
 } aop_stats;
 
 typedef struct aop_ctx aop_ctx;

@@ -26,7 +26,7 @@ LIB_PATH = os.path.join(HERE, "libamerican.so")
 HEADER = os.path.join(os.path.dirname(HERE), "include", "american.h")
 
 BINOMIAL_CALL, TRINOMIAL_CALL, BSM_PUT = 0, 1, 2
-FFT_FP64, FFT_FP32SPLIT, STENCIL_FP64 = 0, 1, 2
+FFT_FP64, FFT_FP32SPLIT, STENCIL_FP64, FFT_DF32 = 0, 1, 2, 3
 TRI_BOYLE, TRI_PAPER = 0, 1
 BOUNDARY_NONE_PUT = -(2 ** 31)
 MAX_T = 1 << 20
@@ -55,7 +55,10 @@ class _Options(ctypes.Structure):
 class _Stats(ctypes.Structure):
     _fields_ = [(n, ctypes.c_int64) for n in (
         "options", "convolutions", "fft_points", "fft_flops", "conv_inputs", "conv_outputs",
-        "basecase_cells", "stencil_cells", "global_fft_bytes")] + [("kernel_ms", ctypes.c_double)]
+        "basecase_cells", "stencil_cells", "global_fft_bytes")] + [("kernel_ms", ctypes.c_double)] + [
+        ("walker_wait_ns", ctypes.c_int64), ("worker_busy_ns", ctypes.c_int64),
+        ("walker_base_ns", ctypes.c_int64), ("basecase_calls", ctypes.c_int64),
+        ("basecase_rows", ctypes.c_int64), ("walker_ns", ctypes.c_int64)]
 
 
 _lock = threading.Lock()

@@ -104,7 +104,7 @@ aop_status run_batch(aop_ctx *c, int64_t n, const aop_request *d_reqs, const aop
                      const int64_t *d_bnd_off, cudaStream_t s, Params *d_params)
 {
     const int method = opt ? opt->method : AOP_FFT_FP64;
-    if (method < 0 || method > 2) return AOP_EINVAL;
+    if (method < 0 || method > 3) return AOP_EINVAL;
     if (n == 0 || T_max < 1) return AOP_OK;
     const int B = resolve_base_case(opt);
     CK(cudaMemsetAsync(c->d_stats, 0, sizeof(aop_stats), s));
@@ -355,7 +355,7 @@ aop_status price_american(int model, double S0, double K, double r, double q, do
 aop_status aop_linear_advance_device(aop_ctx *c, int method, int nw, const double *w, int64_t count,
                                      int64_t W, int64_t h, const double *d_in, double *d_out, void *stream) {
     if (!c || !w || !d_in || !d_out) return AOP_EINVAL;
-    if (method != AOP_FFT_FP64 && method != AOP_FFT_FP32SPLIT) return AOP_EINVAL;
+    if (method != AOP_FFT_FP64 && method != AOP_FFT_FP32SPLIT && method != AOP_FFT_DF32) return AOP_EINVAL;
     if (nw < 2 || nw > 3 || h < 1 || count < 0 || W > ((int64_t)1 << 20) || (int64_t)(nw - 1) * h >= W)
         return AOP_EINVAL;
     if (count == 0) return AOP_OK;

@@ -1,7 +1,7 @@
 // dnc.cu -- the trapezoidal divide-and-conquer pricer (hot-path rows a2-a7).
 //
 // One CTA prices one option at a time (persistent grid over a device queue of
-// options).  Its threads walk the recursion with an explicit stack:
+// options).  The recursion:
 //
 //   calls (binomial Sec. 3.3, trinomial appendix "Algorithm for American call
 //   option pricing under TOPM"): a row's red cells are the columns [c0, b]
@@ -23,10 +23,15 @@
 //   and evaluates the green cells left of it in closed form.  The triangle is a
 //   chain of trapezoids of halving height.
 //
-// Warp 0 runs the FP64 base cases and the value-versus-payoff tests; all
-// warps run the FFT convolutions (fft.cuh).  The kernel power s(theta)^h of
-// every (height, transform length) pair is evaluated once per option in FP64
-// on the band where |s|^h exceeds 2^-60 of its peak and cached.
+// Execution inside the CTA follows the paper's observation that each FFT
+// advance can run in parallel with the recursion beside it (proof of Thm 2.8):
+// warp 0 (the walker) runs the recursion and the FP64 base cases and posts
+// every linear advance as a task in a per-depth slot; warps 1..3 (workers)
+// execute the tasks (warp-level FFT convolutions) while the walker continues
+// down the sub-trapezoid, and the walker waits for a task only when its
+// output is needed.  The kernel power s(theta)^h of every (height, transform
+// length) pair is evaluated once per option in FP64 on the band where |s|^h
+// exceeds 2^-60 of its peak and cached.
 #include <algorithm>
 #include <cstdio>
 #include <cstring>
@@ -40,27 +45,67 @@ namespace aop {
 
 namespace {
 
-constexpr int kThreadsD = 128;
-constexpr int kSpecSlots = 64;
-constexpr int kLeftoverCall = 64;   // rows solved naively at the root
+constexpr int kWarps = 4;                  // walker + 3 workers
+constexpr int kThreadsD = 32 * kWarps;
+constexpr int kWorkers = kWarps - 1;
+constexpr int kBigWorkers = 2;             // workers 1, 2 may take multi-pass transforms
+constexpr int kSpecSlots = 128;
+constexpr int kLeftoverCall = 64;          // rows solved naively at the root
+constexpr int kNaiveCap = 512;             // doubles per walker row buffer
+constexpr uint64_t kWaitNs = 30ull * 1000000000ull;   // bound of every spin-wait (30 s)
+
+__device__ __forceinline__ uint64_t gtime() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+enum { TASK_FREE = 0, TASK_POSTED = 1, TASK_CLAIMED = 2, TASK_DONE = 3 };
+enum { SPEC_BUILDING = 1, SPEC_READY = 2 };
 
 struct SpecEntry {
-    int32_t g;       // height (steps)
-    int32_t lgN;     // transform length
-    int32_t mc;      // band: bins 0..mc stored
-    int32_t pad;
-    int64_t off;     // entry offset in the arena
+    int32_t g;
+    int32_t lgN;
+    int32_t mc;
+    volatile int32_t state;
+    int64_t off;
+};
+
+// a row segment in memory: the value of column x lives at p[x - base]
+struct Buf {
+    double *p;
+    int64_t base;
+};
+
+// Row values as the pricer stores them (FP64 in mode 0, FP32 pairs hi + lo
+// otherwise), read and written in FP64 by the base cases and first rows.
+template <int MODE>
+__device__ __forceinline__ double cell_ld(const Buf &b, int64_t x) {
+    return fft::cell_value(((const typename fft::CellT<MODE>::T *)b.p)[x - b.base]);
+}
+template <int MODE>
+__device__ __forceinline__ void cell_st(const Buf &b, int64_t x, double v) {
+    ((typename fft::CellT<MODE>::T *)b.p)[x - b.base] = fft::make_cell<MODE>(v);
+}
+
+struct Task {
+    Buf in, out;
+    int64_t x_lo, x_hi, g;
+    int32_t lgN;
+    volatile int32_t state;
 };
 
 struct DncArgs {
     const Params *params;
     int64_t n;
     int B;                 // base-case height (power of two)
-    int lg_nsmem;          // log2 of the shared-memory FFT capacity
+    int lg_tile;           // log2 of a worker's shared-memory transform tile
+    int lg_block;          // log2 of the block-level tile (linear advance entry points)
     int64_t W_max;         // widest row (doubles)
     char *ws;
     int64_t ws_stride;     // bytes per CTA
     int64_t off_r0, off_mid, off_scr, off_spec;   // byte offsets inside a CTA slot
+    int64_t scr_stride;    // bytes of global transform scratch per worker
     int64_t mid_off[kMaxDepth];                   // doubles, relative to off_mid
     int64_t spec_cap;      // arena entries
     const void *tw;
@@ -70,343 +115,536 @@ struct DncArgs {
     int32_t *bnd;
     const int64_t *bnd_off;
     int *queue;
+    int *sm_slots;         // per-SM arrival counters (1024 ints, zeroed per launch)
     int *err;
     aop_stats *stats;
     int64_t *opt_ns;       // per-option device time (nullable)
 };
 
-// a row segment in memory: the value of column x lives at p[x - base]
-struct Buf {
-    double *p;
-    int64_t base;
-    __device__ double &at(int64_t x) const { return p[x - base]; }
+struct Counters {
+    long long convs, fft_points, fft_flops, conv_in, conv_out, base_cells, gbytes, wait_ns, busy_ns, base_ns;
+    long long base_calls, base_rows, walker_ns;
 };
 
-struct Counters {
-    long long convs, fft_points, fft_flops, conv_in, conv_out, base_cells, gbytes;
+// Per-CTA shared state (static shared memory).
+struct Shared {
+    ExpTables E;
+    Params P;
+    Task tasks[kMaxDepth];
+    SpecEntry spec[kSpecSlots];
+    int spec_n;
+    int spec_lock;
+    long long arena_used;
+    int opt;
+    volatile int done;
+    volatile int err;
+    int bcast_i;
+    long long bcast_l;
+    double price;
 };
+
+// ---------------------------------------------------------------- groups
+template <class G> __device__ __forceinline__ int bcast_int(Shared &S, int v);
+template <> __device__ __forceinline__ int bcast_int<fft::WarpGroup>(Shared &, int v) {
+    return __shfl_sync(0xffffffffu, v, 0);
+}
+template <> __device__ __forceinline__ int bcast_int<fft::BlockGroup>(Shared &S, int v) {
+    if (threadIdx.x == 0) S.bcast_i = v;
+    __syncthreads();
+    int r = S.bcast_i;
+    __syncthreads();
+    return r;
+}
+template <class G> __device__ __forceinline__ bool leader() { return G::rank() == 0; }
+
+// ------------------------------------------------------------ kernel power
+__device__ int band_mc(const Params &P, int64_t g, int64_t N) {
+    const double w0 = P.w[0], w1 = P.w[1], w2 = P.w[2];
+    double kap = 4.0 * (w0 * w1 + (P.nw == 3 ? w1 * w2 : 0.0)) / (P.wsum * P.wsum);
+    double need = 83.2 / ((double)g * kap);
+    if (!(kap > 0) || need >= 1.0) return (int)(N / 2);
+    double th2 = asin(sqrt(need));               // theta_c / 2
+    double mc = (double)N * th2 / 3.141592653589793 + 2.0;
+    return (int)min((double)(N / 2), ceil(mc));
+}
+
+// s(theta_m)^g in FP64: magnitude through log1p of the exactly formed
+// 1 - |s/s(0)|^2, phase g * arg s reduced in units of pi.
+__device__ double2 bin_value(const Params &P, int64_t g, int lgN, int64_t m) {
+    const double N = (double)((int64_t)1 << lgN);
+    const double w0 = P.w[0], w1 = P.w[1], w2 = P.w[2];
+    const double inv2 = 1.0 / (P.wsum * P.wsum);
+    const double gd = (double)g;
+    double sh, ch;
+    sincospi((double)m / N, &sh, &ch);
+    const double s1 = 2.0 * sh * ch, c1 = 1.0 - 2.0 * sh * sh;
+    double re, im, dl;
+    if (P.nw == 2) {
+        re = w0 + w1 * c1;
+        im = w1 * s1;
+        dl = 4.0 * w0 * w1 * sh * sh * inv2;
+    } else if (P.o_min == 0) {
+        const double s2 = 2.0 * s1 * c1, c2 = 1.0 - 2.0 * s1 * s1;
+        re = w0 + w1 * c1 + w2 * c2;
+        im = w1 * s1 + w2 * s2;
+        dl = 4.0 * ((w0 * w1 + w1 * w2) * sh * sh + w0 * w2 * s1 * s1) * inv2;
+    } else {
+        re = w1 + (w0 + w2) * c1;
+        im = (w2 - w0) * s1;
+        dl = 4.0 * ((w0 * w1 + w1 * w2) * sh * sh + w0 * w2 * s1 * s1) * inv2;
+    }
+    // 1 - |s/s(0)|^2 lies in [0, 1]; rounding can step outside when |s(pi)|
+    // vanishes (e.g. p = 1/2), where the power is zero anyway
+    dl = fmin(fmax(dl, 0.0), 1.0);
+    double lm = (dl >= 1.0) ? -INFINITY : gd * (log(P.wsum) + 0.5 * log1p(-dl));
+    double ph = gd * atan2(im, re);
+    double phpi = ph * 0.3183098861837907;
+    phpi -= 2.0 * rint(0.5 * phpi);
+    double sp, cp;
+    sincospi(phpi, &sp, &cp);
+    double mag = (lm < -745.0) ? 0.0 : exp(lm);
+    return make_double2(mag * cp, mag * sp);
+}
 
 template <int MODE>
-struct Dnc {
+__device__ __forceinline__ typename fft::Cx<MODE>::Sp pack_spec(double2 v) {
+    if constexpr (MODE == 0) {
+        return v;
+    } else {
+        float hr = (float)v.x, hi = (float)v.y;
+        return make_float4(hr, hi, (float)(v.x - (double)hr), (float)(v.y - (double)hi));
+    }
+}
+
+// ------------------------------------------------------- storage policies
+// How a linear advance reads its input and writes its output:
+//   StoreF64  -- plain FP64 arrays (the linear-advance entry points);
+//   StoreCell -- the pricer's row buffers (FP64 in mode 0, FP32 pairs else),
+//                read and written without FP64 arithmetic in modes 1 and 2.
+template <int MODE>
+struct StoreF64 {
+    using T = double;
+    using V = typename fft::Cx<MODE>::V;
+    static constexpr bool kIdentity = false;
+    __device__ static V to_v(double d) { return fft::load_split<MODE>(d); }
+    __device__ static double from_v(V v, double invN) { return fft::unsplit(v, invN); }
+};
+template <int MODE>
+struct StoreCell {
+    using T = typename fft::CellT<MODE>::T;
+    using V = typename fft::Cx<MODE>::V;
+    static constexpr bool kIdentity = (MODE == 1);
+    __device__ static V to_v(T c) {
+        if constexpr (MODE == 0) return fft::cell_to_v(c);
+        else if constexpr (MODE == 1) return fft::cell_to_v1(c);
+        else return fft::cell_to_v2(c);
+    }
+    __device__ static T from_v(V v, double invN) { return fft::v_to_cell(v, invN); }
+};
+
+// ------------------------------------------------------------- per-CTA view
+template <int MODE>
+struct Cta {
     using V = typename fft::Cx<MODE>::V;
     using Tw = typename fft::Cx<MODE>::Tw;
     using Sp = typename fft::Cx<MODE>::Sp;
 
     const DncArgs &a;
-    const Params &P;
-    const ExpTables &E;
-    V *sm;                  // shared FFT buffer (N_smem values)
-    char *slot;             // this CTA's global workspace
-    SpecEntry *cache;       // shared
-    int *ncache;            // shared
-    int64_t *arena_used;    // shared
-    int32_t *bnd;           // divider output of this option (nullable)
-    Counters &cnt;
+    Shared &S;
+    char *slot;
 
-    __device__ Dnc(const DncArgs &a_, const Params &P_, const ExpTables &E_, V *sm_, char *slot_,
-                   SpecEntry *cache_, int *ncache_, int64_t *au, int32_t *bnd_, Counters &c)
-        : a(a_), P(P_), E(E_), sm(sm_), slot(slot_), cache(cache_), ncache(ncache_), arena_used(au),
-          bnd(bnd_), cnt(c) {}
+    __device__ Cta(const DncArgs &a_, Shared &S_, char *slot_) : a(a_), S(S_), slot(slot_) {}
 
-    __device__ double *mid(int d) const {
-        return (double *)(slot + a.off_mid) + a.mid_off[d];
-    }
-    __device__ V *scratch() const { return (V *)(slot + a.off_scr); }
+    __device__ const Params &P() const { return S.P; }
+    __device__ double *mid(int d) const { return (double *)(slot + a.off_mid) + a.mid_off[d]; }
+    __device__ V *scratch(int w) const { return (V *)(slot + a.off_scr + (int64_t)w * a.scr_stride); }
     __device__ Sp *arena() const { return (Sp *)(slot + a.off_spec); }
     __device__ const Tw *tw() const { return (const Tw *)a.tw; }
 
-    __device__ void record(int64_t row, int32_t v) const {
-        if (bnd) bnd[row] = v;
-    }
-
-    // ---------------------------------------------------------- kernel power
-    __device__ int band_mc(int64_t g, int64_t N) const {
-        const double w0 = P.w[0], w1 = P.w[1], w2 = P.w[2];
-        double kap = 4.0 * (w0 * w1 + (P.nw == 3 ? w1 * w2 : 0.0)) / (P.wsum * P.wsum);
-        double need = 83.2 / ((double)g * kap);
-        if (!(kap > 0) || need >= 1.0) return (int)(N / 2);
-        double th2 = asin(sqrt(need));               // theta_c / 2
-        double mc = (double)N * th2 / 3.141592653589793 + 2.0;
-        return (int)min((double)(N / 2), ceil(mc));
-    }
-
-    // s(theta_m)^g for m in [0, mc]: computed in FP64 (magnitude through
-    // log1p of the exactly formed 1 - |s/s(0)|^2, phase reduced in FP64).
-    __device__ void compute_spectrum(Sp *dst, int64_t g, int lgN, int mc) const {
-        const double N = (double)((int64_t)1 << lgN);
-        const double w0 = P.w[0], w1 = P.w[1], w2 = P.w[2];
-        const double lws = log(P.wsum);
-        const double inv2 = 1.0 / (P.wsum * P.wsum);
-        const double gd = (double)g;
-        for (int m = threadIdx.x; m <= mc; m += blockDim.x) {
-            double sh, ch;
-            sincospi((double)m / N, &sh, &ch);
-            const double s1 = 2.0 * sh * ch, c1 = 1.0 - 2.0 * sh * sh;
-            double re, im, dl;
-            if (P.nw == 2) {
-                re = w0 + w1 * c1;
-                im = w1 * s1;
-                dl = 4.0 * w0 * w1 * sh * sh * inv2;
-            } else if (P.o_min == 0) {
-                const double s2 = 2.0 * s1 * c1, c2 = 1.0 - 2.0 * s1 * s1;
-                re = w0 + w1 * c1 + w2 * c2;
-                im = w1 * s1 + w2 * s2;
-                dl = 4.0 * ((w0 * w1 + w1 * w2) * sh * sh + w0 * w2 * s1 * s1) * inv2;
-            } else {
-                re = w1 + (w0 + w2) * c1;
-                im = (w2 - w0) * s1;
-                dl = 4.0 * ((w0 * w1 + w1 * w2) * sh * sh + w0 * w2 * s1 * s1) * inv2;
-            }
-            // 1 - |s/s(0)|^2 lies in [0, 1]; rounding can step outside when
-            // |s(pi)| vanishes (e.g. p = 1/2), where the power is zero anyway
-            dl = fmin(fmax(dl, 0.0), 1.0);
-            double lm = (dl >= 1.0) ? -INFINITY : gd * (lws + 0.5 * log1p(-dl));
-            double ph = gd * atan2(im, re);
-            // reduce the phase to [-pi, pi] in units of pi
-            double phpi = ph * 0.3183098861837907;
-            phpi -= 2.0 * rint(0.5 * phpi);
-            double sp, cp;
-            sincospi(phpi, &sp, &cp);
-            double mag = (lm < -745.0) ? 0.0 : exp(lm);
-            double vr = mag * cp, vi = mag * sp;
-            if constexpr (MODE == 0) {
-                dst[m] = make_double2(vr, vi);
-            } else {
-                float hr = (float)vr, hi_ = (float)vi;
-                dst[m] = make_float4(hr, hi_, (float)(vr - (double)hr), (float)(vi - (double)hi_));
-            }
-        }
-    }
-
-    // Find or build the cached spectrum; returns (pointer, mc) through refs.
-    // Called by all threads (uniform); ends with a block barrier.
+    // Cached kernel power for (g, lgN); nullptr = evaluate bins on the fly
+    // (arena exhausted).  Called by every thread of the group G.
+    template <class G>
     __device__ const Sp *spectrum(int64_t g, int lgN, int &mc_out) {
-        __shared__ int s_idx;
-        __shared__ int s_build;
-        if (threadIdx.x == 0) {
-            int idx = -1;
-            for (int i = 0; i < *ncache; i++)
-                if (cache[i].g == (int32_t)g && cache[i].lgN == lgN) { idx = i; break; }
-            s_build = 0;
-            if (idx < 0) {
-                int mc = band_mc(g, (int64_t)1 << lgN);
-                if (*ncache >= kSpecSlots || *arena_used + mc + 1 > a.spec_cap) {
-                    *ncache = 0;           // evict everything
-                    *arena_used = 0;
-                }
-                idx = (*ncache)++;
-                cache[idx].g = (int32_t)g;
-                cache[idx].lgN = lgN;
-                cache[idx].mc = mc;
-                cache[idx].off = *arena_used;
-                *arena_used += mc + 1;
-                s_build = 1;
+        int idx = -1, build = 0;
+        if (leader<G>()) {
+            const uint64_t t0 = gtime();
+            while (atomicCAS(&S.spec_lock, 0, 1) != 0) {
+                __nanosleep(32);
+                if (gtime() - t0 > kWaitNs) { atomicCAS((int *)&S.err, 0, AOP_ETIMEOUT); break; }
             }
-            s_idx = idx;
+            for (int i = 0; i < S.spec_n; i++)
+                if (S.spec[i].g == (int32_t)g && S.spec[i].lgN == lgN) { idx = i; break; }
+            if (idx < 0) {
+                int mc = band_mc(P(), g, (int64_t)1 << lgN);
+                if (S.spec_n < kSpecSlots && S.arena_used + mc + 1 <= a.spec_cap) {
+                    idx = S.spec_n;
+                    S.spec[idx].g = (int32_t)g;
+                    S.spec[idx].lgN = lgN;
+                    S.spec[idx].mc = mc;
+                    S.spec[idx].off = S.arena_used;
+                    S.spec[idx].state = SPEC_BUILDING;
+                    S.arena_used += mc + 1;
+                    __threadfence_block();
+                    S.spec_n = idx + 1;
+                    build = 1;
+                } else {
+                    idx = -1 - mc;   // no room: evaluate on the fly
+                }
+            }
+            __threadfence_block();
+            atomicExch(&S.spec_lock, 0);
         }
-        __syncthreads();
-        const SpecEntry e = cache[s_idx];
+        idx = bcast_int<G>(S, idx);
+        build = bcast_int<G>(S, build);
+        if (idx < 0) {
+            mc_out = -1 - idx;
+            return nullptr;
+        }
+        SpecEntry &e = S.spec[idx];
         Sp *p = arena() + e.off;
-        if (s_build) {
-            compute_spectrum(p, g, lgN, e.mc);
+        if (build) {
+            for (int m = G::rank(); m <= e.mc; m += G::size()) p[m] = pack_spec<MODE>(bin_value(P(), g, lgN, m));
+            __threadfence_block();
+            G::sync();
+            if (leader<G>()) e.state = SPEC_READY;
+        } else if (leader<G>()) {
+            const uint64_t t0 = gtime();
+            while (e.state != SPEC_READY) {
+                __nanosleep(32);
+                if (gtime() - t0 > kWaitNs) { atomicCAS((int *)&S.err, 0, AOP_ETIMEOUT); break; }
+            }
             __threadfence_block();
         }
-        __syncthreads();
+        G::sync();
         mc_out = e.mc;
         return p;
     }
 
-    // ---------------------------------------------------------- conv helpers
-    __device__ static V load_split(double x) {
-        if constexpr (MODE == 0) {
-            return make_double2(x, 0.0);
+    // Fill tile[s] (s < count) with the stored input value at transform index
+    // e = idx(s) (zero past the window W), converted by the storage policy ST
+    // (8-byte stored values).  The values are staged with cp.async (all in
+    // flight at once; padding is zero-filled, not read) and converted in shared
+    // memory: in place for 8-byte transform values; for 16-byte values they are
+    // staged in the upper half of the tile and read into registers before any
+    // value is written.
+    template <class G, class ST, class IDX>
+    __device__ void stage_input(V *tile, int64_t count, IDX idx, const Buf &in, int64_t x_lo, int64_t W) {
+        using T = typename ST::T;
+        static_assert(sizeof(T) == 8, "stored values are 8 bytes");
+        constexpr int kPer = 16;     // values per thread: count <= 16 * group size
+        const T *src = (const T *)in.p - in.base;
+        if constexpr (sizeof(V) == 8) {
+            for (int64_t s = G::rank(); s < count; s += G::size()) {
+                const int64_t e = idx(s);
+                const bool ok = e < W;
+                fft::cp_async<8>(&tile[s], ok ? (const void *)&src[x_lo + e] : (const void *)in.p, ok ? 8 : 0);
+            }
+            fft::cp_async_wait();
+            if constexpr (!ST::kIdentity) {
+                for (int64_t s = G::rank(); s < count; s += G::size()) {
+                    const T d = *(const T *)&tile[s];
+                    tile[s] = ST::to_v(d);
+                }
+            }
         } else {
-            float hi = (float)x;
-            return make_float2(hi, (float)(x - (double)hi));
+            T *st = (T *)tile + count;
+            for (int64_t s = G::rank(); s < count; s += G::size()) {
+                const int64_t e = idx(s);
+                const bool ok = e < W;
+                fft::cp_async<8>(&st[s], ok ? (const void *)&src[x_lo + e] : (const void *)in.p, ok ? 8 : 0);
+            }
+            fft::cp_async_wait();
+            T r[kPer];
+#pragma unroll
+            for (int k = 0; k < kPer; k++) {
+                const int64_t s = G::rank() + (int64_t)k * G::size();
+                if (s < count) r[k] = st[s];
+            }
+            G::sync();
+#pragma unroll
+            for (int k = 0; k < kPer; k++) {
+                const int64_t s = G::rank() + (int64_t)k * G::size();
+                if (s < count) tile[s] = ST::to_v(r[k]);
+            }
         }
+        G::sync();
     }
-    __device__ static double unsplit(V v, double invN) {
-        if constexpr (MODE == 0) return v.x * invN;
-        else return ((double)v.x + (double)v.y) * invN;
+
+    template <class ST>
+    __device__ static void store(const Buf &out, int64_t y, typename ST::T v) {
+        ((typename ST::T *)out.p)[y - out.base] = v;
     }
-    __device__ static V spec_mul(V z, const Sp *sp, int mc, uint32_t m, uint32_t N) {
+
+    // tile[s] = scr[idx(s)] for s < count, through cp.async
+    template <class G, class IDX>
+    __device__ void stage_scratch(V *tile, int64_t count, IDX idx, const V *scr) {
+        for (int64_t s = G::rank(); s < count; s += G::size())
+            fft::cp_async<(int)sizeof(V)>(&tile[s], &scr[idx(s)], (int)sizeof(V));
+        fft::cp_async_wait();
+        G::sync();
+    }
+
+    __device__ V mul_bin(V z, const Sp *sp, int mc, uint32_t m, uint32_t N, int64_t g, int lgN) const {
+        if (sp) return fft::spec_mul<MODE>(z, sp, mc, m, N);
         uint32_t mm = (m <= N / 2) ? m : N - m;
-        if ((int)mm > mc) {
-            V zero;
-            zero.x = 0; zero.y = 0;
-            return zero;
-        }
-        Sp s = sp[mm];
+        if ((int)mm > mc) return fft::czero<V>();
+        Sp s = pack_spec<MODE>(bin_value(P(), g, lgN, mm));
         return (m <= N / 2) ? fft::twmul<false>(z, s) : fft::twmul<true>(z, s);
     }
 
-    // Linear advance: out[y] = sum_t c_t in[y + o_min g + t] for y in
-    // [x_lo - o_min g, x_hi - (o_min + nw - 1) g] (the window fully inside the
-    // input [x_lo, x_hi]).  All threads call it; ends with a barrier.
-    __device__ void conv(const Buf in, int64_t x_lo, int64_t x_hi, const Buf out, int64_t g) {
+    // One pass over global memory: the stages with half-sizes 2^s_lo .. 2^s_hi
+    // of an N-point transform, on tiles of (2^(s_hi-s_lo+1) elements x Q
+    // consecutive columns) staged in shared memory.  DIF = forward (stages top
+    // down); otherwise inverse.  The first forward pass reads (and splits) the
+    // FP64 input; the last inverse pass extracts the FP64 output.
+    template <class G, class ST, bool DIF>
+    __device__ void tile_pass(V *tile, int lg_tile, V *scr, int lgN, int s_lo, int s_hi, bool first, bool last,
+                              const Buf &in, int64_t x_lo, int64_t W, const Buf &out, int64_t y_lo, int64_t off,
+                              int64_t nout, double invN) {
+        const int L = s_hi - s_lo + 1;
+        const int64_t Gn = (int64_t)1 << L;
+        const int64_t lo_count = (int64_t)1 << s_lo;
+        const int64_t hi_count = ((int64_t)1 << lgN) >> (s_hi + 1);
+        const int64_t Q = min(lo_count, ((int64_t)1 << lg_tile) >> L);
+        const Tw *T = tw();
+        const int twl = a.tw_log2;
+        for (int64_t hb = 0; hb < hi_count; hb++) {
+            const int64_t hbase = hb << (s_hi + 1);
+            for (int64_t q0 = 0; q0 < lo_count; q0 += Q) {
+                auto idx = [=](int64_t s) {
+                    const int64_t t = s / Q, q = s - t * Q;
+                    return hbase + (t << s_lo) + q0 + q;
+                };
+                if (first) stage_input<G, ST>(tile, Gn * Q, idx, in, x_lo, W);
+                else stage_scratch<G>(tile, Gn * Q, idx, scr);
+                for (int step = 0; step < L; step++) {
+                    const int lm = DIF ? (L - 1 - step) : step;
+                    const int64_t m = (int64_t)1 << lm;
+                    const int lgM2 = lm + s_lo + 1;
+                    for (int64_t s = G::rank(); s < (Gn / 2) * Q; s += G::size()) {
+                        const int64_t pr = s / Q, q = s - pr * Q;
+                        const int64_t tm = pr & (m - 1);
+                        const int64_t t = ((pr - tm) << 1) + tm;
+                        const int64_t k = (tm << s_lo) + q0 + q;
+                        const Tw w = fft::tw_get<MODE>(T, twl, k, lgM2);
+                        V *pa = &tile[t * Q + q], *pb = &tile[(t + m) * Q + q];
+                        if (DIF) {
+                            V u = *pa, v = *pb;
+                            *pa = fft::cadd(u, v);
+                            *pb = fft::twmul<false>(fft::csub(u, v), w);
+                        } else {
+                            V u = *pa, v = fft::twmul<true>(*pb, w);
+                            *pa = fft::cadd(u, v);
+                            *pb = fft::csub(u, v);
+                        }
+                    }
+                    G::sync();
+                }
+                for (int64_t s = G::rank(); s < Gn * Q; s += G::size()) {
+                    const int64_t t = s / Q, q = s - t * Q;
+                    const int64_t e = hbase + (t << s_lo) + q0 + q;
+                    if (last) {
+                        const int64_t k = e - off;
+                        if (k >= 0 && k < nout) store<ST>(out, y_lo + k, ST::from_v(tile[s], invN));
+                    } else {
+                        scr[e] = tile[s];
+                    }
+                }
+                G::sync();
+            }
+        }
+    }
+
+    // Linear advance of `g` steps: out[y] = sum_t c_t in[y + o_min g + t] for y
+    // in [x_lo - o_min g, x_hi - (o_min + nw - 1) g].  The group G runs it on its
+    // shared tile (2^lg_tile values) and, for longer transforms, on its global
+    // scratch `scr`.
+    template <class G, class ST>
+    __device__ void conv(const Buf &in, int64_t x_lo, int64_t x_hi, const Buf &out, int64_t g, V *tile,
+                         int lg_tile, V *scr, Counters &cnt) {
+        const Params &Pp = P();
         const int64_t W = x_hi - x_lo + 1;
-        const int64_t span = (int64_t)(P.nw - 1) * g;
-        const int64_t y_lo = x_lo - (int64_t)P.o_min * g;
+        const int64_t span = (int64_t)(Pp.nw - 1) * g;
+        const int64_t y_lo = x_lo - (int64_t)Pp.o_min * g;
         const int64_t nout = W - span;
         if (nout <= 0) return;
         int lgN = ilog2_ceil(W);
         if (lgN < 2) lgN = 2;
         const int64_t N = (int64_t)1 << lgN;
         int mc;
-        const Sp *sp = spectrum(g, lgN, mc);
+        const Sp *sp = spectrum<G>(g, lgN, mc);
         const double invN = 1.0 / (double)N;
-        if (threadIdx.x == 0) {
+        const int64_t off = y_lo - x_lo;
+        if (leader<G>()) {
             cnt.convs++;
             cnt.fft_points += 2 * N;
             cnt.fft_flops += 2 * 5 * N * lgN;
             cnt.conv_in += W;
             cnt.conv_out += nout;
         }
-        if (lgN <= a.lg_nsmem) {
-            for (int64_t e = threadIdx.x; e < N; e += blockDim.x)
-                sm[e] = load_split(e < W ? in.at(x_lo + e) : 0.0);
-            __syncthreads();
-            fft::dif_range<MODE>(sm, N, lgN - 1, 0, tw(), a.tw_log2);
-            for (int64_t p = threadIdx.x; p < N; p += blockDim.x)
-                sm[p] = spec_mul(sm[p], sp, mc, fft::brev_n((uint32_t)p, lgN), (uint32_t)N);
-            __syncthreads();
-            fft::dit_range<MODE>(sm, N, 0, lgN - 1, tw(), a.tw_log2);
-            const int64_t off = y_lo - x_lo;   // output y sits at transform index y - x_lo
-            for (int64_t t = threadIdx.x; t < nout; t += blockDim.x)
-                out.at(y_lo + t) = unsplit(sm[off + t], invN);
-            __syncthreads();
-        } else {
-            conv_global(in, x_lo, W, out, y_lo, nout, lgN, sp, mc, invN);
-        }
-    }
-
-    // Three passes through global scratch for N > shared capacity:
-    //   A: the outer DIF stages (half-sizes N/2 .. N2) on the strided groups
-    //      {q + t N2}, loading (and splitting) the FP64 input;
-    //   B: per contiguous block of N2: inner DIF stages, kernel-power product,
-    //      inner DIT stages;
-    //   C: the outer DIT stages on the strided groups, then the extraction.
-    __device__ void conv_global(const Buf in, int64_t x_lo, int64_t W, const Buf out, int64_t y_lo,
-                                int64_t nout, int lgN, const Sp *sp, int mc, double invN) {
-        const int lg2 = a.lg_nsmem;          // block length N2
-        const int lg1 = lgN - lg2;           // number of blocks N1
-        const int64_t N = (int64_t)1 << lgN, N1 = (int64_t)1 << lg1, N2 = (int64_t)1 << lg2;
-        const int64_t Q = N2 >> lg1;         // columns per tile (>= 1)
-        V *scr = scratch();
         const Tw *T = tw();
         const int twl = a.tw_log2;
-        if (threadIdx.x == 0) cnt.gbytes += (int64_t)sizeof(V) * N * 4 + 8 * (W + nout);
-        // ---- pass A
-        for (int64_t q0 = 0; q0 < N2; q0 += Q) {
-            for (int64_t s = threadIdx.x; s < N1 * Q; s += blockDim.x) {
-                int64_t t = s / Q, q = s - t * Q;
-                int64_t e = q0 + q + t * N2;
-                sm[s] = load_split(e < W ? in.at(x_lo + e) : 0.0);
-            }
-            __syncthreads();
-            for (int lgm = lg1 - 1; lgm >= 0; lgm--) {      // t-space half size m
-                const int64_t m = (int64_t)1 << lgm;
-                const int lgM2 = lgm + lg2 + 1;               // 2M = 2 m N2
-                for (int64_t s = threadIdx.x; s < (N1 / 2) * Q; s += blockDim.x) {
-                    int64_t pr = s / Q, q = s - pr * Q;
-                    int64_t tm = pr & (m - 1);
-                    int64_t t = ((pr - tm) << 1) + tm;
-                    int64_t kk = q0 + q + tm * N2;            // e mod 2M
-                    V u = sm[t * Q + q], v = sm[(t + m) * Q + q];
-                    sm[t * Q + q] = fft::cadd(u, v);
-                    sm[(t + m) * Q + q] = fft::twmul<false>(fft::csub(u, v),
-                                                            fft::tw_get<MODE>(T, twl, kk, lgM2));
-                }
-                __syncthreads();
-            }
-            for (int64_t s = threadIdx.x; s < N1 * Q; s += blockDim.x) {
-                int64_t t = s / Q, q = s - t * Q;
-                scr[q0 + q + t * N2] = sm[s];
-            }
-            __syncthreads();
+        if (lgN <= lg_tile) {
+            stage_input<G, ST>(tile, N, [](int64_t s) { return s; }, in, x_lo, W);
+            fft::dif_range<MODE, G>(tile, N, lgN - 1, 0, T, twl);
+            for (int64_t p = G::rank(); p < N; p += G::size())
+                tile[p] = mul_bin(tile[p], sp, mc, fft::brev_n((uint32_t)p, lgN), (uint32_t)N, g, lgN);
+            G::sync();
+            fft::dit_range<MODE, G>(tile, N, 0, lgN - 1, T, twl);
+            for (int64_t t = G::rank(); t < nout; t += G::size()) store<ST>(out, y_lo + t, ST::from_v(tile[off + t], invN));
+            G::sync();
+            return;
         }
-        // ---- pass B
-        for (int64_t b = 0; b < N1; b++) {
+        if (leader<G>()) cnt.gbytes += (int64_t)sizeof(V) * N * 4 + 8 * (W + nout);
+        // outer stages lg_tile .. lgN-1 in chunks of at most lg_tile - 2 stages
+        // (so that a tile row spans >= 4 consecutive elements)
+        const int chunk = max(1, lg_tile - 2);
+        int nch = 0;
+        int ch_lo[16], ch_hi[16];
+        for (int s_hi = lgN - 1; s_hi >= lg_tile && nch < 16; ) {
+            int s_lo = max(lg_tile, s_hi - chunk + 1);
+            ch_lo[nch] = s_lo;
+            ch_hi[nch] = s_hi;
+            nch++;
+            s_hi = s_lo - 1;
+        }
+        for (int c = 0; c < nch; c++)
+            tile_pass<G, ST, true>(tile, lg_tile, scr, lgN, ch_lo[c], ch_hi[c], c == 0, false, in, x_lo, W, out, y_lo,
+                               off, nout, invN);
+        // inner stages on contiguous blocks, with the kernel-power product
+        const int64_t N2 = (int64_t)1 << lg_tile;
+        for (int64_t b = 0; b < N / N2; b++) {
             V *blk = scr + b * N2;
-            for (int64_t s = threadIdx.x; s < N2; s += blockDim.x) sm[s] = blk[s];
-            __syncthreads();
-            fft::dif_range<MODE>(sm, N2, lg2 - 1, 0, T, twl);
-            for (int64_t s = threadIdx.x; s < N2; s += blockDim.x)
-                sm[s] = spec_mul(sm[s], sp, mc, fft::brev_n((uint32_t)(b * N2 + s), lgN), (uint32_t)N);
-            __syncthreads();
-            fft::dit_range<MODE>(sm, N2, 0, lg2 - 1, T, twl);
-            for (int64_t s = threadIdx.x; s < N2; s += blockDim.x) blk[s] = sm[s];
-            __syncthreads();
+            stage_scratch<G>(tile, N2, [](int64_t s) { return s; }, blk);
+            fft::dif_range<MODE, G>(tile, N2, lg_tile - 1, 0, T, twl);
+            for (int64_t s = G::rank(); s < N2; s += G::size())
+                tile[s] = mul_bin(tile[s], sp, mc, fft::brev_n((uint32_t)(b * N2 + s), lgN), (uint32_t)N, g, lgN);
+            G::sync();
+            fft::dit_range<MODE, G>(tile, N2, 0, lg_tile - 1, T, twl);
+            for (int64_t s = G::rank(); s < N2; s += G::size()) blk[s] = tile[s];
+            G::sync();
         }
-        // ---- pass C
-        const int64_t off = y_lo - x_lo;
-        for (int64_t q0 = 0; q0 < N2; q0 += Q) {
-            for (int64_t s = threadIdx.x; s < N1 * Q; s += blockDim.x) {
-                int64_t t = s / Q, q = s - t * Q;
-                sm[s] = scr[q0 + q + t * N2];
-            }
-            __syncthreads();
-            for (int lgm = 0; lgm < lg1; lgm++) {
-                const int64_t m = (int64_t)1 << lgm;
-                const int lgM2 = lgm + lg2 + 1;
-                for (int64_t s = threadIdx.x; s < (N1 / 2) * Q; s += blockDim.x) {
-                    int64_t pr = s / Q, q = s - pr * Q;
-                    int64_t tm = pr & (m - 1);
-                    int64_t t = ((pr - tm) << 1) + tm;
-                    int64_t kk = q0 + q + tm * N2;
-                    V u = sm[t * Q + q];
-                    V v = fft::twmul<true>(sm[(t + m) * Q + q], fft::tw_get<MODE>(T, twl, kk, lgM2));
-                    sm[t * Q + q] = fft::cadd(u, v);
-                    sm[(t + m) * Q + q] = fft::csub(u, v);
-                }
-                __syncthreads();
-            }
-            for (int64_t s = threadIdx.x; s < N1 * Q; s += blockDim.x) {
-                int64_t t = s / Q, q = s - t * Q;
-                int64_t e = q0 + q + t * N2;
-                int64_t k = e - off;
-                if (k >= 0 && k < nout) out.at(y_lo + k) = unsplit(sm[s], invN);
-            }
-            __syncthreads();
-        }
+        for (int c = nch - 1; c >= 0; c--)
+            tile_pass<G, ST, false>(tile, lg_tile, scr, lgN, ch_lo[c], ch_hi[c], false, c == 0, in, x_lo, W, out, y_lo,
+                                off, nout, invN);
+    }
+};
+
+// ------------------------------------------------------------ the walker
+template <int MODE>
+struct Walker {
+    using V = typename fft::Cx<MODE>::V;
+    Cta<MODE> &c;
+    Shared &S;
+    const Params &P;
+    const ExpTables &E;
+    double *cur0, *nxt0;          // walker shared row buffers (kNaiveCap doubles each)
+    double *exw;                  // exercise values of the current base case
+    int32_t *bnd;
+    Counters &cnt;
+    int lane;
+
+    __device__ Walker(Cta<MODE> &c_, double *buf, int32_t *bnd_, Counters &cnt_)
+        : c(c_), S(c_.S), P(c_.S.P), E(c_.S.E), cur0(buf), nxt0(buf + kNaiveCap), exw(buf + 2 * kNaiveCap),
+          bnd(bnd_), cnt(cnt_),
+          lane(threadIdx.x & 31) {}
+
+    __device__ void record(int64_t row, int32_t v) const {
+        if (bnd && lane == 0) bnd[row] = v;
+    }
+    __device__ void record_range(int64_t r0, int64_t r1, int32_t v) const {
+        if (!bnd) return;
+        for (int64_t r = r0 + lane; r <= r1; r += 32) bnd[r] = v;
     }
 
-    // ------------------------------------------------------ naive base cases
-    // Call: rows i0-1 .. i0-h from the red cells [c0, b] of row i0 (in), red
-    // cells of row i0-h written to out; returns the new divider.  Warp 0 only;
-    // the caller brackets it with barriers.  Values live in shared memory.
-    __device__ int64_t naive_call(int64_t i0, int64_t c0, int64_t b, int64_t h, const Buf in,
-                                  const Buf out) {
-        const int lane = threadIdx.x & 31;
-        double *cur = (double *)sm;
-        const int64_t cap = ((int64_t)sizeof(V) << a.lg_nsmem) / (2 * sizeof(double));
-        double *nxt = cur + cap;
+    // post a linear advance into the slot of depth d
+    __device__ void post(int d, const Buf &in, int64_t x_lo, int64_t x_hi, const Buf &out, int64_t g) {
+        if (lane == 0) {
+            Task &t = S.tasks[d];
+            t.in = in;
+            t.out = out;
+            t.x_lo = x_lo;
+            t.x_hi = x_hi;
+            t.g = g;
+            int lgN = ilog2_ceil(x_hi - x_lo + 1);
+            t.lgN = lgN < 2 ? 2 : lgN;
+            __threadfence_block();
+            t.state = TASK_POSTED;
+        }
+        __syncwarp();
+    }
+    // wait until the task of depth d is done (if one is outstanding)
+    __device__ void wait(int d) {
+        if (lane == 0) {
+            Task &t = S.tasks[d];
+            const uint64_t t0 = gtime();
+            while (t.state == TASK_POSTED || t.state == TASK_CLAIMED) {
+                __nanosleep(20);
+                if (gtime() - t0 > kWaitNs) { atomicCAS((int *)&S.err, 0, AOP_ETIMEOUT); break; }
+            }
+            cnt.wait_ns += (long long)(gtime() - t0);
+            t.state = TASK_FREE;
+            __threadfence_block();
+        }
+        __syncwarp();
+    }
+
+    // ----- base cases (FP64, values in the walker's shared buffers)
+    // continuation >= exercise for a non-negative continuation, decided on the
+    // bit patterns (non-negative doubles order like their integer images), so
+    // the test costs no FP64 instruction
+    __device__ static bool cont_ge(double cont, double ex) {
+        const long long eb = __double_as_longlong(ex);
+        return eb <= 0 || __double_as_longlong(cont) >= eb;
+    }
+
+    __device__ int64_t naive_call(int64_t i0, int64_t c0, int64_t b, int64_t h, const Buf &in, const Buf &out) {
+        const uint64_t tb0 = gtime();
+        const int64_t r = naive_call_body(i0, c0, b, h, in, out);
+        if (lane == 0) {
+            cnt.base_ns += (long long)(gtime() - tb0);
+            cnt.base_calls++;
+            cnt.base_rows += h;
+        }
+        return r;
+    }
+    __device__ int64_t naive_call_body(int64_t i0, int64_t c0, int64_t b, int64_t h, const Buf &in, const Buf &out) {
+        double *cur = cur0, *nxt = nxt0;
         const int D = P.D;
         const double w0 = P.w[0], w1 = P.w[1], w2 = P.w[2];
-        if (b - c0 + 1 + D > cap) {          // never expected: window wider than the buffer
-            if (lane == 0) set_error(a.err, AOP_EINTERNAL);
+        if (b - c0 + 1 + D > kNaiveCap) {          // never expected: window wider than the buffer
+            if (lane == 0) atomicCAS((int *)&S.err, 0, AOP_EINTERNAL);
             return b;
         }
-        for (int64_t x = c0 + lane; x <= b; x += 32) cur[x - c0] = in.at(x);
+        // exercise values the base case can touch (the divider moves <= 1 cell
+        // per row): one table of exponent indices, filled once
+        const int64_t klo = max((int64_t)0, ex_index(P, i0, b) - h - 2);
+        const int64_t khi = min(2 * P.T, ex_index(P, i0 - h, b + D) + 2);
+        if (khi - klo + 1 > kNaiveCap) {
+            if (lane == 0) atomicCAS((int *)&S.err, 0, AOP_EINTERNAL);
+            return b;
+        }
+        for (int64_t kp = klo + lane; kp <= khi; kp += 32) exw[kp - klo] = exercise(P, E, kp);
+        for (int64_t x = c0 + lane; x <= b; x += 32) cur[x - c0] = cell_ld<MODE>(in, x);
         __syncwarp();
         long long cells = 0;
         for (int64_t k = 1; k <= h; k++) {
             const int64_t i = i0 - k;
             const int64_t bp = b;
             if (bp < c0) {
-                if (lane == 0) record(i, (int32_t)(c0 - 1));
+                record(i, (int32_t)(c0 - 1));
                 continue;
             }
             const int64_t top = min(bp, (int64_t)D * i);
             for (int64_t x = c0 + lane; x <= top; x += 32) {
                 double v0 = cur[x - c0];
-                double v1 = (x + 1 <= bp) ? cur[x + 1 - c0] : exercise(P, E, ex_index(P, i + 1, x + 1));
-                double c = w0 * v0 + w1 * v1;
+                double v1 = (x + 1 <= bp) ? cur[x + 1 - c0] : exw[ex_index(P, i + 1, x + 1) - klo];
+                double cv = w0 * v0 + w1 * v1;
                 if (D == 2) {
-                    double v2 = (x + 2 <= bp) ? cur[x + 2 - c0] : exercise(P, E, ex_index(P, i + 1, x + 2));
-                    c += w2 * v2;
+                    double v2 = (x + 2 <= bp) ? cur[x + 2 - c0] : exw[ex_index(P, i + 1, x + 2) - klo];
+                    cv += w2 * v2;
                 }
-                nxt[x - c0] = c;
+                nxt[x - c0] = cv;
                 cells++;
             }
             __syncwarp();
@@ -415,36 +653,46 @@ struct Dnc {
                 bn = (int64_t)D * i;
             } else {
                 // value-versus-payoff test at the previous divider (Cor. 2.7)
-                const double cont = nxt[bp - c0];
-                bn = (cont >= exercise(P, E, ex_index(P, i, bp))) ? bp : bp - 1;
+                bn = cont_ge(nxt[bp - c0], exw[ex_index(P, i, bp) - klo]) ? bp : bp - 1;
             }
             b = bn;
-            if (lane == 0) record(i, (int32_t)(b >= c0 ? b : c0 - 1));
+            record(i, (int32_t)(b >= c0 ? b : c0 - 1));
             double *t = cur; cur = nxt; nxt = t;
             __syncwarp();
         }
-        for (int64_t x = c0 + lane; x <= b; x += 32) out.at(x) = cur[x - c0];
+        for (int64_t x = c0 + lane; x <= b; x += 32) cell_st<MODE>(out, x, cur[x - c0]);
         cells = __reduce_add_sync(0xffffffffu, (unsigned)cells);
         if (lane == 0) cnt.base_cells += cells;
+        __threadfence_block();
+        __syncwarp();
         return b;
     }
 
-    // Put: rows n+1 .. n+h over the window [lo, hi] of row n with divider f;
-    // red cells (> f) come from in; writes the red cells of row n+h to out.
-    __device__ int64_t naive_put(int64_t n, int64_t lo, int64_t hi, int64_t f, int64_t h,
-                                 const Buf in, const Buf out) {
-        const int lane = threadIdx.x & 31;
-        double *cur = (double *)sm;
-        const int64_t cap = ((int64_t)sizeof(V) << a.lg_nsmem) / (2 * sizeof(double));
-        double *nxt = cur + cap;
+    __device__ int64_t naive_put(int64_t n, int64_t lo, int64_t hi, int64_t f, int64_t h, const Buf &in,
+                                 const Buf &out) {
+        const uint64_t tb0 = gtime();
+        const int64_t r = naive_put_body(n, lo, hi, f, h, in, out);
+        if (lane == 0) {
+            cnt.base_ns += (long long)(gtime() - tb0);
+            cnt.base_calls++;
+            cnt.base_rows += h;
+        }
+        return r;
+    }
+    __device__ int64_t naive_put_body(int64_t n, int64_t lo, int64_t hi, int64_t f, int64_t h, const Buf &in,
+                                      const Buf &out) {
+        double *cur = cur0, *nxt = nxt0;
         const double wb = P.w[0], wc = P.w[1], wa = P.w[2];
-        if (hi - lo + 1 > cap) {
-            if (lane == 0) set_error(a.err, AOP_EINTERNAL);
+        if (hi - lo + 1 > kNaiveCap) {
+            if (lane == 0) atomicCAS((int *)&S.err, 0, AOP_EINTERNAL);
             return f;
         }
-        // full window values (green in closed form)
-        for (int64_t x = lo + lane; x <= hi; x += 32)
-            cur[x - lo] = (x <= f) ? exercise(P, E, ex_index(P, n, x)) : in.at(x);
+        // the put's payoff does not depend on the time step: one table per window
+        for (int64_t x = lo + lane; x <= hi; x += 32) {
+            const double e = exercise(P, E, ex_index(P, n, x));
+            exw[x - lo] = e;
+            cur[x - lo] = (x <= f) ? e : cell_ld<MODE>(in, x);
+        }
         __syncwarp();
         long long cells = 0;
         int64_t L = lo, R = hi;
@@ -452,8 +700,7 @@ struct Dnc {
             const int64_t nl = L + 1, nr = R - 1;
             const int64_t fp = f;
             for (int64_t x = nl + lane; x <= nr; x += 32) {
-                double c = wb * cur[x - 1 - lo] + wc * cur[x - lo] + wa * cur[x + 1 - lo];
-                nxt[x - lo] = c;
+                nxt[x - lo] = wb * cur[x - 1 - lo] + wc * cur[x - lo] + wa * cur[x + 1 - lo];
                 cells++;
             }
             __syncwarp();
@@ -461,66 +708,40 @@ struct Dnc {
             if (fp >= nr + 1) fn = nr;
             else if (fp < nl) fn = fp;
             else {
-                const double ex = exercise(P, E, ex_index(P, n + k, fp));
-                fn = (ex > nxt[fp - lo]) ? fp : fp - 1;
+                // exercise > continuation (non-negative continuation; bit compare)
+                const long long eb = __double_as_longlong(exw[fp - lo]);
+                fn = (eb > 0 && eb > __double_as_longlong(nxt[fp - lo])) ? fp : fp - 1;
             }
             f = fn;
-            // green cells of the new row hold the payoff
-            for (int64_t x = nl + lane; x <= min(f, nr); x += 32)
-                nxt[x - lo] = exercise(P, E, ex_index(P, n + k, x));
-            if (lane == 0) record(n + k, (f >= nl) ? (int32_t)f : (int32_t)AOP_BOUNDARY_NONE_PUT);
+            for (int64_t x = nl + lane; x <= min(f, nr); x += 32) nxt[x - lo] = exw[x - lo];
+            record(n + k, (f >= nl) ? (int32_t)f : (int32_t)AOP_BOUNDARY_NONE_PUT);
             double *t = cur; cur = nxt; nxt = t;
             L = nl; R = nr;
             __syncwarp();
         }
-        for (int64_t x = max(L, f + 1) + lane; x <= R; x += 32) out.at(x) = cur[x - lo];
+        for (int64_t x = max(L, f + 1) + lane; x <= R; x += 32) cell_st<MODE>(out, x, cur[x - lo]);
         cells = __reduce_add_sync(0xffffffffu, (unsigned)cells);
         if (lane == 0) cnt.base_cells += cells;
+        __threadfence_block();
+        __syncwarp();
         return f;
     }
 
-    // run naive_* on warp 0 and broadcast the divider
-    __device__ int64_t base_call(int64_t i0, int64_t c0, int64_t b, int64_t h, const Buf in, const Buf out) {
-        __shared__ int64_t s_ret;
-        __syncthreads();
-        if (threadIdx.x < 32) {
-            int64_t r = naive_call(i0, c0, b, h, in, out);
-            if (threadIdx.x == 0) s_ret = r;
-        }
-        __syncthreads();
-        return s_ret;
-    }
-    __device__ int64_t base_put(int64_t n, int64_t lo, int64_t hi, int64_t f, int64_t h, const Buf in,
-                                const Buf out) {
-        __shared__ int64_t s_ret;
-        __syncthreads();
-        if (threadIdx.x < 32) {
-            int64_t r = naive_put(n, lo, hi, f, h, in, out);
-            if (threadIdx.x == 0) s_ret = r;
-        }
-        __syncthreads();
-        return s_ret;
-    }
-
-    __device__ void record_range(int64_t r0, int64_t r1, int32_t v) {
-        if (!bnd) return;
-        for (int64_t r = r0 + threadIdx.x; r <= r1; r += blockDim.x) bnd[r] = v;
-    }
-
-    // ------------------------------------------------------------ the call
+    // ----- call recursion (explicit stack; every lane holds the same state)
     struct FrameC {
         int64_t i0, c0, b, h;
         Buf in, out;
-        int depth, phase;
+        int depth, phase, posted;
     };
 
-    __device__ int64_t solve_call(int64_t i0, int64_t b, int64_t h, const Buf row) {
+    __device__ int64_t solve_call(int64_t i0, int64_t b, int64_t h, const Buf &row) {
         FrameC st[kMaxDepth];
         int sp = 0;
         int64_t ret = 0;
         const int D = P.D;
-        st[sp++] = FrameC{i0, 0, b, h, row, row, 0, 0};
+        st[sp++] = FrameC{i0, 0, b, h, row, row, 0, 0, 0};
         while (sp > 0) {
+            if (S.err) return ret;
             FrameC &F = st[sp - 1];
             if (F.phase == 0) {
                 if (F.b < F.c0) {
@@ -529,252 +750,374 @@ struct Dnc {
                     sp--;
                     continue;
                 }
-                if (F.h <= a.B || F.depth + 1 >= kMaxDepth) {
-                    ret = base_call(F.i0, F.c0, F.b, F.h, F.in, F.out);
+                if (F.h <= c.a.B || F.depth + 1 >= kMaxDepth) {
+                    ret = naive_call(F.i0, F.c0, F.b, F.h, F.in, F.out);
                     sp--;
                     continue;
                 }
                 const int64_t h1 = F.h >> 1;
-                const Buf M{mid(F.depth), F.c0};
-                if (F.b - D * h1 >= F.c0) conv(F.in, F.c0, F.b, M, h1);
+                const Buf M{c.mid(F.depth), F.c0};
+                F.posted = 0;
+                if (F.b - D * h1 >= F.c0) {
+                    post(F.depth, F.in, F.c0, F.b, M, h1);
+                    F.posted = 1;
+                }
                 const int64_t c1 = max(F.c0, F.b - D * h1 + 1);
                 F.phase = 1;
-                st[sp++] = FrameC{F.i0, c1, F.b, h1, F.in, M, F.depth + 1, 0};
+                st[sp++] = FrameC{F.i0, c1, F.b, h1, F.in, M, F.depth + 1, 0, 0};
             } else if (F.phase == 1) {
+                if (F.posted) wait(F.depth);
                 const int64_t b1 = ret;
                 const int64_t h1 = F.h >> 1, h2 = F.h - h1;
-                const Buf M{mid(F.depth), F.c0};
-                if (b1 - D * h2 >= F.c0) conv(M, F.c0, b1, F.out, h2);
+                const Buf M{c.mid(F.depth), F.c0};
+                F.posted = 0;
+                if (b1 - D * h2 >= F.c0) {
+                    post(F.depth, M, F.c0, b1, F.out, h2);
+                    F.posted = 1;
+                }
                 const int64_t c2 = max(F.c0, b1 - D * h2 + 1);
                 F.phase = 2;
-                st[sp++] = FrameC{F.i0 - h1, c2, b1, h2, M, F.out, F.depth + 1, 0};
+                st[sp++] = FrameC{F.i0 - h1, c2, b1, h2, M, F.out, F.depth + 1, 0, 0};
             } else {
+                if (F.posted) wait(F.depth);
                 sp--;
             }
         }
         return ret;
     }
 
-    __device__ double price_call() {
-        const int64_t T = P.T;
+    __device__ double price_call(int64_t b) {
         const int D = P.D;
-        const Buf row{(double *)(slot + a.off_r0), 0};
-        __shared__ int s_b;
-        // row T: red iff its payoff is <= 0 (continuation 0); row T-1 naive.
-        if (threadIdx.x == 0) s_b = -1;
-        __syncthreads();
-        int bt = -1;
-        for (int64_t j = threadIdx.x; j <= (int64_t)D * T; j += blockDim.x)
-            if (0.0 >= exercise(P, E, ex_index(P, T, j))) bt = max(bt, (int)j);
-        bt = __reduce_max_sync(0xffffffffu, bt);
-        if ((threadIdx.x & 31) == 0) atomicMax(&s_b, bt);
-        __syncthreads();
-        if (threadIdx.x == 0) record(T, s_b);
-        __syncthreads();
-        int64_t i = T - 1;
-        if (threadIdx.x == 0) s_b = -1;
-        __syncthreads();
-        int br = -1;
-        const double w0 = P.w[0], w1 = P.w[1], w2 = P.w[2];
-        for (int64_t j = threadIdx.x; j <= (int64_t)D * i; j += blockDim.x) {
-            double c = w0 * fmax(exercise(P, E, ex_index(P, T, j)), 0.0) +
-                       w1 * fmax(exercise(P, E, ex_index(P, T, j + 1)), 0.0);
-            if (D == 2) c += w2 * fmax(exercise(P, E, ex_index(P, T, j + 2)), 0.0);
-            row.at(j) = c;
-            if (c >= exercise(P, E, ex_index(P, i, j))) br = max(br, (int)j);
-        }
-        br = __reduce_max_sync(0xffffffffu, br);
-        if ((threadIdx.x & 31) == 0) atomicMax(&s_b, br);
-        __syncthreads();
-        int64_t b = s_b;
-        if (threadIdx.x == 0) record(i, (int32_t)b);
-        __syncthreads();
+        const Buf row{(double *)(c.slot + c.a.off_r0), 0};
+        int64_t i = P.T - 1;
         while (i > 0) {
+            if (S.err) return __longlong_as_double(0x7ff8000000000000ll);
             if (b < 0) {
                 record_range(0, i - 1, -1);
-                __syncthreads();
                 return exercise(P, E, ex_index(P, 0, 0));
             }
             const int64_t avail = i - kLeftoverCall;
-            if (avail < a.B) {
-                b = base_call(i, 0, b, i, row, row);
+            if (avail < c.a.B) {
+                b = naive_call(i, 0, b, i, row, row);
                 i = 0;
                 break;
             }
             const int64_t w = b + 1;
-            const int64_t want = max((int64_t)a.B, (w + D - 1) / D);
-            int64_t h = a.B;
+            const int64_t want = max((int64_t)c.a.B, (w + D - 1) / D);
+            int64_t h = c.a.B;
             while (2 * h <= want && 2 * h <= avail) h *= 2;
             b = solve_call(i, b, h, row);
             i -= h;
         }
-        __syncthreads();
         if (b < 0) return exercise(P, E, ex_index(P, 0, 0));
-        return row.at(0);
+        return cell_ld<MODE>(row, 0);
     }
 
-    // ------------------------------------------------------------- the put
+    // ----- put recursion
     struct FrameP {
         int64_t n, lo, hi, f, h;
         Buf in, out;
-        int depth, phase;
+        int depth, phase, posted;
     };
 
-    __device__ int64_t solve_put(int64_t n0, int64_t lo0, int64_t hi0, int64_t f0, int64_t h0,
-                                 const Buf row) {
+    __device__ int64_t solve_put(int64_t n0, int64_t lo0, int64_t hi0, int64_t f0, int64_t h0, const Buf &row) {
         FrameP st[kMaxDepth];
         int sp = 0;
         int64_t ret = 0;
-        st[sp++] = FrameP{n0, lo0, hi0, f0, h0, row, row, 0, 0};
+        st[sp++] = FrameP{n0, lo0, hi0, f0, h0, row, row, 0, 0, 0};
         while (sp > 0) {
+            if (S.err) return ret;
             FrameP &F = st[sp - 1];
             const int64_t h1 = F.h >> 1, h2 = F.h - h1;
             if (F.phase == 0) {
                 if (F.f < F.lo) {        // no green cell in the window: one advance
-                    conv(F.in, F.lo, F.hi, F.out, F.h);
+                    post(F.depth, F.in, F.lo, F.hi, F.out, F.h);
                     record_range(F.n + 1, F.n + F.h, AOP_BOUNDARY_NONE_PUT);
+                    wait(F.depth);
                     ret = F.lo + F.h - 1;
                     sp--;
                     continue;
                 }
-                if (F.h <= a.B || F.depth + 1 >= kMaxDepth) {
-                    ret = base_put(F.n, F.lo, F.hi, F.f, F.h, F.in, F.out);
+                if (F.h <= c.a.B || F.depth + 1 >= kMaxDepth) {
+                    ret = naive_put(F.n, F.lo, F.hi, F.f, F.h, F.in, F.out);
                     sp--;
                     continue;
                 }
-                const Buf M{mid(F.depth), F.lo + h1};
-                if (F.f + 1 + h1 <= F.hi - h1) conv(F.in, F.f + 1, F.hi, M, h1);
+                const Buf M{c.mid(F.depth), F.lo + h1};
+                F.posted = 0;
+                if (F.f + 1 + h1 <= F.hi - h1) {
+                    post(F.depth, F.in, F.f + 1, F.hi, M, h1);
+                    F.posted = 1;
+                }
                 const int64_t lo2 = max(F.lo, F.f - 2 * h1), hi2 = min(F.hi, F.f + 2 * h1);
                 F.phase = 1;
-                st[sp++] = FrameP{F.n, lo2, hi2, F.f, h1, F.in, M, F.depth + 1, 0};
+                st[sp++] = FrameP{F.n, lo2, hi2, F.f, h1, F.in, M, F.depth + 1, 0, 0};
             } else if (F.phase == 1) {
+                if (F.posted) wait(F.depth);
                 const int64_t f1 = ret;
                 const int64_t lo1 = F.lo + h1, hi1 = F.hi - h1;
-                const Buf M{mid(F.depth), lo1};
+                const Buf M{c.mid(F.depth), lo1};
                 if (f1 < lo1) {
-                    conv(M, lo1, hi1, F.out, h2);
+                    post(F.depth, M, lo1, hi1, F.out, h2);
                     record_range(F.n + h1 + 1, F.n + F.h, AOP_BOUNDARY_NONE_PUT);
+                    wait(F.depth);
                     ret = F.lo + F.h - 1;
                     sp--;
                     continue;
                 }
-                if (f1 + 1 + h2 <= hi1 - h2) conv(M, f1 + 1, hi1, F.out, h2);
+                F.posted = 0;
+                if (f1 + 1 + h2 <= hi1 - h2) {
+                    post(F.depth, M, f1 + 1, hi1, F.out, h2);
+                    F.posted = 1;
+                }
                 const int64_t lo2 = max(lo1, f1 - 2 * h2), hi2 = min(hi1, f1 + 2 * h2);
                 F.phase = 2;
-                st[sp++] = FrameP{F.n + h1, lo2, hi2, f1, h2, M, F.out, F.depth + 1, 0};
+                st[sp++] = FrameP{F.n + h1, lo2, hi2, f1, h2, M, F.out, F.depth + 1, 0, 0};
             } else {
+                if (F.posted) wait(F.depth);
                 sp--;
             }
         }
         return ret;
     }
 
-    __device__ double price_put() {
+    __device__ double price_put(int64_t f) {
         const int64_t T = P.T;
-        const Buf row{(double *)(slot + a.off_r0), -T};
-        __shared__ int s_f;
-        if (threadIdx.x == 0) s_f = INT32_MIN;
-        __syncthreads();
-        int fb = INT32_MIN;
-        for (int64_t k = -T + threadIdx.x; k <= T; k += blockDim.x) {
-            double e = exercise(P, E, ex_index(P, 0, k));
-            row.at(k) = e > 0.0 ? e : 0.0;
-            if (e > 0.0) fb = max(fb, (int)k);
-        }
-        fb = __reduce_max_sync(0xffffffffu, fb);
-        if ((threadIdx.x & 31) == 0) atomicMax(&s_f, fb);
-        __syncthreads();
-        if (threadIdx.x == 0) record(0, s_f);
-        __syncthreads();
-        // Row 1 over the whole row.  The divider theorem (k_n - k_{n+1} <= 1)
-        // rests on the divider cell being green by the max at row n; at the
-        // expiry row it is green by its payoff alone, so row 0 -> 1 may move
-        // the divider arbitrarily far (e.g. r = 0: no cell stays green).
-        if (threadIdx.x == 0) s_f = INT32_MIN;
-        const Buf tmp{mid(0), -T};
-        __syncthreads();
-        fb = INT32_MIN;
-        {
-            const double wb = P.w[0], wc = P.w[1], wa = P.w[2];
-            for (int64_t k = -(T - 1) + threadIdx.x; k <= T - 1; k += blockDim.x) {
-                const double c = wb * row.at(k - 1) + wc * row.at(k) + wa * row.at(k + 1);
-                const double e = exercise(P, E, ex_index(P, 1, k));
-                const bool green = e > c;
-                tmp.at(k) = green ? e : c;
-                if (green) fb = max(fb, (int)k);
-            }
-        }
-        fb = __reduce_max_sync(0xffffffffu, fb);
-        if ((threadIdx.x & 31) == 0) atomicMax(&s_f, fb);
-        __syncthreads();
-        for (int64_t k = -(T - 1) + threadIdx.x; k <= T - 1; k += blockDim.x) row.at(k) = tmp.at(k);
-        if (threadIdx.x == 0) record(1, s_f);
-        int64_t f = (s_f == INT32_MIN) ? -T - 1 : s_f;
-        __syncthreads();
+        const Buf row{(double *)(c.slot + c.a.off_r0), -T};
         int64_t n = 1;
         while (T - n > 0) {
+            if (S.err) return __longlong_as_double(0x7ff8000000000000ll);
             const int64_t R = T - n;
             if (f >= R) {                // every remaining cell is green
-                for (int64_t r = n + 1 + threadIdx.x; r <= T; r += blockDim.x)
-                    if (bnd) bnd[r] = (int32_t)(T - r);
-                __syncthreads();
+                if (bnd)
+                    for (int64_t r = n + 1 + lane; r <= T; r += 32) bnd[r] = (int32_t)(T - r);
                 return P.out_scale * exercise(P, E, ex_index(P, T, 0));
             }
-            if (R / 2 < a.B || R <= 2 * a.B) {
-                f = base_put(n, -R, R, f, R, row, row);
+            if (R / 2 < c.a.B || R <= 2 * c.a.B) {
+                f = naive_put(n, -R, R, f, R, row, row);
                 n = T;
                 break;
             }
-            int64_t h = a.B;
+            int64_t h = c.a.B;
             while (2 * h <= R / 2) h *= 2;
             f = solve_put(n, -R, R, f, h, row);
             n += h;
         }
-        __syncthreads();
         if (f >= 0) return P.out_scale * exercise(P, E, ex_index(P, T, 0));
-        return P.out_scale * row.at(0);
+        return P.out_scale * cell_ld<MODE>(row, 0);
     }
 };
 
+// -------------------------------------------------- block-level first rows
+// Calls: row T (continuation 0) and row T-1 over the whole row.  Cor. 2.7
+// holds from row T-1 down only: with r > q the divider jumps right between
+// rows T and T-1.  Returns the divider of row T-1.
+template <int MODE>
+__device__ int64_t first_rows_call(Cta<MODE> &c, int32_t *bnd) {
+    Shared &S = c.S;
+    const Params &P = S.P;
+    const ExpTables &E = S.E;
+    const int64_t T = P.T;
+    const int D = P.D;
+    const Buf row{(double *)(c.slot + c.a.off_r0), 0};
+    if (threadIdx.x == 0) S.bcast_i = -1;
+    __syncthreads();
+    int bt = -1;
+    for (int64_t j = threadIdx.x; j <= (int64_t)D * T; j += blockDim.x)
+        if (0.0 >= exercise(P, E, ex_index(P, T, j))) bt = max(bt, (int)j);
+    bt = __reduce_max_sync(0xffffffffu, bt);
+    if ((threadIdx.x & 31) == 0) atomicMax(&S.bcast_i, bt);
+    __syncthreads();
+    if (threadIdx.x == 0 && bnd) bnd[T] = S.bcast_i;
+    __syncthreads();
+    if (threadIdx.x == 0) S.bcast_i = -1;
+    __syncthreads();
+    const int64_t i = T - 1;
+    int br = -1;
+    const double w0 = P.w[0], w1 = P.w[1], w2 = P.w[2];
+    for (int64_t j = threadIdx.x; j <= (int64_t)D * i; j += blockDim.x) {
+        double cv = w0 * fmax(exercise(P, E, ex_index(P, T, j)), 0.0) +
+                    w1 * fmax(exercise(P, E, ex_index(P, T, j + 1)), 0.0);
+        if (D == 2) cv += w2 * fmax(exercise(P, E, ex_index(P, T, j + 2)), 0.0);
+        cell_st<MODE>(row, j, cv);
+        if (cv >= exercise(P, E, ex_index(P, i, j))) br = max(br, (int)j);
+    }
+    br = __reduce_max_sync(0xffffffffu, br);
+    if ((threadIdx.x & 31) == 0) atomicMax(&S.bcast_i, br);
+    __syncthreads();
+    const int64_t b = S.bcast_i;
+    if (threadIdx.x == 0 && bnd) bnd[i] = (int32_t)b;
+    __syncthreads();
+    return b;
+}
+
+// Put: row 0 (the payoff) and row 1 over the whole row.  The BSM divider
+// theorem's step k_n - k_{n+1} <= 1 rests on the divider cell being green by
+// the max at row n; at the expiry row it is green by its payoff alone, so the
+// step 0 -> 1 may move the divider arbitrarily far (r = 0: no cell stays
+// green).  Returns the divider of row 1 (or -T-1 when it has no green cell).
+template <int MODE>
+__device__ int64_t first_rows_put(Cta<MODE> &c, int32_t *bnd) {
+    Shared &S = c.S;
+    const Params &P = S.P;
+    const ExpTables &E = S.E;
+    const int64_t T = P.T;
+    const Buf row{(double *)(c.slot + c.a.off_r0), -T};
+    if (threadIdx.x == 0) S.bcast_i = INT32_MIN;
+    __syncthreads();
+    int fb = INT32_MIN;
+    for (int64_t k = -T + threadIdx.x; k <= T; k += blockDim.x)
+        if (exercise(P, E, ex_index(P, 0, k)) > 0.0) fb = max(fb, (int)k);
+    fb = __reduce_max_sync(0xffffffffu, fb);
+    if ((threadIdx.x & 31) == 0) atomicMax(&S.bcast_i, fb);
+    __syncthreads();
+    if (threadIdx.x == 0 && bnd) bnd[0] = S.bcast_i;
+    __syncthreads();
+    if (threadIdx.x == 0) S.bcast_i = INT32_MIN;
+    __syncthreads();
+    // row 1 straight from the payoff max(e, 0) of row 0
+    fb = INT32_MIN;
+    const double wb = P.w[0], wc = P.w[1], wa = P.w[2];
+    for (int64_t k = -(T - 1) + threadIdx.x; k <= T - 1; k += blockDim.x) {
+        const double cv = wb * fmax(exercise(P, E, ex_index(P, 0, k - 1)), 0.0) +
+                          wc * fmax(exercise(P, E, ex_index(P, 0, k)), 0.0) +
+                          wa * fmax(exercise(P, E, ex_index(P, 0, k + 1)), 0.0);
+        const double e = exercise(P, E, ex_index(P, 1, k));
+        const bool green = e > cv;
+        cell_st<MODE>(row, k, green ? e : cv);
+        if (green) fb = max(fb, (int)k);
+    }
+    fb = __reduce_max_sync(0xffffffffu, fb);
+    if ((threadIdx.x & 31) == 0) atomicMax(&S.bcast_i, fb);
+    __syncthreads();
+    const int f = S.bcast_i;
+    if (threadIdx.x == 0 && bnd) bnd[1] = f;
+    __syncthreads();
+    return (f == INT32_MIN) ? -T - 1 : f;
+}
+
+// ------------------------------------------------------------------ kernel
 template <int MODE>
 __global__ void __launch_bounds__(kThreadsD) dnc_kernel(const __grid_constant__ DncArgs a)
 {
     using V = typename fft::Cx<MODE>::V;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    __shared__ ExpTables E;
-    __shared__ Params sP;
-    __shared__ SpecEntry cache[kSpecSlots];
-    __shared__ int ncache;
-    __shared__ int64_t arena_used;
-    __shared__ int s_opt;
-    V *sm = (V *)smem_raw;
+    __shared__ Shared S;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    double *walker_buf = (double *)smem_raw;                              // 3 x kNaiveCap doubles
+    V *tiles = (V *)(smem_raw + 3 * kNaiveCap * sizeof(double));        // one tile per worker
     char *slot = a.ws + (int64_t)blockIdx.x * a.ws_stride;
-    Counters cnt{0, 0, 0, 0, 0, 0, 0};
+    Cta<MODE> c(a, S, slot);
+    Counters cnt{};
+    // Place the recursion warp of each resident CTA on a different SM
+    // sub-partition: FP64 instructions issue at a fraction of a warp per cycle
+    // per sub-partition, and the walkers' FP64 base cases must not queue behind
+    // one another.  The k-th CTA to arrive on an SM walks with the warp whose
+    // hardware slot lies in sub-partition k mod 4.
+    __shared__ int s_walker;
+    __shared__ int s_sub[kWarps];
+    if (lane == 0) {
+        unsigned wid_hw;
+        asm volatile("mov.u32 %0, %%warpid;" : "=r"(wid_hw));
+        s_sub[warp] = (int)(wid_hw & 3);
+    }
+    if (threadIdx.x == 0) {
+        unsigned smid;
+        asm volatile("mov.u32 %0, %%smid;" : "=r"(smid));
+        s_walker = a.sm_slots ? (atomicAdd(&a.sm_slots[smid & 1023], 1) & 3) : 0;
+    }
+    __syncthreads();
+    int walker = 0;
+    for (int w = 0; w < kWarps; w++)
+        if (s_sub[w] == s_walker) { walker = w; break; }
+    const int role = (warp - walker + kWarps) % kWarps;    // 0 = walker, 1..3 = workers
     for (;;) {
-        if (threadIdx.x == 0) s_opt = atomicAdd(a.queue, 1);
+        if (threadIdx.x == 0) S.opt = atomicAdd(a.queue, 1);
         __syncthreads();
-        const int64_t o = s_opt;
+        const int64_t o = S.opt;
         if (o >= a.n) break;
         if (threadIdx.x == 0) {
-            sP = a.params[o];
-            ncache = 0;
-            arena_used = 0;
+            S.P = a.params[o];
+            S.spec_n = 0;
+            S.spec_lock = 0;
+            S.arena_used = 0;
+            S.done = 0;
+            S.err = 0;
+            for (int d = 0; d < kMaxDepth; d++) S.tasks[d].state = TASK_FREE;
         }
         __syncthreads();
-        if (sP.status != AOP_OK) {
+        if (S.P.status != AOP_OK) {
             if (threadIdx.x == 0) a.prices[o] = __longlong_as_double(0x7ff8000000000000ll);
             __syncthreads();
             continue;
         }
-        build_exp_tables(sP, E);
-        __syncthreads();
         uint64_t t_start = 0;
         if (threadIdx.x == 0 && a.opt_ns) asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t_start));
+        build_exp_tables(S.P, S.E);
+        __syncthreads();
         int32_t *bnd = a.bnd ? a.bnd + a.bnd_off[o] : nullptr;
-        Dnc<MODE> d(a, sP, E, sm, slot, cache, &ncache, &arena_used, bnd, cnt);
-        double price = (sP.model == AOP_BSM_PUT) ? d.price_put() : d.price_call();
+        const bool put = (S.P.model == AOP_BSM_PUT);
+        const int64_t first = put ? first_rows_put(c, bnd) : first_rows_call(c, bnd);
+        if (role == 0) {
+            Walker<MODE> wk(c, walker_buf, bnd, cnt);
+            const uint64_t tw0 = gtime();
+            const double price = put ? wk.price_put(first) : wk.price_call(first);
+            if (lane == 0) {
+                cnt.walker_ns += (long long)(gtime() - tw0);
+                S.price = price;
+                __threadfence_block();
+                S.done = 1;
+            }
+            __syncwarp();
+        } else {
+            const int wid = role - 1;
+            V *tile = tiles + ((int64_t)wid << a.lg_tile);
+            uint64_t idle0 = gtime();
+            for (;;) {
+                int pick = -1;
+                if (lane == 0) {
+                    if (S.done) pick = -2;
+                    else {
+                        for (int d = kMaxDepth - 1; d >= 0; d--) {
+                            if (S.tasks[d].state != TASK_POSTED) continue;
+                            if (wid >= kBigWorkers && S.tasks[d].lgN > a.lg_tile) continue;
+                            if (atomicCAS((int *)&S.tasks[d].state, TASK_POSTED, TASK_CLAIMED) == TASK_POSTED) {
+                                pick = d;
+                                break;
+                            }
+                        }
+                    }
+                }
+                pick = __shfl_sync(0xffffffffu, pick, 0);
+                if (pick == -2) break;
+                if (pick < 0) {
+                    __nanosleep(64);
+                    if (gtime() - idle0 > kWaitNs) {
+                        if (lane == 0) atomicCAS((int *)&S.err, 0, AOP_ETIMEOUT);
+                        break;
+                    }
+                    continue;
+                }
+                const uint64_t tb = gtime();
+                __threadfence_block();
+                const Task t = *(const Task *)&S.tasks[pick];
+                c.template conv<fft::WarpGroup, StoreCell<MODE>>(t.in, t.x_lo, t.x_hi, t.out, t.g, tile, a.lg_tile,
+                                                wid < kBigWorkers ? c.scratch(wid) : nullptr, cnt);
+                __threadfence_block();
+                __syncwarp();
+                if (lane == 0) S.tasks[pick].state = TASK_DONE;
+                idle0 = gtime();
+                if (lane == 0) cnt.busy_ns += (long long)(idle0 - tb);
+            }
+        }
+        __syncthreads();
         if (threadIdx.x == 0) {
-            a.prices[o] = price;
+            const int err = S.err;
+            a.prices[o] = err ? __longlong_as_double(0x7ff8000000000000ll) : S.price;
+            if (err) {
+                if (a.status) a.status[o] = err;
+                if (a.err) atomicCAS(a.err, 0, err);
+            }
             if (a.opt_ns) {
                 uint64_t t_end;
                 asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t_end));
@@ -783,35 +1126,44 @@ __global__ void __launch_bounds__(kThreadsD) dnc_kernel(const __grid_constant__ 
         }
         __syncthreads();
     }
-    if (threadIdx.x == 0 && a.stats) {
+    if (lane == 0 && a.stats) {
         atomicAdd((unsigned long long *)&a.stats->convolutions, (unsigned long long)cnt.convs);
         atomicAdd((unsigned long long *)&a.stats->fft_points, (unsigned long long)cnt.fft_points);
         atomicAdd((unsigned long long *)&a.stats->fft_flops, (unsigned long long)cnt.fft_flops);
         atomicAdd((unsigned long long *)&a.stats->conv_inputs, (unsigned long long)cnt.conv_in);
         atomicAdd((unsigned long long *)&a.stats->conv_outputs, (unsigned long long)cnt.conv_out);
         atomicAdd((unsigned long long *)&a.stats->global_fft_bytes, (unsigned long long)cnt.gbytes);
-    }
-    if ((threadIdx.x & 31) == 0 && threadIdx.x == 0 && a.stats)
         atomicAdd((unsigned long long *)&a.stats->basecase_cells, (unsigned long long)cnt.base_cells);
+        atomicAdd((unsigned long long *)&a.stats->walker_wait_ns, (unsigned long long)cnt.wait_ns);
+        atomicAdd((unsigned long long *)&a.stats->worker_busy_ns, (unsigned long long)cnt.busy_ns);
+        atomicAdd((unsigned long long *)&a.stats->walker_base_ns, (unsigned long long)cnt.base_ns);
+        atomicAdd((unsigned long long *)&a.stats->basecase_calls, (unsigned long long)cnt.base_calls);
+        atomicAdd((unsigned long long *)&a.stats->basecase_rows, (unsigned long long)cnt.base_rows);
+        atomicAdd((unsigned long long *)&a.stats->walker_ns, (unsigned long long)cnt.walker_ns);
+    }
 }
 
 // ------------------------------------------------------------ layout/launch
 struct Layout {
     int64_t W_max, N_max, spec_cap;
-    int64_t off_r0, off_mid, off_scr, off_spec, stride;
+    int64_t off_r0, off_mid, off_scr, off_spec, scr_stride, stride;
     int64_t mid_off[kMaxDepth];
-    int lg_nsmem, tw_log2;
+    int lg_tile, lg_block, tw_log2, vsz;
+    size_t smem;
 };
 
-Layout make_layout(int method, int64_t T_max, int B) {
+int value_bytes(int method) {
+    return method == AOP_FFT_FP32SPLIT ? 8 : 16;
+}
+
+Layout make_layout(int method, int64_t T_max, int B, int scratch_units) {
     Layout L;
+    L.vsz = value_bytes(method);
     L.W_max = 2 * T_max + 1;
     L.N_max = (int64_t)1 << ilog2_ceil(L.W_max);
-    L.lg_nsmem = (method == AOP_FFT_FP64) ? 11 : 12;   // 32 KiB of shared memory
-    L.tw_log2 = max(ilog2_ceil(L.N_max), L.lg_nsmem + 1);
-    const int64_t vsz = (method == AOP_FFT_FP64) ? 16 : 8;
-    const int64_t ssz = 16;
-    // one spectrum holds at most N/2 + 1 bins: the arena always fits the largest
+    L.lg_tile = (L.vsz == 8) ? 10 : 9;       // 8 KiB per worker tile
+    L.lg_block = (L.vsz == 8) ? 12 : 11;     // 32 KiB block tile (linear advance entry points)
+    L.tw_log2 = std::max(ilog2_ceil(L.N_max), L.lg_block + 1);
     L.spec_cap = std::max<int64_t>(1 << 17, L.N_max / 2 + 2);
     int64_t off = 0;
     L.off_r0 = off;
@@ -825,10 +1177,12 @@ Layout make_layout(int method, int64_t T_max, int B) {
     }
     off += (m * 8 + 255) & ~255ll;
     L.off_scr = off;
-    off += (L.N_max * vsz + 255) & ~255ll;
+    L.scr_stride = (L.N_max * L.vsz + 255) & ~255ll;
+    off += L.scr_stride * scratch_units;
     L.off_spec = off;
-    off += (L.spec_cap * ssz + 255) & ~255ll;
+    off += (L.spec_cap * 16 + 255) & ~255ll;
     L.stride = off;
+    L.smem = 3 * kNaiveCap * sizeof(double) + (size_t)kWorkers * ((size_t)L.vsz << L.lg_tile);
     return L;
 }
 
@@ -844,15 +1198,34 @@ int sm_count(int device) {
     return g_sms_cache[device];
 }
 
+template <int MODE>
+int resident_ctas(size_t smem) {
+    int per_sm = 0;
+    cudaFuncSetAttribute(dnc_kernel<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, dnc_kernel<MODE>, kThreadsD, smem) != cudaSuccess) {
+        cudaGetLastError();
+        per_sm = 2;
+    }
+    return std::max(1, per_sm);
+}
+
+int ctas_per_sm(int method, size_t smem) {
+    switch (method) {
+    case AOP_FFT_FP64: return resident_ctas<0>(smem);
+    case AOP_FFT_FP32SPLIT: return resident_ctas<1>(smem);
+    default: return resident_ctas<2>(smem);
+    }
+}
+
 }  // namespace
 
 size_t dnc_workspace_bytes(int method, int64_t n, int64_t T_max, int base_case, int *grid_out, int device)
 {
-    Layout L = make_layout(method, T_max, base_case);
-    int64_t grid = std::min<int64_t>(n, (int64_t)sm_count(device) * 4);
+    Layout L = make_layout(method, T_max, base_case, kBigWorkers);
+    int64_t grid = std::min<int64_t>(n, (int64_t)sm_count(device) * ctas_per_sm(method, L.smem));
     if (grid < 1) grid = 1;
     if (grid_out) *grid_out = (int)grid;
-    return (size_t)(grid * L.stride + 4096);
+    return (size_t)(grid * L.stride + 8192);
 }
 
 cudaError_t run_dnc(int method, int64_t n, const Params *d_params, int64_t T_max, int base_case,
@@ -861,23 +1234,25 @@ cudaError_t run_dnc(int method, int64_t n, const Params *d_params, int64_t T_max
                     aop_stats *d_stats, int *d_err, int64_t *d_opt_ns, int device, cudaStream_t s)
 {
     if (n == 0) return cudaSuccess;
-    Layout L = make_layout(method, T_max, base_case);
+    Layout L = make_layout(method, T_max, base_case, kBigWorkers);
     if (tw_log2 < L.tw_log2) return cudaErrorInvalidValue;
-    int64_t grid = std::min<int64_t>(n, (int64_t)sm_count(device) * 4);
-    // the queue counter lives at the end of the workspace
-    const size_t need = (size_t)(grid * L.stride) + 4096;
+    int64_t grid = std::min<int64_t>(n, (int64_t)sm_count(device) * ctas_per_sm(method, L.smem));
+    const size_t need = (size_t)(grid * L.stride) + 8192;
     if (ws_bytes < need) {
-        grid = (int64_t)((ws_bytes - 4096) / L.stride);
+        grid = (int64_t)((ws_bytes - 8192) / L.stride);
         if (grid < 1) return cudaErrorMemoryAllocation;
     }
     char *base = (char *)ws;
     int *queue = (int *)(base + grid * L.stride);
-    cudaMemsetAsync(queue, 0, sizeof(int), s);
+    int *sm_slots = queue + 1;
+    cudaMemsetAsync(queue, 0, 8192, s);
     DncArgs a;
+    memset(&a, 0, sizeof(a));
     a.params = d_params;
     a.n = n;
     a.B = base_case;
-    a.lg_nsmem = L.lg_nsmem;
+    a.lg_tile = L.lg_tile;
+    a.lg_block = L.lg_block;
     a.W_max = L.W_max;
     a.ws = base;
     a.ws_stride = L.stride;
@@ -885,6 +1260,7 @@ cudaError_t run_dnc(int method, int64_t n, const Params *d_params, int64_t T_max
     a.off_mid = L.off_mid;
     a.off_scr = L.off_scr;
     a.off_spec = L.off_spec;
+    a.scr_stride = L.scr_stride;
     for (int d = 0; d < kMaxDepth; d++) a.mid_off[d] = L.mid_off[d];
     a.spec_cap = L.spec_cap;
     a.tw = d_tw;
@@ -894,16 +1270,20 @@ cudaError_t run_dnc(int method, int64_t n, const Params *d_params, int64_t T_max
     a.bnd = d_bnd;
     a.bnd_off = d_bnd_off;
     a.queue = queue;
+    a.sm_slots = sm_slots;
     a.err = d_err;
     a.stats = d_stats;
     a.opt_ns = d_opt_ns;
-    const size_t smem = (size_t)((method == AOP_FFT_FP64) ? 16 : 8) << L.lg_nsmem;
-    if (method == AOP_FFT_FP64) {
-        cudaFuncSetAttribute(dnc_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        dnc_kernel<0><<<(unsigned)grid, kThreadsD, smem, s>>>(a);
-    } else {
-        cudaFuncSetAttribute(dnc_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        dnc_kernel<1><<<(unsigned)grid, kThreadsD, smem, s>>>(a);
+    switch (method) {
+    case AOP_FFT_FP64:
+        dnc_kernel<0><<<(unsigned)grid, kThreadsD, L.smem, s>>>(a);
+        break;
+    case AOP_FFT_FP32SPLIT:
+        dnc_kernel<1><<<(unsigned)grid, kThreadsD, L.smem, s>>>(a);
+        break;
+    default:
+        dnc_kernel<2><<<(unsigned)grid, kThreadsD, L.smem, s>>>(a);
+        break;
     }
     return cudaGetLastError();
 }
@@ -912,48 +1292,48 @@ cudaError_t run_dnc(int method, int64_t n, const Params *d_params, int64_t T_max
 namespace {
 
 template <int MODE>
-__global__ void __launch_bounds__(kThreadsD) advance_kernel(const __grid_constant__ DncArgs a, const __grid_constant__ Params P0, int64_t count,
-                                                            int64_t W, int64_t h, const double *in,
-                                                            double *out)
+__global__ void __launch_bounds__(kThreadsD) advance_kernel(const __grid_constant__ DncArgs a,
+                                                            const __grid_constant__ Params P0, int64_t count,
+                                                            int64_t W, int64_t h, const double *in, double *out)
 {
     using V = typename fft::Cx<MODE>::V;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    __shared__ ExpTables E;
-    __shared__ SpecEntry cache[kSpecSlots];
-    __shared__ int ncache;
-    __shared__ int64_t arena_used;
-    V *sm = (V *)smem_raw;
+    __shared__ Shared S;
+    V *tile = (V *)smem_raw;
     char *slot = a.ws + (int64_t)blockIdx.x * a.ws_stride;
-    Counters cnt{0, 0, 0, 0, 0, 0, 0};
-    if (threadIdx.x == 0) { ncache = 0; arena_used = 0; }
+    Cta<MODE> c(a, S, slot);
+    Counters cnt{};
+    if (threadIdx.x == 0) {
+        S.P = P0;
+        S.spec_n = 0;
+        S.spec_lock = 0;
+        S.arena_used = 0;
+        S.err = 0;
+    }
     __syncthreads();
     const int64_t nout = W - (int64_t)(P0.nw - 1) * h;
     for (int64_t s = blockIdx.x; s < count; s += gridDim.x) {
-        Dnc<MODE> d(a, P0, E, sm, slot, cache, &ncache, &arena_used, nullptr, cnt);
         Buf bi{const_cast<double *>(in) + s * W, 0};
         Buf bo{out + s * nout, 0};
-        d.conv(bi, 0, W - 1, bo, h);
+        c.template conv<fft::BlockGroup, StoreF64<MODE>>(bi, 0, W - 1, bo, h, tile, a.lg_block, c.scratch(0), cnt);
     }
 }
 
-}  // namespace
-
-size_t linear_advance_workspace_bytes(int method, int64_t W, int64_t h)
-{
-    (void)h;
-    Layout L = make_layout(method, (W + 1) / 2 + 1, 16);
-    return (size_t)(L.stride * 64 + 4096);
+template <int MODE>
+void launch_advance(const DncArgs &a, const Params &P, int64_t grid, size_t smem, int64_t count, int64_t W,
+                    int64_t h, const double *d_in, double *d_out, cudaStream_t s) {
+    cudaFuncSetAttribute(advance_kernel<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    advance_kernel<MODE><<<(unsigned)grid, kThreadsD, smem, s>>>(a, P, count, W, h, d_in, d_out);
 }
 
-cudaError_t run_linear_advance(int method, int nw, const double *w, int64_t count, int64_t W, int64_t h,
-                               const double *d_in, double *d_out, const void *d_tw, int tw_log2,
-                               void *ws, size_t ws_bytes, int *d_err, cudaStream_t s)
-{
-    Layout L = make_layout(method, (W + 1) / 2 + 1, 16);
-    int64_t grid = std::min<int64_t>(count, 64);
-    if ((size_t)(grid * L.stride) > ws_bytes) grid = (int64_t)(ws_bytes / L.stride);
-    if (grid < 1) return cudaErrorMemoryAllocation;
-    if (tw_log2 < L.tw_log2) return cudaErrorInvalidValue;
+void launch_advance_any(int method, const DncArgs &a, const Params &P, int64_t grid, size_t smem, int64_t count,
+                        int64_t W, int64_t h, const double *d_in, double *d_out, cudaStream_t s) {
+    if (method == AOP_FFT_FP64) launch_advance<0>(a, P, grid, smem, count, W, h, d_in, d_out, s);
+    else if (method == AOP_FFT_FP32SPLIT) launch_advance<1>(a, P, grid, smem, count, W, h, d_in, d_out, s);
+    else launch_advance<2>(a, P, grid, smem, count, W, h, d_in, d_out, s);
+}
+
+Params advance_params(int nw, const double *w) {
     Params P;
     memset(&P, 0, sizeof(P));
     P.model = AOP_BINOMIAL_CALL;
@@ -962,26 +1342,44 @@ cudaError_t run_linear_advance(int method, int nw, const double *w, int64_t coun
     P.o_min = 0;
     P.w[0] = w[0]; P.w[1] = w[1]; P.w[2] = nw == 3 ? w[2] : 0.0;
     P.wsum = P.w[0] + P.w[1] + P.w[2];
+    return P;
+}
+
+}  // namespace
+
+size_t linear_advance_workspace_bytes(int method, int64_t W, int64_t h)
+{
+    (void)h;
+    Layout L = make_layout(method, (W + 1) / 2 + 1, 16, 1);
+    return (size_t)(L.stride * 64 + 4096);
+}
+
+cudaError_t run_linear_advance(int method, int nw, const double *w, int64_t count, int64_t W, int64_t h,
+                               const double *d_in, double *d_out, const void *d_tw, int tw_log2,
+                               void *ws, size_t ws_bytes, int *d_err, cudaStream_t s)
+{
+    Layout L = make_layout(method, (W + 1) / 2 + 1, 16, 1);
+    int64_t grid = std::min<int64_t>(count, 64);
+    if ((size_t)(grid * L.stride) > ws_bytes) grid = (int64_t)(ws_bytes / L.stride);
+    if (grid < 1) return cudaErrorMemoryAllocation;
+    if (tw_log2 < L.tw_log2) return cudaErrorInvalidValue;
+    Params P = advance_params(nw, w);
     DncArgs a;
     memset(&a, 0, sizeof(a));
     a.B = 16;
-    a.lg_nsmem = L.lg_nsmem;
+    a.lg_tile = L.lg_tile;
+    a.lg_block = L.lg_block;
     a.W_max = L.W_max;
     a.ws = (char *)ws;
     a.ws_stride = L.stride;
     a.off_r0 = L.off_r0; a.off_mid = L.off_mid; a.off_scr = L.off_scr; a.off_spec = L.off_spec;
+    a.scr_stride = L.scr_stride;
     a.spec_cap = L.spec_cap;
     a.tw = d_tw;
     a.tw_log2 = tw_log2;
     a.err = d_err;
-    const size_t smem = (size_t)((method == AOP_FFT_FP64) ? 16 : 8) << L.lg_nsmem;
-    if (method == AOP_FFT_FP64) {
-        cudaFuncSetAttribute(advance_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        advance_kernel<0><<<(unsigned)grid, kThreadsD, smem, s>>>(a, P, count, W, h, d_in, d_out);
-    } else {
-        cudaFuncSetAttribute(advance_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        advance_kernel<1><<<(unsigned)grid, kThreadsD, smem, s>>>(a, P, count, W, h, d_in, d_out);
-    }
+    const size_t smem = (size_t)L.vsz << L.lg_block;
+    launch_advance_any(method, a, P, grid, smem, count, W, h, d_in, d_out, s);
     return cudaGetLastError();
 }
 
@@ -1000,7 +1398,7 @@ constexpr int64_t kNoAllocNmax = AOP_NOALLOC_MAX_W;     // largest transform len
 constexpr int kNoAllocCtas = 16;
 constexpr int kNoAllocTwLog2 = 15;                      // twiddles for N <= 2^15
 constexpr int64_t kNoAllocSpec = kNoAllocNmax / 2 + 2;  // one kernel power per call
-constexpr int64_t kNoAllocStride = kNoAllocNmax * 16 + kNoAllocSpec * 16;   // FP64 worst case
+constexpr int64_t kNoAllocStride = kNoAllocNmax * 16 + kNoAllocSpec * 16;   // 16-byte values, worst case
 constexpr int64_t kNoAllocTwEntries = (int64_t)1 << (kNoAllocTwLog2 - 1);
 constexpr int64_t kNoAllocTw32Off = kNoAllocCtas * kNoAllocStride;
 constexpr int64_t kNoAllocTw64Off = kNoAllocTw32Off + kNoAllocTwEntries * 16;
@@ -1054,36 +1452,25 @@ extern "C" aop_status aop_linear_advance_noalloc(int method, int nw, const doubl
         }
         base = D.base;
     }
-    Params P;
-    memset(&P, 0, sizeof(P));
-    P.model = AOP_BINOMIAL_CALL;
-    P.nw = nw;
-    P.D = nw - 1;
-    P.o_min = 0;
-    P.w[0] = w[0]; P.w[1] = w[1]; P.w[2] = nw == 3 ? w[2] : 0.0;
-    P.wsum = P.w[0] + P.w[1] + P.w[2];
+    Params P = advance_params(nw, w);
     DncArgs a;
     memset(&a, 0, sizeof(a));
     a.B = 16;
-    a.lg_nsmem = (method == AOP_FFT_FP64) ? 11 : 12;
+    a.lg_block = (method == AOP_FFT_FP64) ? 11 : 12;
+    a.lg_tile = a.lg_block;
     a.W_max = kNoAllocMaxW;
     a.ws = base;
     a.ws_stride = kNoAllocStride;
     a.off_scr = 0;
+    a.scr_stride = kNoAllocNmax * 16;
     a.off_spec = kNoAllocNmax * 16;
     a.spec_cap = kNoAllocSpec;
     a.tw = base + ((method == AOP_FFT_FP64) ? kNoAllocTw64Off : kNoAllocTw32Off);
     a.tw_log2 = kNoAllocTwLog2;
     a.err = nullptr;
     const int64_t grid = std::min<int64_t>(count, kNoAllocCtas);
-    const size_t smem = (size_t)((method == AOP_FFT_FP64) ? 16 : 8) << a.lg_nsmem;
-    if (method == AOP_FFT_FP64) {
-        cudaFuncSetAttribute(advance_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        advance_kernel<0><<<(unsigned)grid, kThreadsD, smem, s>>>(a, P, count, W, h, d_in, d_out);
-    } else {
-        cudaFuncSetAttribute(advance_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        advance_kernel<1><<<(unsigned)grid, kThreadsD, smem, s>>>(a, P, count, W, h, d_in, d_out);
-    }
+    const size_t smem = (size_t)((method == AOP_FFT_FP64) ? 16 : 8) << a.lg_block;
+    launch_advance_any(method, a, P, grid, smem, count, W, h, d_in, d_out, s);
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? AOP_OK : AOP_ECUDA;
 }

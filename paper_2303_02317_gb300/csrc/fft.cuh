@@ -12,13 +12,21 @@
 // decimation-in-time pass (bit-reversed in, natural out), so no reordering pass
 // is ever made.  Outputs whose correlation window wraps around are discarded.
 //
-// Two arithmetic modes:
+// Arithmetic modes:
 //   MODE 0: FP64 complex values (double2), FP64 twiddles.
 //   MODE 1: FP32 complex values (float2) carrying hi + i*lo of the FP64 input
 //           (hi = fl32(x), lo = fl32(x - hi)); because the stencil power is
 //           real, the real part of the result is conv(hi) and the imaginary
 //           part conv(lo).  Twiddles and the kernel power are FP32 hi/lo pairs
 //           applied with a compensated product.
+//   MODE 2: double-float ("FP32 x 2") complex values: each component is an
+//           unevaluated sum hi + lo of two FP32 numbers, added and multiplied
+//           with error-free transformations (two-sum, two-product via FMA), so
+//           the transform runs on the FP32 pipe with ~48-bit significands.
+//
+// Stage functions run on a thread group G (a warp or the whole block): G::rank()
+// and G::size() give the thread's index and the group size, G::sync() the
+// barrier between stages.
 #pragma once
 
 #include <cstdint>
@@ -27,20 +35,80 @@
 namespace aop {
 namespace fft {
 
+struct BlockGroup {
+    __device__ static int rank() { return threadIdx.x; }
+    __device__ static int size() { return blockDim.x; }
+    __device__ static void sync() { __syncthreads(); }
+};
+struct WarpGroup {
+    __device__ static int rank() { return threadIdx.x & 31; }
+    __device__ static int size() { return 32; }
+    __device__ static void sync() { __syncwarp(); }
+};
+
+// double-float complex: x = re_hi, y = im_hi, z = re_lo, w = im_lo
+struct df2 {
+    float4 v;
+};
+
 template <int MODE> struct Cx;
 template <> struct Cx<0> { using V = double2; using Tw = double2; using Sp = double2; };
 template <> struct Cx<1> { using V = float2;  using Tw = float4;  using Sp = float4; };
+template <> struct Cx<2> { using V = df2;     using Tw = float4;  using Sp = float4; };
+
+// ------------------------------------------------------- double-float ops
+// two-sum: s + e == a + b exactly
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
+    s = a + b;
+    float bb = s - a;
+    e = (a - (s - bb)) + (b - bb);
+}
+// fast two-sum, |a| >= |b|
+__device__ __forceinline__ void fast_two_sum(float a, float b, float &s, float &e) {
+    s = a + b;
+    e = b - (s - a);
+}
+// (ah + al) + (bh + bl) with the low parts summed before renormalising; the
+// error is a few units of 2^-48 of |a| + |b|
+__device__ __forceinline__ void df_add(float ah, float al, float bh, float bl, float &rh, float &rl) {
+    float s, e;
+    two_sum(ah, bh, s, e);
+    e += al + bl;
+    fast_two_sum(s, e, rh, rl);
+}
+// (ah + al) * (bh + bl): exact high product through FMA, cross terms added
+__device__ __forceinline__ void df_mul(float ah, float al, float bh, float bl, float &rh, float &rl) {
+    float p = ah * bh;
+    float e = fmaf(ah, bh, -p);
+    e = fmaf(ah, bl, e);
+    e = fmaf(al, bh, e);
+    fast_two_sum(p, e, rh, rl);
+}
 
 // ------------------------------------------------------------- complex ops
 __device__ __forceinline__ double2 cadd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
 __device__ __forceinline__ double2 csub(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
 __device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
 __device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ df2 cadd(df2 a, df2 b) {
+    df2 r;
+    df_add(a.v.x, a.v.z, b.v.x, b.v.z, r.v.x, r.v.z);
+    df_add(a.v.y, a.v.w, b.v.y, b.v.w, r.v.y, r.v.w);
+    return r;
+}
+__device__ __forceinline__ df2 csub(df2 a, df2 b) {
+    df2 r;
+    df_add(a.v.x, a.v.z, -b.v.x, -b.v.z, r.v.x, r.v.z);
+    df_add(a.v.y, a.v.w, -b.v.y, -b.v.w, r.v.y, r.v.w);
+    return r;
+}
 // multiply by -i and by +i
 __device__ __forceinline__ double2 cmul_mi(double2 a) { return make_double2(a.y, -a.x); }
 __device__ __forceinline__ double2 cmul_pi(double2 a) { return make_double2(-a.y, a.x); }
 __device__ __forceinline__ float2 cmul_mi(float2 a) { return make_float2(a.y, -a.x); }
 __device__ __forceinline__ float2 cmul_pi(float2 a) { return make_float2(-a.y, a.x); }
+__device__ __forceinline__ df2 cmul_mi(df2 a) { df2 r; r.v = make_float4(a.v.y, -a.v.x, a.v.w, -a.v.z); return r; }
+__device__ __forceinline__ df2 cmul_pi(df2 a) { df2 r; r.v = make_float4(-a.v.y, a.v.x, -a.v.w, a.v.z); return r; }
 
 // v * w (CONJ: v * conj(w))
 template <bool CONJ>
@@ -60,6 +128,21 @@ __device__ __forceinline__ float2 twmul(float2 v, float4 w) {
     float im = fmaf(v.x, sh, fmaf(v.y, w.x, im_lo));
     return make_float2(re, im);
 }
+// double-float complex product with a double-float twiddle (hi.x, hi.y, lo.x, lo.y)
+template <bool CONJ>
+__device__ __forceinline__ df2 twmul(df2 v, float4 w) {
+    const float ch = w.x, cl = w.z;
+    const float sh = CONJ ? -w.y : w.y, sl = CONJ ? -w.w : w.w;
+    float a_h, a_l, b_h, b_l, c_h, c_l, d_h, d_l;
+    df_mul(v.v.x, v.v.z, ch, cl, a_h, a_l);   // re * c
+    df_mul(v.v.y, v.v.w, sh, sl, b_h, b_l);   // im * s
+    df_mul(v.v.x, v.v.z, sh, sl, c_h, c_l);   // re * s
+    df_mul(v.v.y, v.v.w, ch, cl, d_h, d_l);   // im * c
+    df2 r;
+    df_add(a_h, a_l, -b_h, -b_l, r.v.x, r.v.z);
+    df_add(c_h, c_l, d_h, d_l, r.v.y, r.v.w);
+    return r;
+}
 
 // Twiddle e^{-2 pi i k / 2^lg} for 0 <= k < 2^(lg-1) from the table of the
 // largest transform 2^tw_log2 (entries k' < 2^(tw_log2-1)).
@@ -73,15 +156,32 @@ __device__ __forceinline__ uint32_t brev_n(uint32_t p, int lgN) {
     return lgN == 0 ? 0u : (__brev(p) >> (32 - lgN));
 }
 
-// --------------------------------------------------- in-place stage kernels
-// All threads of the block (nthr = blockDim.x) cooperate; x is N values in
-// shared or global memory.  Caller synchronises between calls.
+// ------------------------------------------- asynchronous global->shared copy
+// cp.async with a source size: bytes past src_bytes are zero-filled, so the
+// zero padding of a transform costs no global read.  Every copy of a tile is
+// in flight at once; cp_async_wait() waits for this thread's copies.
+template <int BYTES>
+__device__ __forceinline__ void cp_async(void *smem_dst, const void *gmem_src, int src_bytes) {
+    const uint32_t s = (uint32_t)__cvta_generic_to_shared(smem_dst);
+    if constexpr (BYTES == 16) {
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(s), "l"(gmem_src), "r"(src_bytes)
+                     : "memory");
+    } else {
+        asm volatile("cp.async.ca.shared.global [%0], [%1], %2, %3;" ::"r"(s), "l"(gmem_src), "n"(BYTES),
+                     "r"(src_bytes)
+                     : "memory");
+    }
+}
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
-// one radix-2 DIF stage of half-size M
-template <int MODE, class V>
+// --------------------------------------------------- in-place stage kernels
+// The group G cooperates on the N values of x (shared or global memory); the
+// caller synchronises the group between calls.
+
+template <int MODE, class G, class V>
 __device__ __forceinline__ void dif2(V *x, int64_t N, int64_t M, const typename Cx<MODE>::Tw *tw,
                                      int tw_log2, int lgM2) {
-    for (int64_t t = threadIdx.x; t < N / 2; t += blockDim.x) {
+    for (int64_t t = G::rank(); t < N / 2; t += G::size()) {
         int64_t k = t & (M - 1);
         int64_t j = ((t - k) << 1) + k;
         V u = x[j], v = x[j + M];
@@ -89,11 +189,10 @@ __device__ __forceinline__ void dif2(V *x, int64_t N, int64_t M, const typename 
         x[j + M] = twmul<false>(csub(u, v), tw_get<MODE>(tw, tw_log2, k, lgM2));
     }
 }
-// one radix-2 DIT (inverse) stage of half-size M
-template <int MODE, class V>
+template <int MODE, class G, class V>
 __device__ __forceinline__ void dit2(V *x, int64_t N, int64_t M, const typename Cx<MODE>::Tw *tw,
                                      int tw_log2, int lgM2) {
-    for (int64_t t = threadIdx.x; t < N / 2; t += blockDim.x) {
+    for (int64_t t = G::rank(); t < N / 2; t += G::size()) {
         int64_t k = t & (M - 1);
         int64_t j = ((t - k) << 1) + k;
         V u = x[j];
@@ -103,11 +202,11 @@ __device__ __forceinline__ void dit2(V *x, int64_t N, int64_t M, const typename 
     }
 }
 // two DIF stages (half-sizes M and M/2) as one radix-4 pass, M >= 2
-template <int MODE, class V>
+template <int MODE, class G, class V>
 __device__ __forceinline__ void dif4(V *x, int64_t N, int64_t M, const typename Cx<MODE>::Tw *tw,
                                      int tw_log2, int lgM2) {
     const int64_t h = M >> 1;
-    for (int64_t t = threadIdx.x; t < N / 4; t += blockDim.x) {
+    for (int64_t t = G::rank(); t < N / 4; t += G::size()) {
         int64_t k = t & (h - 1);
         int64_t j = ((t - k) << 2) + k;
         V a0 = x[j], a1 = x[j + h], a2 = x[j + M], a3 = x[j + M + h];
@@ -122,11 +221,11 @@ __device__ __forceinline__ void dif4(V *x, int64_t N, int64_t M, const typename 
     }
 }
 // inverse of dif4 (up to the factor 4)
-template <int MODE, class V>
+template <int MODE, class G, class V>
 __device__ __forceinline__ void dit4(V *x, int64_t N, int64_t M, const typename Cx<MODE>::Tw *tw,
                                      int tw_log2, int lgM2) {
     const int64_t h = M >> 1;
-    for (int64_t t = threadIdx.x; t < N / 4; t += blockDim.x) {
+    for (int64_t t = G::rank(); t < N / 4; t += G::size()) {
         int64_t k = t & (h - 1);
         int64_t j = ((t - k) << 2) + k;
         V c0 = x[j], c1 = x[j + h], c2 = x[j + M], c3 = x[j + M + h];
@@ -145,38 +244,104 @@ __device__ __forceinline__ void dit4(V *x, int64_t N, int64_t M, const typename 
     }
 }
 
-// Forward DIF stages with half-sizes from Mhi down to Mlo (powers of two,
-// Mhi >= Mlo >= 1) over N values, synchronising the block after each pass.
-template <int MODE, class V>
+// Forward DIF stages with half-sizes from 2^lgMhi down to 2^lgMlo, with a group
+// barrier after each pass.
+template <int MODE, class G, class V>
 __device__ void dif_range(V *x, int64_t N, int lgMhi, int lgMlo, const typename Cx<MODE>::Tw *tw,
                           int tw_log2) {
     int lg = lgMhi;
     if (((lgMhi - lgMlo + 1) & 1) != 0) {   // odd number of stages: one radix-2 first
-        dif2<MODE>(x, N, (int64_t)1 << lg, tw, tw_log2, lg + 1);
-        __syncthreads();
+        dif2<MODE, G>(x, N, (int64_t)1 << lg, tw, tw_log2, lg + 1);
+        G::sync();
         lg--;
     }
     for (; lg > lgMlo; lg -= 2) {
-        dif4<MODE>(x, N, (int64_t)1 << lg, tw, tw_log2, lg + 1);
-        __syncthreads();
+        dif4<MODE, G>(x, N, (int64_t)1 << lg, tw, tw_log2, lg + 1);
+        G::sync();
     }
 }
-// Inverse DIT stages with half-sizes from Mlo up to Mhi.
-template <int MODE, class V>
+// Inverse DIT stages with half-sizes from 2^lgMlo up to 2^lgMhi.
+template <int MODE, class G, class V>
 __device__ void dit_range(V *x, int64_t N, int lgMlo, int lgMhi, const typename Cx<MODE>::Tw *tw,
                           int tw_log2) {
     int lg = lgMlo;
-    // radix-4 pairs (lg, lg+1) first: the pair's stage order is h = 2^lg then 2^(lg+1)
     const int nst = lgMhi - lgMlo + 1;
     const int pairs = nst / 2;
     for (int p = 0; p < pairs; p++, lg += 2) {
-        dit4<MODE>(x, N, (int64_t)1 << (lg + 1), tw, tw_log2, lg + 2);
-        __syncthreads();
+        dit4<MODE, G>(x, N, (int64_t)1 << (lg + 1), tw, tw_log2, lg + 2);
+        G::sync();
     }
     if (nst & 1) {
-        dit2<MODE>(x, N, (int64_t)1 << lg, tw, tw_log2, lg + 1);
-        __syncthreads();
+        dit2<MODE, G>(x, N, (int64_t)1 << lg, tw, tw_log2, lg + 1);
+        G::sync();
     }
+}
+
+// ------------------------------------------------- value conversions by mode
+template <int MODE> __device__ __forceinline__ typename Cx<MODE>::V load_split(double x);
+template <> __device__ __forceinline__ double2 load_split<0>(double x) { return make_double2(x, 0.0); }
+template <> __device__ __forceinline__ float2 load_split<1>(double x) {
+    float hi = (float)x;
+    return make_float2(hi, (float)(x - (double)hi));
+}
+template <> __device__ __forceinline__ df2 load_split<2>(double x) {
+    float hi = (float)x;
+    df2 r;
+    r.v = make_float4(hi, 0.f, (float)(x - (double)hi), 0.f);
+    return r;
+}
+__device__ __forceinline__ double unsplit(double2 v, double invN) { return v.x * invN; }
+__device__ __forceinline__ double unsplit(float2 v, double invN) { return ((double)v.x + (double)v.y) * invN; }
+__device__ __forceinline__ double unsplit(df2 v, double invN) { return ((double)v.v.x + (double)v.v.z) * invN; }
+
+// ----------------------------------------------------- stored row values
+// Row values between transforms.  MODE 0 stores FP64.  MODES 1 and 2 store
+// an unevaluated pair of FP32 numbers (value = hi + lo, ~48 significant bits):
+// a transform then reads and writes FP32 only, so the convolution path issues
+// no FP64 instruction (on GB300 an FP64 instruction occupies the sub-partition's
+// FP64 unit for ~64 cycles and would stall the FP64 base cases beside it).
+template <int MODE> struct CellT { using T = float2; };
+template <> struct CellT<0> { using T = double; };
+
+__device__ __forceinline__ double cell_value(double c) { return c; }
+__device__ __forceinline__ double cell_value(float2 c) { return (double)c.x + (double)c.y; }
+template <int MODE> __device__ __forceinline__ typename CellT<MODE>::T make_cell(double v);
+template <> __device__ __forceinline__ double make_cell<0>(double v) { return v; }
+template <> __device__ __forceinline__ float2 make_cell<1>(double v) {
+    float hi = (float)v;
+    return make_float2(hi, (float)(v - (double)hi));
+}
+template <> __device__ __forceinline__ float2 make_cell<2>(double v) { return make_cell<1>(v); }
+
+// cell -> transform value (moves only)
+__device__ __forceinline__ double2 cell_to_v(double c) { return make_double2(c, 0.0); }
+__device__ __forceinline__ float2 cell_to_v1(float2 c) { return c; }
+__device__ __forceinline__ df2 cell_to_v2(float2 c) { df2 r; r.v = make_float4(c.x, 0.f, c.y, 0.f); return r; }
+// transform value -> cell, scaled by 1/N (a power of two: exact in FP32)
+__device__ __forceinline__ double v_to_cell(double2 v, double invN) { return v.x * invN; }
+__device__ __forceinline__ float2 v_to_cell(float2 v, double invN) {
+    const float s = (float)invN;
+    return make_float2(v.x * s, v.y * s);
+}
+__device__ __forceinline__ float2 v_to_cell(df2 v, double invN) {
+    const float s = (float)invN;
+    return make_float2(v.v.x * s, v.v.z * s);
+}
+
+template <class V> __device__ __forceinline__ V czero();
+template <> __device__ __forceinline__ double2 czero<double2>() { return make_double2(0.0, 0.0); }
+template <> __device__ __forceinline__ float2 czero<float2>() { return make_float2(0.f, 0.f); }
+template <> __device__ __forceinline__ df2 czero<df2>() { df2 r; r.v = make_float4(0.f, 0.f, 0.f, 0.f); return r; }
+
+// Kernel power entry for a bin from the band-limited half spectrum sp[0..mc]
+// (entries beyond the band are zero; the upper half is the conjugate mirror).
+template <int MODE>
+__device__ __forceinline__ typename Cx<MODE>::V spec_mul(typename Cx<MODE>::V z, const typename Cx<MODE>::Sp *sp,
+                                                         int mc, uint32_t m, uint32_t N) {
+    uint32_t mm = (m <= N / 2) ? m : N - m;
+    if ((int)mm > mc) return czero<typename Cx<MODE>::V>();
+    typename Cx<MODE>::Sp s = sp[mm];
+    return (m <= N / 2) ? twmul<false>(z, s) : twmul<true>(z, s);
 }
 
 }  // namespace fft

@@ -33,7 +33,7 @@ CASES = [
 ]
 
 
-@pytest.mark.parametrize("method", [aop.FFT_FP64, aop.FFT_FP32SPLIT], ids=["fft64", "fft32"])
+@pytest.mark.parametrize("method", [aop.FFT_FP64, aop.FFT_FP32SPLIT, aop.FFT_DF32], ids=["fft64", "fft32", "df32"])
 @pytest.mark.parametrize("nw,W,h,count", CASES)
 def test_linear_advance(ctx, method, nw, W, h, count):
     rng = np.random.default_rng(W * 7 + h)

@@ -12,8 +12,8 @@ from tests import parity
 
 pytestmark = pytest.mark.gpu
 
-METHODS = [aop.FFT_FP64, aop.FFT_FP32SPLIT, aop.STENCIL_FP64]
-MNAME = {0: "fft64", 1: "fft32", 2: "stencil"}
+METHODS = [aop.FFT_FP64, aop.FFT_FP32SPLIT, aop.STENCIL_FP64, aop.FFT_DF32]
+MNAME = {0: "fft64", 1: "fft32", 2: "stencil", 3: "df32"}
 
 
 @pytest.fixture(scope="module")
@@ -75,7 +75,7 @@ def test_random_small(ctx, method):
         _check(r, method)
 
 
-@pytest.mark.parametrize("method", [aop.FFT_FP64, aop.FFT_FP32SPLIT], ids=["fft64", "fft32"])
+@pytest.mark.parametrize("method", [aop.FFT_FP64, aop.FFT_FP32SPLIT, aop.FFT_DF32], ids=["fft64", "fft32", "df32"])
 @pytest.mark.parametrize("B", [2, 8, 32, 64])
 def test_base_case_heights(ctx, method, B):
     """The trapezoid cut does not change the result (any base-case height)."""
