@@ -95,6 +95,11 @@ typedef struct aop_request {
 } aop_request;
 
 #define AOP_FLAG_OPTION_TIMES 1   /* record each option's device time (D&C methods) */
+/* FP32-split calls: the convolutions carry the values tilted by the node-price
+ * growth e^{-kappa x} when the exercise boundary lies far above the strike
+ * (automatic).  These two bits force the tilt off or on for every call. */
+#define AOP_FLAG_TILT_OFF 2
+#define AOP_FLAG_TILT_ON 4
 
 typedef struct aop_options {
     int32_t method;     /* aop_method */
@@ -128,6 +133,11 @@ typedef struct aop_stats {
     int64_t basecase_rows;      /* D&C: rows stepped by the naive base cases */
     int64_t walker_ns;          /* D&C: time from the first recursion step to the
                                    root price, summed over options */
+    int64_t spectrum_ns;        /* D&C: time spent evaluating kernel-power spectra
+                                   (FP64), summed over the building warps */
+    int64_t spectrum_bins;      /* D&C: kernel-power bins evaluated */
+    int64_t basecase_loop_cycles;  /* D&C: SM cycles in the call base cases' row loops */
+    int64_t basecase_fill_cycles;  /* D&C: SM cycles filling their exercise tables */
 } aop_stats;
 
 typedef struct aop_ctx aop_ctx;

@@ -58,7 +58,9 @@ class _Stats(ctypes.Structure):
         "basecase_cells", "stencil_cells", "global_fft_bytes")] + [("kernel_ms", ctypes.c_double)] + [
         ("walker_wait_ns", ctypes.c_int64), ("worker_busy_ns", ctypes.c_int64),
         ("walker_base_ns", ctypes.c_int64), ("basecase_calls", ctypes.c_int64),
-        ("basecase_rows", ctypes.c_int64), ("walker_ns", ctypes.c_int64)]
+        ("basecase_rows", ctypes.c_int64), ("walker_ns", ctypes.c_int64),
+        ("spectrum_ns", ctypes.c_int64), ("spectrum_bins", ctypes.c_int64),
+        ("basecase_loop_cycles", ctypes.c_int64), ("basecase_fill_cycles", ctypes.c_int64)]
 
 
 _lock = threading.Lock()
@@ -130,6 +132,8 @@ def _check(code: int, what: str = ""):
 
 
 FLAG_OPTION_TIMES = 1
+FLAG_TILT_OFF = 2
+FLAG_TILT_ON = 4
 
 
 def _opts(method: int, base_case: int = 0, flags: int = 0) -> _Options:

@@ -139,7 +139,8 @@ aop_status run_batch(aop_ctx *c, int64_t n, const aop_request *d_reqs, const aop
         }
         CK(cudaEventRecord(c->ev0, s));
         CK(run_dnc(method, n, d_params, T_max, B, c->ws, c->ws_size, tw, c->tw_log2, d_prices,
-                   d_status, d_bnd, d_bnd_off, c->d_stats, c->d_err, opt_ns, c->device, s));
+                   d_status, d_bnd, d_bnd_off, c->d_stats, c->d_err, opt_ns, opt ? opt->flags : 0,
+                   c->device, s));
         CK(cudaEventRecord(c->ev1, s));
     }
     c->timed = true;

@@ -34,6 +34,15 @@ struct Params {
     double S, K;
     double xbase;        // calls: ln S - T logu;  BSM: ln(S/K) - T ds
     double out_scale;    // 1 for the calls, K for the put (price = K v)
+    // Exponential tilt of the call stencil: a call value never exceeds its
+    // node price S u^k, which grows like e^{kappa x} along a row, so the
+    // FP32-split convolutions carry v(x) e^{-kappa x} (kept near the local
+    // scale of the node prices) with the tilted weights w_j e^{kappa j},
+    // normalised to unit sum: wt_j = w_j e^{kappa j} / e^{tL}.
+    double kappa;        // log growth of the node price per column (0: BSM)
+    double wt[3];
+    double wtsum;
+    double tL;           // log of the tilted weights' sum
 };
 static_assert(sizeof(Params) % 8 == 0, "Params alignment");
 
@@ -167,6 +176,15 @@ __device__ inline Params make_params(const aop_request &q) {
         P.out_scale = q.K;
     }
     P.wsum = P.w[0] + P.w[1] + P.w[2];
+    P.kappa = P.model == AOP_BINOMIAL_CALL ? 2.0 * P.logu : (P.model == AOP_TRINOMIAL_CALL ? P.logu : 0.0);
+    double ts = 0.0;
+    for (int j = 0; j < 3; j++) {
+        P.wt[j] = P.w[j] * exp(P.kappa * j);
+        ts += P.wt[j];
+    }
+    for (int j = 0; j < 3; j++) P.wt[j] /= ts;
+    P.wtsum = P.wt[0] + P.wt[1] + P.wt[2];
+    P.tL = log(ts);
     return P;
 }
 

@@ -41,6 +41,8 @@
 #include "fft.cuh"
 #include "internal.h"
 
+#include <type_traits>
+
 namespace aop {
 
 namespace {
@@ -50,8 +52,11 @@ constexpr int kThreadsD = 32 * kWarps;
 constexpr int kWorkers = kWarps - 1;
 constexpr int kBigWorkers = 2;             // workers 1, 2 may take multi-pass transforms
 constexpr int kSpecSlots = 128;
-constexpr int kLeftoverCall = 64;          // rows solved naively at the root
-constexpr int kNaiveCap = 512;             // doubles per walker row buffer
+constexpr int kLeftoverCall = 48;          // rows solved naively at the root
+constexpr int kMinCtasPerSm = 4;          // register budget: 4 options in flight per SM
+constexpr double kDfLogRange = 80.0;       // largest log price ratio of a doubled-FP32 base case
+constexpr int kRegCells = 288;             // widest base-case window: 9 registers per lane
+constexpr int kNaiveCap = 512;             // widest base-case window (cells) and exercise table
 constexpr uint64_t kWaitNs = 30ull * 1000000000ull;   // bound of every spin-wait (30 s)
 
 __device__ __forceinline__ uint64_t gtime() {
@@ -69,7 +74,30 @@ struct SpecEntry {
     int32_t mc;
     volatile int32_t state;
     int64_t off;
+    int64_t n0;           // tilted advances: output factor e^{-kappa (n - n0)} resid
+    float2 resid;
 };
+
+// Per-advance output scaling: 1/N (FP64 and FP32 copies, both exact powers
+// of two) and the tilt's output factor.
+struct ConvScale {
+    double d;
+    float f;
+    int64_t n0;
+    float2 resid;
+};
+
+// e^{g tL - kappa n0} with n0 = floor(g tL / kappa): the part of a g-step
+// tilted advance's output factor e^{g tL - kappa n} left after the table
+// factor e^{-kappa (n - n0)}; n >= D g > n0 for every output cell.
+__device__ inline void tilt_shift(const Params &P, int64_t g, int64_t &n0, float2 &resid) {
+    const double e = (double)g * P.tL;
+    const double q = floor(e / P.kappa);
+    n0 = (int64_t)q;
+    const double v = exp(e - P.kappa * q);
+    const float h = (float)v;
+    resid = make_float2(h, (float)(v - (double)h));
+}
 
 // a row segment in memory: the value of column x lives at p[x - base]
 struct Buf {
@@ -119,11 +147,12 @@ struct DncArgs {
     int *err;
     aop_stats *stats;
     int64_t *opt_ns;       // per-option device time (nullable)
+    int flags;             // AOP_FLAG_* bits
 };
 
 struct Counters {
     long long convs, fft_points, fft_flops, conv_in, conv_out, base_cells, gbytes, wait_ns, busy_ns, base_ns;
-    long long base_calls, base_rows, walker_ns;
+    long long base_calls, base_rows, walker_ns, spec_ns, spec_bins, loop_cyc, fill_cyc;
 };
 
 // Per-CTA shared state (static shared memory).
@@ -141,7 +170,33 @@ struct Shared {
     int bcast_i;
     long long bcast_l;
     double price;
+    // e^{+-kappa n} = t2[n >> 14] t1[(n >> 7) & 127] t0[n & 127] in doubled
+    // FP32 (FP32-split calls)
+    float2 tup0[128], tup1[128], tup2[256];
+    float2 tdn0[128], tdn1[128], tdn2[256];
+    int tilt_nmax;        // largest n with e^{kappa n} inside the float range
+    // doubled-FP32 copies for the base cases of the FP32 modes: u^j, j < kNaiveCap
+    float2 updf[kNaiveCap];
+    float2 wdf[3];
+    float2 kdf;
 };
+
+// Tilt tables of the current option (all threads of the block).
+__device__ void build_tilt_tables(Shared &S) {
+    const double kap = S.P.kappa;
+    for (int t = threadIdx.x; t < 1024; t += blockDim.x) {
+        const int dir = t >> 9, u = t & 511;
+        const int lvl = u < 128 ? 0 : (u < 256 ? 1 : 2);
+        const int j = lvl == 0 ? u : (lvl == 1 ? u - 128 : u - 256);
+        const double e = kap * (double)j * (double)(1 << (7 * lvl));
+        const double v = exp(dir ? -e : e);
+        const float h = (float)v;
+        float2 *tab = dir ? (lvl == 0 ? S.tdn0 : (lvl == 1 ? S.tdn1 : S.tdn2))
+                          : (lvl == 0 ? S.tup0 : (lvl == 1 ? S.tup1 : S.tup2));
+        tab[j] = isfinite(h) ? make_float2(h, (float)(v - (double)h)) : make_float2(h, 0.0f);
+    }
+    if (threadIdx.x == 0) S.tilt_nmax = (int)fmin(87.0 / kap, (double)((1 << 22) - 1));
+}
 
 // ---------------------------------------------------------------- groups
 template <class G> __device__ __forceinline__ int bcast_int(Shared &S, int v);
@@ -158,9 +213,11 @@ template <> __device__ __forceinline__ int bcast_int<fft::BlockGroup>(Shared &S,
 template <class G> __device__ __forceinline__ bool leader() { return G::rank() == 0; }
 
 // ------------------------------------------------------------ kernel power
-__device__ int band_mc(const Params &P, int64_t g, int64_t N) {
-    const double w0 = P.w[0], w1 = P.w[1], w2 = P.w[2];
-    double kap = 4.0 * (w0 * w1 + (P.nw == 3 ? w1 * w2 : 0.0)) / (P.wsum * P.wsum);
+__device__ int band_mc(const Params &P, int64_t g, int64_t N, bool tilt) {
+    const double *w = tilt ? P.wt : P.w;
+    const double wsum = tilt ? P.wtsum : P.wsum;
+    const double w0 = w[0], w1 = w[1], w2 = w[2];
+    double kap = 4.0 * (w0 * w1 + (P.nw == 3 ? w1 * w2 : 0.0)) / (wsum * wsum);
     double need = 83.2 / ((double)g * kap);
     if (!(kap > 0) || need >= 1.0) return (int)(N / 2);
     double th2 = asin(sqrt(need));               // theta_c / 2
@@ -170,10 +227,12 @@ __device__ int band_mc(const Params &P, int64_t g, int64_t N) {
 
 // s(theta_m)^g in FP64: magnitude through log1p of the exactly formed
 // 1 - |s/s(0)|^2, phase g * arg s reduced in units of pi.
-__device__ double2 bin_value(const Params &P, int64_t g, int lgN, int64_t m) {
+__device__ double2 bin_value(const Params &P, int64_t g, int lgN, int64_t m, bool tilt) {
     const double N = (double)((int64_t)1 << lgN);
-    const double w0 = P.w[0], w1 = P.w[1], w2 = P.w[2];
-    const double inv2 = 1.0 / (P.wsum * P.wsum);
+    const double *w = tilt ? P.wt : P.w;
+    const double wsum = tilt ? P.wtsum : P.wsum;
+    const double w0 = w[0], w1 = w[1], w2 = w[2];
+    const double inv2 = 1.0 / (wsum * wsum);
     const double gd = (double)g;
     double sh, ch;
     sincospi((double)m / N, &sh, &ch);
@@ -196,7 +255,7 @@ __device__ double2 bin_value(const Params &P, int64_t g, int lgN, int64_t m) {
     // 1 - |s/s(0)|^2 lies in [0, 1]; rounding can step outside when |s(pi)|
     // vanishes (e.g. p = 1/2), where the power is zero anyway
     dl = fmin(fmax(dl, 0.0), 1.0);
-    double lm = (dl >= 1.0) ? -INFINITY : gd * (log(P.wsum) + 0.5 * log1p(-dl));
+    double lm = (dl >= 1.0) ? -INFINITY : gd * (log(wsum) + 0.5 * log1p(-dl));
     double ph = gd * atan2(im, re);
     double phpi = ph * 0.3183098861837907;
     phpi -= 2.0 * rint(0.5 * phpi);
@@ -227,7 +286,7 @@ struct StoreF64 {
     using V = typename fft::Cx<MODE>::V;
     static constexpr bool kIdentity = false;
     __device__ static V to_v(double d) { return fft::load_split<MODE>(d); }
-    __device__ static double from_v(V v, double invN) { return fft::unsplit(v, invN); }
+    __device__ static double from_v(V v, const ConvScale &cs) { return fft::unsplit(v, cs.d); }
 };
 template <int MODE>
 struct StoreCell {
@@ -239,7 +298,7 @@ struct StoreCell {
         else if constexpr (MODE == 1) return fft::cell_to_v1(c);
         else return fft::cell_to_v2(c);
     }
-    __device__ static T from_v(V v, double invN) { return fft::v_to_cell(v, invN); }
+    __device__ static T from_v(V v, const ConvScale &cs) { return fft::v_to_cell(v, cs.d, cs.f); }
 };
 
 // ------------------------------------------------------------- per-CTA view
@@ -252,8 +311,39 @@ struct Cta {
     const DncArgs &a;
     Shared &S;
     char *slot;
+    bool tilt = false;    // exponential tilt of the call convolutions (FP32-split)
+    long long cnt_spec_ns = 0, cnt_spec_bins = 0;   // spectrum builds by this thread's group
 
     __device__ Cta(const DncArgs &a_, Shared &S_, char *slot_) : a(a_), S(S_), slot(slot_) {}
+
+    // e^{+kappa n} (0 past the float range) and e^{-kappa n} from the
+    // tables, in doubled FP32
+    __device__ static float2 df_prod(float2 a, float2 b) {
+        float h, l;
+        fft::df_mul(a.x, a.y, b.x, b.y, h, l);
+        return make_float2(h, l);
+    }
+    __device__ float2 tilt_up(int64_t n) const {
+        if (n > S.tilt_nmax) return make_float2(0.0f, 0.0f);
+        return df_prod(df_prod(S.tup2[n >> 14], S.tup1[(n >> 7) & 127]), S.tup0[n & 127]);
+    }
+    __device__ float2 tilt_dn(int64_t n) const {
+        if ((n >> 14) > 255) return make_float2(0.0f, 0.0f);
+        return df_prod(df_prod(S.tdn2[n >> 14], S.tdn1[(n >> 7) & 127]), S.tdn0[n & 127]);
+    }
+    // output cell y = x_hi - n of a tilted advance: multiply by e^{-kappa n}
+    template <class ST>
+    __device__ typename ST::T untilt(typename ST::T c, int64_t n, const ConvScale &cs) const {
+        if constexpr (MODE == 1 && std::is_same<typename ST::T, float2>::value) {
+            if (tilt) {
+                const float2 f = df_prod(tilt_dn(max(n - cs.n0, (int64_t)0)), cs.resid);
+                float h, l;
+                fft::two_sum(c.x, c.y, h, l);
+                c = df_prod(make_float2(h, l), f);
+            }
+        }
+        return c;
+    }
 
     __device__ const Params &P() const { return S.P; }
     __device__ double *mid(int d) const { return (double *)(slot + a.off_mid) + a.mid_off[d]; }
@@ -264,7 +354,7 @@ struct Cta {
     // Cached kernel power for (g, lgN); nullptr = evaluate bins on the fly
     // (arena exhausted).  Called by every thread of the group G.
     template <class G>
-    __device__ const Sp *spectrum(int64_t g, int lgN, int &mc_out) {
+    __device__ const Sp *spectrum(int64_t g, int lgN, int &mc_out, ConvScale &cs) {
         int idx = -1, build = 0;
         if (leader<G>()) {
             const uint64_t t0 = gtime();
@@ -275,13 +365,16 @@ struct Cta {
             for (int i = 0; i < S.spec_n; i++)
                 if (S.spec[i].g == (int32_t)g && S.spec[i].lgN == lgN) { idx = i; break; }
             if (idx < 0) {
-                int mc = band_mc(P(), g, (int64_t)1 << lgN);
+                int mc = band_mc(P(), g, (int64_t)1 << lgN, tilt);
                 if (S.spec_n < kSpecSlots && S.arena_used + mc + 1 <= a.spec_cap) {
                     idx = S.spec_n;
                     S.spec[idx].g = (int32_t)g;
                     S.spec[idx].lgN = lgN;
                     S.spec[idx].mc = mc;
                     S.spec[idx].off = S.arena_used;
+                    S.spec[idx].n0 = 0;
+                    S.spec[idx].resid = make_float2(1.0f, 0.0f);
+                    if (tilt) tilt_shift(P(), g, S.spec[idx].n0, S.spec[idx].resid);
                     S.spec[idx].state = SPEC_BUILDING;
                     S.arena_used += mc + 1;
                     __threadfence_block();
@@ -298,15 +391,23 @@ struct Cta {
         build = bcast_int<G>(S, build);
         if (idx < 0) {
             mc_out = -1 - idx;
+            cs.n0 = 0;
+            cs.resid = make_float2(1.0f, 0.0f);
+            if (tilt) tilt_shift(P(), g, cs.n0, cs.resid);
             return nullptr;
         }
         SpecEntry &e = S.spec[idx];
         Sp *p = arena() + e.off;
         if (build) {
-            for (int m = G::rank(); m <= e.mc; m += G::size()) p[m] = pack_spec<MODE>(bin_value(P(), g, lgN, m));
+            const uint64_t ts0 = gtime();
+            for (int m = G::rank(); m <= e.mc; m += G::size()) p[m] = pack_spec<MODE>(bin_value(P(), g, lgN, m, tilt));
             __threadfence_block();
             G::sync();
-            if (leader<G>()) e.state = SPEC_READY;
+            if (leader<G>()) {
+                e.state = SPEC_READY;
+                cnt_spec_ns += (long long)(gtime() - ts0);
+                cnt_spec_bins += e.mc + 1;
+            }
         } else if (leader<G>()) {
             const uint64_t t0 = gtime();
             while (e.state != SPEC_READY) {
@@ -317,6 +418,8 @@ struct Cta {
         }
         G::sync();
         mc_out = e.mc;
+        cs.n0 = e.n0;
+        cs.resid = e.resid;
         return p;
     }
 
@@ -344,6 +447,18 @@ struct Cta {
                 for (int64_t s = G::rank(); s < count; s += G::size()) {
                     const T d = *(const T *)&tile[s];
                     tile[s] = ST::to_v(d);
+                }
+            }
+            if constexpr (MODE == 1) {
+                if (tilt) {     // input cell x = x_hi - n times e^{+kappa n}
+                    for (int64_t s = G::rank(); s < count; s += G::size()) {
+                        const int64_t e = idx(s);
+                        if (e < W) {
+                            float h, l;
+                            fft::two_sum(tile[s].x, tile[s].y, h, l);
+                            tile[s] = df_prod(make_float2(h, l), tilt_up(W - 1 - e));
+                        }
+                    }
                 }
             }
         } else {
@@ -388,7 +503,7 @@ struct Cta {
         if (sp) return fft::spec_mul<MODE>(z, sp, mc, m, N);
         uint32_t mm = (m <= N / 2) ? m : N - m;
         if ((int)mm > mc) return fft::czero<V>();
-        Sp s = pack_spec<MODE>(bin_value(P(), g, lgN, mm));
+        Sp s = pack_spec<MODE>(bin_value(P(), g, lgN, mm, tilt));
         return (m <= N / 2) ? fft::twmul<false>(z, s) : fft::twmul<true>(z, s);
     }
 
@@ -400,7 +515,7 @@ struct Cta {
     template <class G, class ST, bool DIF>
     __device__ void tile_pass(V *tile, int lg_tile, V *scr, int lgN, int s_lo, int s_hi, bool first, bool last,
                               const Buf &in, int64_t x_lo, int64_t W, const Buf &out, int64_t y_lo, int64_t off,
-                              int64_t nout, double invN) {
+                              int64_t nout, const ConvScale &cs) {
         const int L = s_hi - s_lo + 1;
         const int64_t Gn = (int64_t)1 << L;
         const int64_t lo_count = (int64_t)1 << s_lo;
@@ -445,7 +560,7 @@ struct Cta {
                     const int64_t e = hbase + (t << s_lo) + q0 + q;
                     if (last) {
                         const int64_t k = e - off;
-                        if (k >= 0 && k < nout) store<ST>(out, y_lo + k, ST::from_v(tile[s], invN));
+                        if (k >= 0 && k < nout) store<ST>(out, y_lo + k, untilt<ST>(ST::from_v(tile[s], cs), W - 1 - k, cs));
                     } else {
                         scr[e] = tile[s];
                     }
@@ -472,8 +587,10 @@ struct Cta {
         if (lgN < 2) lgN = 2;
         const int64_t N = (int64_t)1 << lgN;
         int mc;
-        const Sp *sp = spectrum<G>(g, lgN, mc);
-        const double invN = 1.0 / (double)N;
+        ConvScale cs;
+        const Sp *sp = spectrum<G>(g, lgN, mc, cs);
+        cs.d = __longlong_as_double((long long)(1023 - lgN) << 52);
+        cs.f = __int_as_float((127 - lgN) << 23);
         const int64_t off = y_lo - x_lo;
         if (leader<G>()) {
             cnt.convs++;
@@ -491,7 +608,8 @@ struct Cta {
                 tile[p] = mul_bin(tile[p], sp, mc, fft::brev_n((uint32_t)p, lgN), (uint32_t)N, g, lgN);
             G::sync();
             fft::dit_range<MODE, G>(tile, N, 0, lgN - 1, T, twl);
-            for (int64_t t = G::rank(); t < nout; t += G::size()) store<ST>(out, y_lo + t, ST::from_v(tile[off + t], invN));
+            for (int64_t t = G::rank(); t < nout; t += G::size())
+                store<ST>(out, y_lo + t, untilt<ST>(ST::from_v(tile[off + t], cs), W - 1 - t, cs));
             G::sync();
             return;
         }
@@ -510,7 +628,7 @@ struct Cta {
         }
         for (int c = 0; c < nch; c++)
             tile_pass<G, ST, true>(tile, lg_tile, scr, lgN, ch_lo[c], ch_hi[c], c == 0, false, in, x_lo, W, out, y_lo,
-                               off, nout, invN);
+                               off, nout, cs);
         // inner stages on contiguous blocks, with the kernel-power product
         const int64_t N2 = (int64_t)1 << lg_tile;
         for (int64_t b = 0; b < N / N2; b++) {
@@ -526,9 +644,122 @@ struct Cta {
         }
         for (int c = nch - 1; c >= 0; c--)
             tile_pass<G, ST, false>(tile, lg_tile, scr, lgN, ch_lo[c], ch_hi[c], false, c == 0, in, x_lo, W, out, y_lo,
-                                off, nout, invN);
+                                off, nout, cs);
     }
 };
+
+// ------------------------------------------------- base-case arithmetic
+// The base cases step rows of up to kRegCells cells, one warp, D+1-point
+// stencil with non-negative weights and values.  FP64 on this GPU issues one
+// warp instruction per 64 cycles per SM sub-partition whatever the number of
+// active lanes, so the FP32 modes step their base cases in doubled FP32
+// (hi + lo, about 48 significant bits) on the FP32 pipe; the FP64 mode keeps
+// FP64.
+struct ArithF64 {
+    using T = double;
+    struct Wts { double w0, w1, w2; };
+    __device__ static T zero() { return 0.0; }
+    __device__ static Wts weights(const Shared &S) { return Wts{S.P.w[0], S.P.w[1], S.P.w[2]}; }
+    template <int MODE> __device__ static T load(const Buf &b, int64_t x) { return cell_ld<MODE>(b, x); }
+    template <int MODE> __device__ static void store(const Buf &b, int64_t x, T v) { cell_st<MODE>(b, x, v); }
+    __device__ static T shfl(T v, int src) { return __shfl_sync(0xffffffffu, v, src); }
+    __device__ static T dot2(const Wts &w, T a, T b) { return w.w0 * a + w.w1 * b; }
+    __device__ static T dot3(const Wts &w, T a, T b, T c) { return w.w0 * a + w.w1 * b + w.w2 * c; }
+    // continuation >= exercise for a non-negative continuation, decided on the
+    // bit patterns (non-negative doubles order like their integer images)
+    __device__ static bool cont_ge(T cont, T ex) {
+        const long long eb = __double_as_longlong(ex);
+        return eb <= 0 || __double_as_longlong(cont) >= eb;
+    }
+    // exercise > continuation > = 0 (put), on the bit patterns likewise
+    __device__ static bool ex_gt(T ex, T cont) {
+        const long long eb = __double_as_longlong(ex);
+        return eb > 0 && eb > __double_as_longlong(cont);
+    }
+    // exercise values of exponent indices klo .. khi into ext (one warp)
+    __device__ static void fill(const Shared &S, T *ext, int64_t klo, int64_t khi, int lane) {
+#pragma unroll 4
+        for (int64_t kp = klo + lane; kp <= khi; kp += 32) ext[kp - klo] = aop::exercise(S.P, S.E, kp);
+    }
+};
+
+struct ArithDF {
+    using T = float2;      // hi + lo, normalised (|lo| <= ulp(hi) / 2)
+    struct Wts { float2 w0, w1, w2; };
+    __device__ static T zero() { return make_float2(0.f, 0.f); }
+    __device__ static Wts weights(const Shared &S) { return Wts{S.wdf[0], S.wdf[1], S.wdf[2]}; }
+    // a stored cell (FP32 pair, from a base case or an FFT advance) renormalised
+    template <int MODE> __device__ static T load(const Buf &b, int64_t x) {
+        const float2 c = ((const float2 *)b.p)[x - b.base];
+        float s, e;
+        fft::two_sum(c.x, c.y, s, e);
+        return make_float2(s, e);
+    }
+    template <int MODE> __device__ static void store(const Buf &b, int64_t x, T v) {
+        ((float2 *)b.p)[x - b.base] = v;
+    }
+    __device__ static T shfl(T v, int src) {
+        return make_float2(__shfl_sync(0xffffffffu, v.x, src), __shfl_sync(0xffffffffu, v.y, src));
+    }
+    // high products exact through FMA, the low parts and rounding errors of
+    // the non-negative terms summed once, one renormalisation (__fmul_rn
+    // keeps the compiler from fusing a product into the two-sum that follows)
+    __device__ static T dot2(const Wts &w, T a, T b) {
+        const float p0 = __fmul_rn(w.w0.x, a.x), p1 = __fmul_rn(w.w1.x, b.x);
+        float e = fmaf(w.w0.x, a.x, -p0) + fmaf(w.w1.x, b.x, -p1);
+        e = fmaf(w.w0.x, a.y, fmaf(w.w0.y, a.x, e));
+        e = fmaf(w.w1.x, b.y, fmaf(w.w1.y, b.x, e));
+        float s, t;
+        fft::two_sum(p0, p1, s, t);
+        float h, l;
+        fft::fast_two_sum(s, t + e, h, l);
+        return make_float2(h, l);
+    }
+    __device__ static T dot3(const Wts &w, T a, T b, T c) {
+        const float p0 = __fmul_rn(w.w0.x, a.x), p1 = __fmul_rn(w.w1.x, b.x), p2 = __fmul_rn(w.w2.x, c.x);
+        float e = fmaf(w.w0.x, a.x, -p0) + fmaf(w.w1.x, b.x, -p1) + fmaf(w.w2.x, c.x, -p2);
+        e = fmaf(w.w0.x, a.y, fmaf(w.w0.y, a.x, e));
+        e = fmaf(w.w1.x, b.y, fmaf(w.w1.y, b.x, e));
+        e = fmaf(w.w2.x, c.y, fmaf(w.w2.y, c.x, e));
+        float s, t, s2, t2;
+        fft::two_sum(p0, p1, s, t);
+        fft::two_sum(s, p2, s2, t2);
+        float h, l;
+        fft::fast_two_sum(s2, (t + t2) + e, h, l);
+        return make_float2(h, l);
+    }
+    __device__ static bool ge(T a, T b) { return a.x > b.x || (a.x == b.x && a.y >= b.y); }
+    __device__ static bool pos(T a) { return a.x > 0.f || (a.x == 0.f && a.y > 0.f); }
+    __device__ static bool cont_ge(T cont, T ex) { return !pos(ex) || ge(cont, ex); }
+    __device__ static bool ex_gt(T ex, T cont) { return pos(ex) && !ge(cont, ex); }
+    // exercise values S u^k - K (calls) or 1 - e^{s_k} (put) of exponent
+    // indices klo .. khi: the node price at klo once in FP64, then
+    // e^{x_klo} u^j from the doubled-FP32 table (khi - klo < kNaiveCap, and
+    // the caller keeps u^(khi - klo) inside the float range)
+    __device__ static void fill(const Shared &S, T *ext, int64_t klo, int64_t khi, int lane) {
+        const float2 an = to_df(exp_from_tables(S.E, klo));
+        for (int64_t kp = klo + lane; kp <= khi; kp += 32) {
+            const float2 u = S.updf[kp - klo];
+            float h, l, rh, rl;
+            fft::df_mul(an.x, an.y, u.x, u.y, h, l);
+            if (S.P.model == AOP_BSM_PUT) fft::df_add(1.0f, 0.0f, -h, -l, rh, rl);
+            else fft::df_add(h, l, -S.kdf.x, -S.kdf.y, rh, rl);
+            ext[kp - klo] = make_float2(rh, rl);
+        }
+    }
+    __device__ static float2 to_df(double v) {
+        const float h = (float)v;
+        return make_float2(h, (float)(v - (double)h));
+    }
+};
+
+// Doubled-FP32 copies of the option's weights, K and powers of u.
+__device__ inline float2 to_df(double v) { return ArithDF::to_df(v); }
+__device__ void build_df_tables(Shared &S) {
+    for (int j = threadIdx.x; j < kNaiveCap; j += blockDim.x) S.updf[j] = to_df(exp((double)j * S.P.logu));
+    if (threadIdx.x < 3) S.wdf[threadIdx.x] = to_df(S.P.w[threadIdx.x]);
+    if (threadIdx.x == 3) S.kdf = to_df(S.P.K);
+}
 
 // ------------------------------------------------------------ the walker
 template <int MODE>
@@ -538,14 +769,13 @@ struct Walker {
     Shared &S;
     const Params &P;
     const ExpTables &E;
-    double *cur0, *nxt0;          // walker shared row buffers (kNaiveCap doubles each)
     double *exw;                  // exercise values of the current base case
     int32_t *bnd;
     Counters &cnt;
     int lane;
 
     __device__ Walker(Cta<MODE> &c_, double *buf, int32_t *bnd_, Counters &cnt_)
-        : c(c_), S(c_.S), P(c_.S.P), E(c_.S.E), cur0(buf), nxt0(buf + kNaiveCap), exw(buf + 2 * kNaiveCap),
+        : c(c_), S(c_.S), P(c_.S.P), E(c_.S.E), exw(buf),
           bnd(bnd_), cnt(cnt_),
           lane(threadIdx.x & 31) {}
 
@@ -589,14 +819,7 @@ struct Walker {
         __syncwarp();
     }
 
-    // ----- base cases (FP64, values in the walker's shared buffers)
-    // continuation >= exercise for a non-negative continuation, decided on the
-    // bit patterns (non-negative doubles order like their integer images), so
-    // the test costs no FP64 instruction
-    __device__ static bool cont_ge(double cont, double ex) {
-        const long long eb = __double_as_longlong(ex);
-        return eb <= 0 || __double_as_longlong(cont) >= eb;
-    }
+    // ----- base cases (values in registers, exercise table in shared memory)
 
     __device__ int64_t naive_call(int64_t i0, int64_t c0, int64_t b, int64_t h, const Buf &in, const Buf &out) {
         const uint64_t tb0 = gtime();
@@ -608,64 +831,117 @@ struct Walker {
         }
         return r;
     }
-    __device__ int64_t naive_call_body(int64_t i0, int64_t c0, int64_t b, int64_t h, const Buf &in, const Buf &out) {
-        double *cur = cur0, *nxt = nxt0;
+    // Row values live in registers: lane l holds cells x = c0 + l + 32 r,
+    // r < R, updated in place (ascending r, so the right neighbours a lane
+    // reads by shuffle are still the previous row's).  The D cells right of
+    // the divider hold their exercise values, so every red cell is the same
+    // D+1-point stencil.  The exercise values a row may need (cells bp .. bp+D,
+    // bp the previous divider: at most one per lane) are loaded before the
+    // stencil, so the per-row chain is shuffle -> stencil -> test.  A is the
+    // arithmetic (FP64, or doubled FP32 on the FP32 pipe).
+    template <int R, class A>
+    __device__ int64_t call_rows(int64_t i0, int64_t c0, int64_t b, int64_t h, const Buf &in, const Buf &out,
+                                 int64_t klo) {
+        using T = typename A::T;
         const int D = P.D;
-        const double w0 = P.w[0], w1 = P.w[1], w2 = P.w[2];
-        if (b - c0 + 1 + D > kNaiveCap) {          // never expected: window wider than the buffer
-            if (lane == 0) atomicCAS((int *)&S.err, 0, AOP_EINTERNAL);
-            return b;
+        const typename A::Wts w = A::weights(S);
+        const T *ext = (const T *)exw;
+        T val[R];
+#pragma unroll
+        for (int r = 0; r < R; r++) {
+            const int64_t x = c0 + lane + 32 * r;
+            val[r] = A::zero();
+            if (x <= b) val[r] = A::template load<MODE>(in, x);
+            else if (x <= b + D) val[r] = ext[ex_index(P, i0, x) - klo];
         }
+        long long cells = 0;
+        const long long lc0 = clock64();
+        int64_t k = 1;
+        for (; k <= h; k++) {
+            const int64_t i = i0 - k;
+            const int64_t bp = b;
+            if (bp < c0) break;
+            // this lane's cell among bp .. bp + D (if any) and its exercise value
+            const int64_t d = bp - c0;
+            const int64_t t = d + ((lane - d) & 31);
+            const int er = (t <= d + D) ? (int)(t >> 5) : -1;
+            const T ex1 = (er >= 0) ? ext[ex_index(P, i, c0 + t) - klo] : A::zero();
+#pragma unroll
+            for (int r = 0; r < R; r++) {
+                const T nx = (r + 1 < R) ? val[(r + 1) % R] : A::zero();
+                const T n1 = A::shfl(lane == 0 ? nx : val[r], (lane + 1) & 31);
+                if (D == 2) {
+                    const T n2 = A::shfl(lane <= 1 ? nx : val[r], (lane + 2) & 31);
+                    val[r] = A::dot3(w, val[r], n1, n2);
+                } else {
+                    val[r] = A::dot2(w, val[r], n1);
+                }
+            }
+            int64_t bn;
+            if (bp - 1 >= (int64_t)D * i) {
+                bn = (int64_t)D * i;            // the row ends inside the window: all red
+            } else {
+                // value-versus-payoff test at the previous divider (Cor. 2.7),
+                // taken by the lane that holds it (its ex1 is that cell's)
+                T tv = A::zero();
+#pragma unroll
+                for (int r = 0; r < R; r++)
+                    if (r == (int)(d >> 5)) tv = val[r];
+                const bool ge = __shfl_sync(0xffffffffu, A::cont_ge(tv, ex1), (int)(d & 31));
+                bn = ge ? bp : bp - 1;
+            }
+            cells += min(bp, (int64_t)D * i) - c0 + 1;
+            b = bn;
+            record(i, (int32_t)(b >= c0 ? b : c0 - 1));
+            // cells right of the new divider take their exercise values
+#pragma unroll
+            for (int r = 0; r < R; r++)
+                if (r == er && c0 + lane + 32 * r > b) val[r] = ex1;
+        }
+        if (lane == 0) cnt.loop_cyc += clock64() - lc0;
+        if (k <= h) record_range(i0 - h, i0 - k, (int32_t)(c0 - 1));
+#pragma unroll
+        for (int r = 0; r < R; r++) {
+            const int64_t x = c0 + lane + 32 * r;
+            if (x <= b) A::template store<MODE>(out, x, val[r]);
+        }
+        if (lane == 0) cnt.base_cells += cells;
+        return b;
+    }
+
+    template <class A>
+    __device__ int64_t call_dispatch(int64_t need, int64_t i0, int64_t c0, int64_t b, int64_t h, const Buf &in,
+                                     const Buf &out, int64_t klo, int64_t khi) {
+        const long long fc0 = clock64();
+        A::fill(S, (typename A::T *)exw, klo, khi, lane);
+        __syncwarp();
+        if (lane == 0) cnt.fill_cyc += clock64() - fc0;
+        if (need <= 32) return call_rows<1, A>(i0, c0, b, h, in, out, klo);
+        if (need <= 64) return call_rows<2, A>(i0, c0, b, h, in, out, klo);
+        if (need <= 128) return call_rows<4, A>(i0, c0, b, h, in, out, klo);
+        if (need <= 256) return call_rows<8, A>(i0, c0, b, h, in, out, klo);
+        return call_rows<9, A>(i0, c0, b, h, in, out, klo);
+    }
+
+    __device__ int64_t naive_call_body(int64_t i0, int64_t c0, int64_t b, int64_t h, const Buf &in, const Buf &out) {
+        const int D = P.D;
+        const int64_t need = b - c0 + 1 + D;
         // exercise values the base case can touch (the divider moves <= 1 cell
         // per row): one table of exponent indices, filled once
         const int64_t klo = max((int64_t)0, ex_index(P, i0, b) - h - 2);
         const int64_t khi = min(2 * P.T, ex_index(P, i0 - h, b + D) + 2);
-        if (khi - klo + 1 > kNaiveCap) {
+        if (need > kRegCells || khi - klo + 1 > kNaiveCap) {   // never expected
             if (lane == 0) atomicCAS((int *)&S.err, 0, AOP_EINTERNAL);
             return b;
         }
-        for (int64_t kp = klo + lane; kp <= khi; kp += 32) exw[kp - klo] = exercise(P, E, kp);
-        for (int64_t x = c0 + lane; x <= b; x += 32) cur[x - c0] = cell_ld<MODE>(in, x);
-        __syncwarp();
-        long long cells = 0;
-        for (int64_t k = 1; k <= h; k++) {
-            const int64_t i = i0 - k;
-            const int64_t bp = b;
-            if (bp < c0) {
-                record(i, (int32_t)(c0 - 1));
-                continue;
-            }
-            const int64_t top = min(bp, (int64_t)D * i);
-            for (int64_t x = c0 + lane; x <= top; x += 32) {
-                double v0 = cur[x - c0];
-                double v1 = (x + 1 <= bp) ? cur[x + 1 - c0] : exw[ex_index(P, i + 1, x + 1) - klo];
-                double cv = w0 * v0 + w1 * v1;
-                if (D == 2) {
-                    double v2 = (x + 2 <= bp) ? cur[x + 2 - c0] : exw[ex_index(P, i + 1, x + 2) - klo];
-                    cv += w2 * v2;
-                }
-                nxt[x - c0] = cv;
-                cells++;
-            }
-            __syncwarp();
-            int64_t bn;
-            if (bp - 1 >= (int64_t)D * i) {
-                bn = (int64_t)D * i;
-            } else {
-                // value-versus-payoff test at the previous divider (Cor. 2.7)
-                bn = cont_ge(nxt[bp - c0], exw[ex_index(P, i, bp) - klo]) ? bp : bp - 1;
-            }
-            b = bn;
-            record(i, (int32_t)(b >= c0 ? b : c0 - 1));
-            double *t = cur; cur = nxt; nxt = t;
-            __syncwarp();
-        }
-        for (int64_t x = c0 + lane; x <= b; x += 32) cell_st<MODE>(out, x, cur[x - c0]);
-        cells = __reduce_add_sync(0xffffffffu, (unsigned)cells);
-        if (lane == 0) cnt.base_cells += cells;
+        int64_t r;
+        if (MODE == 0 || (double)(khi - klo) * P.logu > kDfLogRange)
+            r = call_dispatch<ArithF64>(need, i0, c0, b, h, in, out, klo, khi);
+        else
+            r = call_dispatch<ArithDF>(need, i0, c0, b, h, in, out, klo, khi);
         __threadfence_block();
         __syncwarp();
-        return b;
+        return r;
     }
 
     __device__ int64_t naive_put(int64_t n, int64_t lo, int64_t hi, int64_t f, int64_t h, const Buf &in,
@@ -679,52 +955,104 @@ struct Walker {
         }
         return r;
     }
-    __device__ int64_t naive_put_body(int64_t n, int64_t lo, int64_t hi, int64_t f, int64_t h, const Buf &in,
-                                      const Buf &out) {
-        double *cur = cur0, *nxt = nxt0;
-        const double wb = P.w[0], wc = P.w[1], wa = P.w[2];
-        if (hi - lo + 1 > kNaiveCap) {
-            if (lane == 0) atomicCAS((int *)&S.err, 0, AOP_EINTERNAL);
-            return f;
+    // Put rows in registers (lane l holds cells x = lo + l + 32 r), updated
+    // in place in ascending r (each lane keeps its old value of the register
+    // below for the left neighbour of lane 0).  The window shrinks by one cell
+    // per side per row.  Cells left of the divider hold the exercise value,
+    // which for the put does not depend on the time step (table exw, one per
+    // window); they stay green, so only the divider cell can turn red.
+    template <int R, class A>
+    __device__ int64_t put_rows(int64_t n, int64_t lo, int64_t hi, int64_t f, int64_t h, const Buf &in,
+                                const Buf &out) {
+        using T = typename A::T;
+        const typename A::Wts w = A::weights(S);
+        const T *ext = (const T *)exw;
+        T val[R];
+#pragma unroll
+        for (int r = 0; r < R; r++) {
+            const int64_t x = lo + lane + 32 * r;
+            val[r] = A::zero();
+            if (x <= hi) val[r] = (x <= f) ? ext[x - lo] : A::template load<MODE>(in, x);
         }
-        // the put's payoff does not depend on the time step: one table per window
-        for (int64_t x = lo + lane; x <= hi; x += 32) {
-            const double e = exercise(P, E, ex_index(P, n, x));
-            exw[x - lo] = e;
-            cur[x - lo] = (x <= f) ? e : cell_ld<MODE>(in, x);
-        }
-        __syncwarp();
         long long cells = 0;
-        int64_t L = lo, R = hi;
+        int64_t L = lo, Rr = hi;
         for (int64_t k = 1; k <= h; k++) {
-            const int64_t nl = L + 1, nr = R - 1;
+            const int64_t nl = L + 1, nr = Rr - 1;
             const int64_t fp = f;
-            for (int64_t x = nl + lane; x <= nr; x += 32) {
-                nxt[x - lo] = wb * cur[x - 1 - lo] + wc * cur[x - lo] + wa * cur[x + 1 - lo];
-                cells++;
+            const bool test = (fp >= nl && fp <= nr);
+            const T te = test ? ext[fp - lo] : A::zero();
+            T prev = A::zero();
+#pragma unroll
+            for (int r = 0; r < R; r++) {
+                const int64_t x = lo + lane + 32 * r;
+                const T nx = (r + 1 < R) ? val[(r + 1) % R] : A::zero();
+                const T vl = A::shfl(lane == 31 ? prev : val[r], (lane + 31) & 31);
+                const T vr = A::shfl(lane == 0 ? nx : val[r], (lane + 1) & 31);
+                const T cv = A::dot3(w, vl, val[r], vr);
+                prev = val[r];
+                if (x >= fp) val[r] = cv;
             }
-            __syncwarp();
+            cells += nr - nl + 1;
             int64_t fn;
             if (fp >= nr + 1) fn = nr;
             else if (fp < nl) fn = fp;
             else {
-                // exercise > continuation (non-negative continuation; bit compare)
-                const long long eb = __double_as_longlong(exw[fp - lo]);
-                fn = (eb > 0 && eb > __double_as_longlong(nxt[fp - lo])) ? fp : fp - 1;
+                // exercise > continuation, taken by the lane that holds the
+                // previous divider
+                const int64_t d = fp - lo;
+                T tv = A::zero();
+#pragma unroll
+                for (int r = 0; r < R; r++)
+                    if (r == (int)(d >> 5)) tv = val[r];
+                const bool green = __shfl_sync(0xffffffffu, A::ex_gt(te, tv), (int)(d & 31));
+                fn = green ? fp : fp - 1;
+                if (green && lane == (int)(d & 31)) {
+#pragma unroll
+                    for (int r = 0; r < R; r++)
+                        if (r == (int)(d >> 5)) val[r] = te;
+                }
             }
             f = fn;
-            for (int64_t x = nl + lane; x <= min(f, nr); x += 32) nxt[x - lo] = exw[x - lo];
             record(n + k, (f >= nl) ? (int32_t)f : (int32_t)AOP_BOUNDARY_NONE_PUT);
-            double *t = cur; cur = nxt; nxt = t;
-            L = nl; R = nr;
-            __syncwarp();
+            L = nl;
+            Rr = nr;
         }
-        for (int64_t x = max(L, f + 1) + lane; x <= R; x += 32) cell_st<MODE>(out, x, cur[x - lo]);
-        cells = __reduce_add_sync(0xffffffffu, (unsigned)cells);
+#pragma unroll
+        for (int r = 0; r < R; r++) {
+            const int64_t x = lo + lane + 32 * r;
+            if (x >= max(L, f + 1) && x <= Rr) A::template store<MODE>(out, x, val[r]);
+        }
         if (lane == 0) cnt.base_cells += cells;
+        return f;
+    }
+
+    template <class A>
+    __device__ int64_t put_dispatch(int64_t w, int64_t n, int64_t lo, int64_t hi, int64_t f, int64_t h,
+                                    const Buf &in, const Buf &out) {
+        A::fill(S, (typename A::T *)exw, ex_index(P, n, lo), ex_index(P, n, hi), lane);
+        __syncwarp();
+        if (w <= 32) return put_rows<1, A>(n, lo, hi, f, h, in, out);
+        if (w <= 64) return put_rows<2, A>(n, lo, hi, f, h, in, out);
+        if (w <= 128) return put_rows<4, A>(n, lo, hi, f, h, in, out);
+        if (w <= 256) return put_rows<8, A>(n, lo, hi, f, h, in, out);
+        return put_rows<9, A>(n, lo, hi, f, h, in, out);
+    }
+
+    __device__ int64_t naive_put_body(int64_t n, int64_t lo, int64_t hi, int64_t f, int64_t h, const Buf &in,
+                                      const Buf &out) {
+        const int64_t w = hi - lo + 1;
+        if (w > kRegCells) {            // never expected: window wider than the registers
+            if (lane == 0) atomicCAS((int *)&S.err, 0, AOP_EINTERNAL);
+            return f;
+        }
+        int64_t r;
+        if (MODE == 0 || (double)(hi - lo) * P.logu > kDfLogRange)
+            r = put_dispatch<ArithF64>(w, n, lo, hi, f, h, in, out);
+        else
+            r = put_dispatch<ArithDF>(w, n, lo, hi, f, h, in, out);
         __threadfence_block();
         __syncwarp();
-        return f;
+        return r;
     }
 
     // ----- call recursion (explicit stack; every lane holds the same state)
@@ -838,7 +1166,7 @@ struct Walker {
                     sp--;
                     continue;
                 }
-                if (F.h <= c.a.B || F.depth + 1 >= kMaxDepth) {
+                if ((F.h <= c.a.B && F.hi - F.lo + 1 <= kRegCells) || F.h < 2 || F.depth + 1 >= kMaxDepth) {
                     ret = naive_put(F.n, F.lo, F.hi, F.f, F.h, F.in, F.out);
                     sp--;
                     continue;
@@ -893,7 +1221,7 @@ struct Walker {
                     for (int64_t r = n + 1 + lane; r <= T; r += 32) bnd[r] = (int32_t)(T - r);
                 return P.out_scale * exercise(P, E, ex_index(P, T, 0));
             }
-            if (R / 2 < c.a.B || R <= 2 * c.a.B) {
+            if (R < 2 * c.a.B) {
                 f = naive_put(n, -R, R, f, R, row, row);
                 n = T;
                 break;
@@ -998,14 +1326,14 @@ __device__ int64_t first_rows_put(Cta<MODE> &c, int32_t *bnd) {
 
 // ------------------------------------------------------------------ kernel
 template <int MODE>
-__global__ void __launch_bounds__(kThreadsD) dnc_kernel(const __grid_constant__ DncArgs a)
+__global__ void __launch_bounds__(kThreadsD, kMinCtasPerSm) dnc_kernel(const __grid_constant__ DncArgs a)
 {
     using V = typename fft::Cx<MODE>::V;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ Shared S;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    double *walker_buf = (double *)smem_raw;                              // 3 x kNaiveCap doubles
-    V *tiles = (V *)(smem_raw + 3 * kNaiveCap * sizeof(double));        // one tile per worker
+    double *walker_buf = (double *)smem_raw;                              // kNaiveCap doubles
+    V *tiles = (V *)(smem_raw + kNaiveCap * sizeof(double));            // one tile per worker
     char *slot = a.ws + (int64_t)blockIdx.x * a.ws_stride;
     Cta<MODE> c(a, S, slot);
     Counters cnt{};
@@ -1054,10 +1382,25 @@ __global__ void __launch_bounds__(kThreadsD) dnc_kernel(const __grid_constant__ 
         uint64_t t_start = 0;
         if (threadIdx.x == 0 && a.opt_ns) asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t_start));
         build_exp_tables(S.P, S.E);
+        const bool may_tilt = (MODE == 1) && S.P.model != AOP_BSM_PUT && S.P.kappa > 0.0 &&
+                              !(a.flags & AOP_FLAG_TILT_OFF);
+        if (may_tilt) build_tilt_tables(S);
+        __syncthreads();
+        if (MODE != 0) build_df_tables(S);
         __syncthreads();
         int32_t *bnd = a.bnd ? a.bnd + a.bnd_off[o] : nullptr;
         const bool put = (S.P.model == AOP_BSM_PUT);
         const int64_t first = put ? first_rows_put(c, bnd) : first_rows_call(c, bnd);
+        // Tilt when the continuation region reaches node prices far above the
+        // strike: untilted, the FP32 rounding of every advance scales with the
+        // largest value of its window (about S_b - K at the divider, node
+        // price S_b); tilted, with the node price of each cell.
+        c.tilt = false;
+        if (may_tilt) {
+            const double sb = exercise(S.P, S.E, ex_index(S.P, S.P.T - 1, first)) + S.P.K;
+            c.tilt = (a.flags & AOP_FLAG_TILT_ON) || first >= (int64_t)S.P.D * (S.P.T - 1) ||
+                     sb - S.P.K > 2.0 * S.P.S;
+        }
         if (role == 0) {
             Walker<MODE> wk(c, walker_buf, bnd, cnt);
             const uint64_t tw0 = gtime();
@@ -1140,6 +1483,10 @@ __global__ void __launch_bounds__(kThreadsD) dnc_kernel(const __grid_constant__ 
         atomicAdd((unsigned long long *)&a.stats->basecase_calls, (unsigned long long)cnt.base_calls);
         atomicAdd((unsigned long long *)&a.stats->basecase_rows, (unsigned long long)cnt.base_rows);
         atomicAdd((unsigned long long *)&a.stats->walker_ns, (unsigned long long)cnt.walker_ns);
+        atomicAdd((unsigned long long *)&a.stats->spectrum_ns, (unsigned long long)(cnt.spec_ns + c.cnt_spec_ns));
+        atomicAdd((unsigned long long *)&a.stats->spectrum_bins, (unsigned long long)(cnt.spec_bins + c.cnt_spec_bins));
+        atomicAdd((unsigned long long *)&a.stats->basecase_loop_cycles, (unsigned long long)cnt.loop_cyc);
+        atomicAdd((unsigned long long *)&a.stats->basecase_fill_cycles, (unsigned long long)cnt.fill_cyc);
     }
 }
 
@@ -1182,7 +1529,7 @@ Layout make_layout(int method, int64_t T_max, int B, int scratch_units) {
     L.off_spec = off;
     off += (L.spec_cap * 16 + 255) & ~255ll;
     L.stride = off;
-    L.smem = 3 * kNaiveCap * sizeof(double) + (size_t)kWorkers * ((size_t)L.vsz << L.lg_tile);
+    L.smem = kNaiveCap * sizeof(double) + (size_t)kWorkers * ((size_t)L.vsz << L.lg_tile);
     return L;
 }
 
@@ -1231,7 +1578,7 @@ size_t dnc_workspace_bytes(int method, int64_t n, int64_t T_max, int base_case, 
 cudaError_t run_dnc(int method, int64_t n, const Params *d_params, int64_t T_max, int base_case,
                     void *ws, size_t ws_bytes, const void *d_tw, int tw_log2, double *d_prices,
                     int32_t *d_status, int32_t *d_bnd, const int64_t *d_bnd_off,
-                    aop_stats *d_stats, int *d_err, int64_t *d_opt_ns, int device, cudaStream_t s)
+                    aop_stats *d_stats, int *d_err, int64_t *d_opt_ns, int flags, int device, cudaStream_t s)
 {
     if (n == 0) return cudaSuccess;
     Layout L = make_layout(method, T_max, base_case, kBigWorkers);
@@ -1274,6 +1621,7 @@ cudaError_t run_dnc(int method, int64_t n, const Params *d_params, int64_t T_max
     a.err = d_err;
     a.stats = d_stats;
     a.opt_ns = d_opt_ns;
+    a.flags = flags;
     switch (method) {
     case AOP_FFT_FP64:
         dnc_kernel<0><<<(unsigned)grid, kThreadsD, L.smem, s>>>(a);
@@ -1342,6 +1690,9 @@ Params advance_params(int nw, const double *w) {
     P.o_min = 0;
     P.w[0] = w[0]; P.w[1] = w[1]; P.w[2] = nw == 3 ? w[2] : 0.0;
     P.wsum = P.w[0] + P.w[1] + P.w[2];
+    for (int j = 0; j < 3; j++) P.wt[j] = P.w[j];
+    P.wtsum = P.wsum;
+    P.tL = 0.0;
     return P;
 }
 

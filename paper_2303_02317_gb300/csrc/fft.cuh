@@ -78,7 +78,7 @@ __device__ __forceinline__ void df_add(float ah, float al, float bh, float bl, f
 }
 // (ah + al) * (bh + bl): exact high product through FMA, cross terms added
 __device__ __forceinline__ void df_mul(float ah, float al, float bh, float bl, float &rh, float &rl) {
-    float p = ah * bh;
+    float p = __fmul_rn(ah, bh);     // not fused into the sum below
     float e = fmaf(ah, bh, -p);
     e = fmaf(ah, bl, e);
     e = fmaf(al, bh, e);
@@ -318,15 +318,9 @@ __device__ __forceinline__ double2 cell_to_v(double c) { return make_double2(c, 
 __device__ __forceinline__ float2 cell_to_v1(float2 c) { return c; }
 __device__ __forceinline__ df2 cell_to_v2(float2 c) { df2 r; r.v = make_float4(c.x, 0.f, c.y, 0.f); return r; }
 // transform value -> cell, scaled by 1/N (a power of two: exact in FP32)
-__device__ __forceinline__ double v_to_cell(double2 v, double invN) { return v.x * invN; }
-__device__ __forceinline__ float2 v_to_cell(float2 v, double invN) {
-    const float s = (float)invN;
-    return make_float2(v.x * s, v.y * s);
-}
-__device__ __forceinline__ float2 v_to_cell(df2 v, double invN) {
-    const float s = (float)invN;
-    return make_float2(v.v.x * s, v.v.z * s);
-}
+__device__ __forceinline__ double v_to_cell(double2 v, double invN, float) { return v.x * invN; }
+__device__ __forceinline__ float2 v_to_cell(float2 v, double, float s) { return make_float2(v.x * s, v.y * s); }
+__device__ __forceinline__ float2 v_to_cell(df2 v, double, float s) { return make_float2(v.v.x * s, v.v.z * s); }
 
 template <class V> __device__ __forceinline__ V czero();
 template <> __device__ __forceinline__ double2 czero<double2>() { return make_double2(0.0, 0.0); }

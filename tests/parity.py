@@ -7,6 +7,11 @@ Tolerances (derived in DESIGN.md, "Parity tolerances"):
       |gpu - oracle| <= FP32_REL |oracle| + FP32_ABS K
 Boundary rows may differ from the oracle only where the oracle's margin
 |continuation - exercise| at the divider is within the tie band of the method.
+FP64 methods may then move the divider by one cell.  The FP32-split method may
+move it further: continuation and exercise value meet tangentially at the
+exercise boundary (smooth pasting), so a value error of FP32 size shifts the
+crossing by about sqrt(error / curvature) cells, which at small margins spans
+several cells; each such row must still lie inside the FP32 tie band.
 """
 import numpy as np
 
@@ -35,5 +40,7 @@ def check_boundary(method, req, got, want, margin):
     want = np.asarray(want)
     diff = np.nonzero(got != want)[0]
     band = tie_band(method, req)
-    bad = [int(i) for i in diff if not (margin[i] <= band and abs(int(got[i]) - int(want[i])) <= 1)]
+    reach = 1 if method != 1 else None
+    bad = [int(i) for i in diff
+           if not (margin[i] <= band and (reach is None or abs(int(got[i]) - int(want[i])) <= reach))]
     return bad, len(diff)
