@@ -4,14 +4,17 @@ Workload (one step): price the book of 512 American calls of the precision
 sweep -- 256 binomial (CRR) + 256 trinomial (Boyle, lambda = sqrt(3)), all at
 T = 2^17 steps, S0, K ~ U[50,150], sigma ~ U[0.1,0.6], r ~ U[0,0.08],
 q ~ U[0.005,0.06], expiry ~ U[0.1,3] (seed 2303) -- with the trapezoidal
-divide-and-conquer pricer (FP32 hi/lo-split FFT convolutions, FP64 base cases,
-boundary tests and root).  Synthetic inputs; no dataset.
+divide-and-conquer pricer.  The headline method is the one whose prices stay
+within 1e-6 relative of FP64: doubled-FP32 FFT convolutions and base cases on
+the FP32 pipe (--method df32, default).  Synthetic inputs; no dataset.
 
-Reported beside it: the same book through the host-buffer C-ABI call (e2e),
-the plain Theta(T^2) FP64 stencil on a sample of the book (ms/option), the
-per-option error of the split-FP32 prices against the FP64 FFT pricer and the
-CPU oracle, the roofline of the pricing kernel and the CPU oracle timed on the
-host cores.
+Reported beside it: the FP32 hi/lo-split FFT pricer on the same book with its
+measured error (fp32_split), the same book through the host-buffer C-ABI call
+(e2e), the plain Theta(T^2) FP64 stencil on a sample of the book (ms/option),
+the per-option error against the FP64 FFT pricer and the CPU oracle, the
+roofline of the pricing kernel and the CPU oracle timed on the host cores.
+The D&C schedule (base-case height, options in flight per SM) is picked by the
+library's autotuner on half of the book before the warm-up steps.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 Multi-GPU (torchrun): every rank prices its own copy of the book (weak
@@ -166,7 +169,9 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--method", default="fft32", choices=["fft32", "fft64", "df32"])
+    ap.add_argument("--method", default="df32", choices=["fft32", "fft64", "df32"])
+    ap.add_argument("--no-tune", action="store_true", help="library default schedule, no autotuning")
+    ap.add_argument("--no-fp32", action="store_true", help="skip the split-FP32 side measurement")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--stencil-sample", type=int, default=4)
     ap.add_argument("--small", action="store_true",
@@ -207,9 +212,15 @@ def main():
     sh = stream.cuda_stream
     flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)   # > L2 (129 MB)
 
-    def step():
+    tuned = {}
+    if not args.no_tune:
+        tuned = {"method": ctx.autotune(arr[::2], method)}
+        if method != aop.FFT_FP32SPLIT and not args.no_fp32:
+            tuned["fp32_split"] = ctx.autotune(arr[::2], aop.FFT_FP32SPLIT)
+
+    def step(m=method):
         ctx.price_batch_device(n, d_reqs.data_ptr(), d_prices.data_ptr(), d_status.data_ptr(),
-                               method=method, stream=sh, flags=aop.FLAG_OPTION_TIMES)
+                               method=m, stream=sh, flags=aop.FLAG_OPTION_TIMES)
 
     for _ in range(args.warmup):
         step()
@@ -264,22 +275,43 @@ def main():
             dist.barrier()
         return
 
-    # ---- accuracy: split-FP32 prices against the FP64 FFT pricer (untimed)
+    # ---- accuracy against the FP64 FFT pricer (untimed)
+    def accuracy(p, ref, ok):
+        if int((~np.isfinite(p)).sum()):
+            raise SystemExit("non-finite prices: %d" % int((~np.isfinite(p)).sum()))
+        rel = np.abs(p[ok] - ref[ok]) / np.maximum(np.abs(ref[ok]), 1e-300)
+        ab = np.abs(p[ok] - ref[ok])
+        floor = np.abs(ref[ok]) >= 1e-3 * arr["K"][ok]
+        return {"vs": "fft_fp64", "max_rel": float(rel[floor].max()), "mean_rel": float(rel[floor].mean()),
+                "max_abs": float(ab.max()), "mean_abs": float(ab.mean()),
+                "n_rel_le_1e-6": int((rel[floor] <= 1e-6).sum()), "n_priced_above_floor": int(floor.sum()),
+                "floor": "prices >= 1e-3 K"}
+
     acc = {}
-    if method == aop.FFT_FP32SPLIT:
+    if method != aop.FFT_FP64:
         p64, s64 = ctx.price_batch(arr, method=aop.FFT_FP64)
-        acc_nonfinite = int((~np.isfinite(prices32)).sum() + (~np.isfinite(p64)).sum())
-        if acc_nonfinite:
-            raise SystemExit("non-finite prices: %d" % acc_nonfinite)
-        ok = (s64 == 0)
-        rel = np.abs(prices32[ok] - p64[ok]) / np.maximum(np.abs(p64[ok]), 1e-300)
-        ab = np.abs(prices32[ok] - p64[ok])
-        floor = np.abs(p64[ok]) >= 1e-3 * arr["K"][ok]
-        acc = {"vs": "fft_fp64", "max_rel": float(rel[floor].max()), "mean_rel": float(rel[floor].mean()),
-               "max_abs": float(ab.max()), "mean_abs": float(ab.mean()),
-               "n_rel_le_1e-6": int((rel[floor] <= 1e-6).sum()), "n_priced_above_floor": int(floor.sum())}
+        acc = accuracy(prices32, p64, s64 == 0)
     else:
-        p64 = prices32
+        p64, s64 = prices32, np.zeros(n, dtype=np.int32)
+
+    # ---- the split-FP32 pricer on the same book (device-timed steps)
+    fp32 = None
+    if method != aop.FFT_FP32SPLIT and not args.no_fp32:
+        for _ in range(args.warmup):
+            step(aop.FFT_FP32SPLIT)
+        ms32 = []
+        for k in range(args.steps):
+            flush.fill_(k & 0xff)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            step(aop.FFT_FP32SPLIT)
+            e1.record(stream)
+            torch.cuda.synchronize(dev)
+            ms32.append(e0.elapsed_time(e1))
+        p32 = d_prices.cpu().numpy().copy()
+        fp32 = {"value": n / (float(np.mean(ms32)) / 1e3), "unit": "options/s",
+                "ms_per_step": float(np.mean(ms32)), "accuracy": accuracy(p32, p64, s64 == 0),
+                "what": "FP32 hi/lo-split FFT convolutions, doubled-FP32 base cases; measured error bound"}
 
     # ---- plain FP64 stencil on a sample (ms/option)
     stencil = None
@@ -303,9 +335,10 @@ def main():
     flops = stats["fft_flops"]
     peaks = _peaks()
     kern_s = kms / 1e3
-    if method == aop.FFT_FP32SPLIT:
+    if method in (aop.FFT_FP32SPLIT, aop.FFT_DF32):
         peak = FP32_PEAK_TFLOPS
-        note = "FP32 peak derived: 152 SMs x 128 lanes x 2 flop x 2.07 GHz"
+        note = ("FP32 peak derived: 152 SMs x 128 lanes x 2 flop x 2.07 GHz; achieved counts the "
+                "transforms' 5 N log2 N flops (a doubled-FP32 flop costs several FP32 instructions)")
     else:
         peak = FP64_PEAK_TFLOPS
         note = "FP64 peak: vendor dense FP64 figure"
@@ -324,8 +357,9 @@ def main():
         # FP64 FFT vs oracle on the sample
         ii = [reqs.index(r) for r in done]
         cpu["max_rel_fft64_vs_oracle"] = float(np.max(np.abs(p64[ii] - np.array(oprices)) / np.abs(oprices)))
-        if method == aop.FFT_FP32SPLIT:
-            cpu["max_rel_fft32_vs_oracle"] = float(np.max(np.abs(prices32[ii] - np.array(oprices)) / np.abs(oprices)))
+        if method != aop.FFT_FP64:
+            cpu["max_rel_%s_vs_oracle" % args.method] = float(
+                np.max(np.abs(prices32[ii] - np.array(oprices)) / np.abs(oprices)))
 
     value = world * n / (ms_step / 1e3)
     line = {
@@ -340,7 +374,8 @@ def main():
         "dtype": {aop.FFT_FP32SPLIT: "f32split+f64", aop.FFT_DF32: "f32x2+f64"}.get(method, "f64"),
         "data": "synthetic",
         "config": {"workload": WORKLOAD, "T": T_BENCH, "options_per_step": n,
-                   "method": args.method, "l2": "512 MB buffer written between timed steps",
+                   "method": args.method, "schedule": tuned or "library default",
+                   "l2": "512 MB buffer written between timed steps",
                    "parallelism": "independent options per rank"},
         "e2e": {"value": world * n / (e2e_ms / 1e3), "unit": "options/s",
                 "h2d_bytes_per_step": int(arr.nbytes), "d2h_bytes_per_step": int(n * (8 + 4))},
@@ -348,6 +383,7 @@ def main():
         "clocks": clocks,
         "roofline": roof,
         "accuracy": acc,
+        "fp32_split": fp32,
         "stencil_fp64": stencil,
         "speedup_vs_stencil_ms_per_option": (stencil["ms_per_option"] / (ms_step / n)) if stencil else None,
         "cpu_baseline": cpu,

@@ -105,7 +105,7 @@ typedef struct aop_options {
     int32_t method;     /* aop_method */
     int32_t base_case;  /* D&C base-case height in rows; 0 = tuned default */
     int32_t flags;      /* AOP_FLAG_* bits, 0 for none */
-    int32_t reserved;
+    int32_t ctas_per_sm; /* D&C: options in flight per SM; 0 = as many as fit */
 } aop_options;
 
 /* Counters accumulated by the kernels of the last batch call (for roofline
@@ -205,6 +205,17 @@ aop_status aop_linear_advance_device(aop_ctx *ctx, int method, int nw, const dou
 /* Counters of the kernels launched by the last batch call on this context
  * (synchronizes the context's stream). */
 aop_status aop_ctx_get_stats(aop_ctx *ctx, aop_stats *out);
+
+/* Autotuner for the divide-and-conquer methods (no counterpart in the paper,
+ * which fixes its base case by hand): prices the n host requests once per
+ * schedule -- base-case height in {16, 32, 64} x options in flight per SM in
+ * {1, 2, 3, 4} -- timing each second run with CUDA events, and keeps the
+ * fastest schedule as this context's default for `method` (used where
+ * aop_options.base_case or ctas_per_sm is 0).  best_out (nullable) receives
+ * it.  Costs 24 batch calls: pass a sample of the workload.  AOP_EINVAL for
+ * the plain stencil or a bad method. */
+aop_status aop_ctx_autotune(aop_ctx *ctx, int64_t n, const aop_request *reqs, int32_t method,
+                            aop_options *best_out);
 
 /* Allocation-free variant of aop_linear_advance_device (the paper has no
  * counterpart; this is a deployment convenience).

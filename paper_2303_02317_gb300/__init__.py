@@ -49,7 +49,7 @@ class AopError(RuntimeError):
 
 class _Options(ctypes.Structure):
     _fields_ = [("method", ctypes.c_int32), ("base_case", ctypes.c_int32),
-                ("flags", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("flags", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32)]
 
 
 class _Stats(ctypes.Structure):
@@ -98,12 +98,13 @@ def load(path: Optional[str] = None):
                                                   i64, vp, vp, vp]
         lib.aop_ctx_get_stats.argtypes = [vp, ctypes.POINTER(_Stats)]
         lib.aop_ctx_get_option_times.argtypes = [vp, i64, vp]
+        lib.aop_ctx_autotune.argtypes = [vp, i64, vp, i32, ctypes.POINTER(_Options)]
         lib.aop_linear_advance_noalloc.argtypes = [ctypes.c_int, ctypes.c_int, vp, i64, i64, i64,
                                                    vp, vp, vp]
         lib.aop_linear_advance_noalloc.restype = ctypes.c_int
         for f in ("aop_ctx_get_option_times", "aop_ctx_create", "aop_ctx_destroy", "price_american", "price_american_ex",
                   "price_american_batch", "price_american_batch_device",
-                  "aop_linear_advance_device", "aop_ctx_get_stats"):
+                  "aop_linear_advance_device", "aop_ctx_get_stats", "aop_ctx_autotune"):
             getattr(lib, f).restype = ctypes.c_int
         _lib = lib
         return lib
@@ -136,8 +137,8 @@ FLAG_TILT_OFF = 2
 FLAG_TILT_ON = 4
 
 
-def _opts(method: int, base_case: int = 0, flags: int = 0) -> _Options:
-    return _Options(int(method), int(base_case), int(flags), 0)
+def _opts(method: int, base_case: int = 0, flags: int = 0, ctas_per_sm: int = 0) -> _Options:
+    return _Options(int(method), int(base_case), int(flags), int(ctas_per_sm))
 
 
 def requests_array(reqs: Iterable) -> np.ndarray:
@@ -225,12 +226,12 @@ class Context:
 
     # host buffers in, host buffers out (C: price_american_batch)
     def price_batch(self, reqs, method: int = FFT_FP64, base_case: int = 0, stream: int = 0,
-                    flags: int = 0):
+                    flags: int = 0, ctas_per_sm: int = 0):
         arr = reqs if isinstance(reqs, np.ndarray) else requests_array(reqs)
         n = len(arr)
         prices = np.empty(n, dtype=np.float64)
         status = np.empty(n, dtype=np.int32)
-        o = _opts(method, base_case, flags)
+        o = _opts(method, base_case, flags, ctas_per_sm)
         _check(load().price_american_batch(self._h, n, arr.ctypes.data, ctypes.byref(o),
                                            prices.ctypes.data, status.ctypes.data,
                                            ctypes.c_void_p(stream) if stream else None),
@@ -241,8 +242,8 @@ class Context:
     def price_batch_device(self, n: int, d_reqs: int, d_prices: int, d_status: int = 0,
                            d_boundary: int = 0, d_boundary_offsets: int = 0,
                            method: int = FFT_FP64, base_case: int = 0, stream: int = 0,
-                           flags: int = 0):
-        o = _opts(method, base_case, flags)
+                           flags: int = 0, ctas_per_sm: int = 0):
+        o = _opts(method, base_case, flags, ctas_per_sm)
         _check(load().price_american_batch_device(
             self._h, int(n), ctypes.c_void_p(d_reqs), ctypes.byref(o), ctypes.c_void_p(d_prices),
             ctypes.c_void_p(d_status) if d_status else None,
@@ -257,6 +258,16 @@ class Context:
                                                 int(h), ctypes.c_void_p(d_in), ctypes.c_void_p(d_out),
                                                 ctypes.c_void_p(stream) if stream else None),
                "aop_linear_advance_device")
+
+    def autotune(self, reqs, method: int) -> dict:
+        """Pick this context's default D&C schedule (base-case height and
+        options in flight per SM) for `method` by timing a sample of requests
+        (C: aop_ctx_autotune)."""
+        arr = reqs if isinstance(reqs, np.ndarray) else requests_array(reqs)
+        best = _Options()
+        _check(load().aop_ctx_autotune(self._h, len(arr), arr.ctypes.data, int(method), ctypes.byref(best)),
+               "aop_ctx_autotune")
+        return {"base_case": int(best.base_case), "ctas_per_sm": int(best.ctas_per_sm)}
 
     def option_times_ns(self, n: int) -> np.ndarray:
         out = np.empty(int(n), dtype=np.int64)

@@ -36,11 +36,14 @@ struct aop_ctx {
     int64_t last_n = 0;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;   // bracket the pricing kernels
     bool timed = false;
+    // autotuned D&C schedule per method (0 = not tuned)
+    int tuned_B[4] = {0, 0, 0, 0};
+    int tuned_cap[4] = {0, 0, 0, 0};
 };
 
 namespace {
 
-constexpr int kDefaultBaseCase = 16;
+constexpr int kDefaultBaseCase = 32;
 
 aop_status cuda_fail(cudaError_t e) {
     return e == cudaSuccess ? AOP_OK : (e == cudaErrorMemoryAllocation ? AOP_ENOMEM : AOP_ECUDA);
@@ -89,8 +92,11 @@ aop_status ensure_twiddles(aop_ctx *c, int log2n) {
     return AOP_OK;
 }
 
-int resolve_base_case(const aop_options *opt) {
-    int b = (opt && opt->base_case > 0) ? opt->base_case : kDefaultBaseCase;
+int resolve_base_case(const aop_ctx *c, const aop_options *opt) {
+    const int m = opt ? opt->method : 0;
+    int b = kDefaultBaseCase;
+    if (opt && opt->base_case > 0) b = opt->base_case;
+    else if (c && m >= 0 && m < 4 && c->tuned_B[m] > 0) b = c->tuned_B[m];
     int p = 1;
     while (p < b) p <<= 1;   // power of two
     if (p < 2) p = 2;
@@ -106,7 +112,7 @@ aop_status run_batch(aop_ctx *c, int64_t n, const aop_request *d_reqs, const aop
     const int method = opt ? opt->method : AOP_FFT_FP64;
     if (method < 0 || method > 3) return AOP_EINVAL;
     if (n == 0 || T_max < 1) return AOP_OK;
-    const int B = resolve_base_case(opt);
+    const int B = resolve_base_case(c, opt);
     CK(cudaMemsetAsync(c->d_stats, 0, sizeof(aop_stats), s));
     CK(cudaMemsetAsync(c->d_err, 0, sizeof(int), s));
     if (method == AOP_STENCIL_FP64) {
@@ -123,7 +129,9 @@ aop_status run_batch(aop_ctx *c, int64_t n, const aop_request *d_reqs, const aop
         aop_status st = ensure_twiddles(c, lg);
         if (st) return st;
         int grid = 0;
-        size_t need = dnc_workspace_bytes(method, n, T_max, B, &grid, c->device);
+        int cap = opt ? opt->ctas_per_sm : 0;
+        if (cap <= 0) cap = c->tuned_cap[method];
+        size_t need = dnc_workspace_bytes(method, n, T_max, B, cap, &grid, c->device);
         size_t have_cap = c->cap ? c->cap : need;
         if (need > have_cap) need = have_cap;   // fewer resident CTAs
         st = ensure(&c->ws, &c->ws_size, need, c->cap);
@@ -140,7 +148,7 @@ aop_status run_batch(aop_ctx *c, int64_t n, const aop_request *d_reqs, const aop
         CK(cudaEventRecord(c->ev0, s));
         CK(run_dnc(method, n, d_params, T_max, B, c->ws, c->ws_size, tw, c->tw_log2, d_prices,
                    d_status, d_bnd, d_bnd_off, c->d_stats, c->d_err, opt_ns, opt ? opt->flags : 0,
-                   c->device, s));
+                   cap, c->device, s));
         CK(cudaEventRecord(c->ev1, s));
     }
     c->timed = true;
@@ -383,6 +391,37 @@ aop_status aop_ctx_get_option_times(aop_ctx *c, int64_t n, int64_t *ns_out) {
     CK(cudaStreamSynchronize(c->stream));
     CK(cudaDeviceSynchronize());
     CK(cudaMemcpy(ns_out, c->d_opt_ns, (size_t)n * sizeof(int64_t), cudaMemcpyDeviceToHost));
+    return AOP_OK;
+}
+
+aop_status aop_ctx_autotune(aop_ctx *c, int64_t n, const aop_request *reqs, int32_t method,
+                            aop_options *best_out) {
+    if (!c || n <= 0 || !reqs || method < 0 || method > 3 || method == AOP_STENCIL_FP64) return AOP_EINVAL;
+    static const int kB[] = {16, 32, 64};
+    static const int kCap[] = {1, 2, 3, 4};
+    std::vector<double> prices((size_t)n);
+    std::vector<aop_status> status((size_t)n);
+    float best = -1.f;
+    int bB = 0, bCap = 0;
+    for (int B : kB) {
+        for (int cap : kCap) {
+            aop_options o{method, B, 0, cap};
+            float ms = 0.f;
+            for (int rep = 0; rep < 2; rep++) {   // the first run sizes the workspace
+                aop_status st = price_american_batch(c, n, reqs, &o, prices.data(), status.data(), nullptr);
+                if (st) return st;
+                CK(cudaEventElapsedTime(&ms, c->ev0, c->ev1));
+            }
+            if (best < 0.f || ms < best) {
+                best = ms;
+                bB = B;
+                bCap = cap;
+            }
+        }
+    }
+    c->tuned_B[method] = bB;
+    c->tuned_cap[method] = bCap;
+    if (best_out) *best_out = aop_options{method, bB, 0, bCap};
     return AOP_OK;
 }
 

@@ -835,25 +835,41 @@ struct Walker {
     // r < R, updated in place (ascending r, so the right neighbours a lane
     // reads by shuffle are still the previous row's).  The D cells right of
     // the divider hold their exercise values, so every red cell is the same
-    // D+1-point stencil.  The exercise values a row may need (cells bp .. bp+D,
-    // bp the previous divider: at most one per lane) are loaded before the
-    // stencil, so the per-row chain is shuffle -> stencil -> test.  A is the
-    // arithmetic (FP64, or doubled FP32 on the FP32 pipe).
+    // D+1-point stencil.  Row i needs exercise values at cells bp .. bp + D
+    // (bp the divider of row i+1); they lie in bp' - 1 .. bp' + D (bp' the
+    // divider one row up, the divider moving <= 1 cell per row), one cell per
+    // lane, so each lane loads its one value a row ahead and the per-row chain
+    // is shuffle -> stencil -> test.  A is the arithmetic (FP64, or doubled
+    // FP32 on the FP32 pipe).
     template <int R, class A>
     __device__ int64_t call_rows(int64_t i0, int64_t c0, int64_t b, int64_t h, const Buf &in, const Buf &out,
-                                 int64_t klo) {
+                                 int64_t klo, int64_t khi) {
         using T = typename A::T;
         const int D = P.D;
         const typename A::Wts w = A::weights(S);
         const T *ext = (const T *)exw;
+        // table slot of the exercise value of (row, column), clamped into the
+        // table: the columns past a row's end that can reach it are never read
+        const int64_t alpha = (P.model == AOP_BINOMIAL_CALL) ? 2 : 1;
+        const int64_t kofs = P.T - klo, kmax = khi - klo;
+        int32_t *const rec = (lane == 0) ? bnd : nullptr;
+        auto slot = [&](int64_t row, int64_t x) { return min(max(alpha * x - row + kofs, (int64_t)0), kmax); };
         T val[R];
 #pragma unroll
         for (int r = 0; r < R; r++) {
             const int64_t x = c0 + lane + 32 * r;
             val[r] = A::zero();
             if (x <= b) val[r] = A::template load<MODE>(in, x);
-            else if (x <= b + D) val[r] = ext[ex_index(P, i0, x) - klo];
+            else if (x <= b + D) val[r] = ext[slot(i0, x)];
         }
+        // this lane's column (relative to c0) among bb - 1 .. bb + D, or -1
+        auto cand = [&](int64_t bb) -> int64_t {
+            const int64_t d = bb - 1 - c0;
+            const int64_t t = d + ((lane - d) & 31);
+            return (t >= 0 && t <= d + D + 1) ? t : -1;
+        };
+        int64_t pt = cand(b);
+        T pre = (pt >= 0) ? ext[slot(i0 - 1, c0 + pt)] : A::zero();
         long long cells = 0;
         const long long lc0 = clock64();
         int64_t k = 1;
@@ -861,11 +877,10 @@ struct Walker {
             const int64_t i = i0 - k;
             const int64_t bp = b;
             if (bp < c0) break;
-            // this lane's cell among bp .. bp + D (if any) and its exercise value
-            const int64_t d = bp - c0;
-            const int64_t t = d + ((lane - d) & 31);
-            const int er = (t <= d + D) ? (int)(t >> 5) : -1;
-            const T ex1 = (er >= 0) ? ext[ex_index(P, i, c0 + t) - klo] : A::zero();
+            const T ex1 = pre;           // exercise value of row i at column c0 + t1
+            const int64_t t1 = pt;
+            pt = cand(bp);               // and of row i - 1 for the next row
+            pre = (pt >= 0) ? ext[slot(i - 1, c0 + pt)] : A::zero();
 #pragma unroll
             for (int r = 0; r < R; r++) {
                 const T nx = (r + 1 < R) ? val[(r + 1) % R] : A::zero();
@@ -883,6 +898,7 @@ struct Walker {
             } else {
                 // value-versus-payoff test at the previous divider (Cor. 2.7),
                 // taken by the lane that holds it (its ex1 is that cell's)
+                const int64_t d = bp - c0;
                 T tv = A::zero();
 #pragma unroll
                 for (int r = 0; r < R; r++)
@@ -892,11 +908,13 @@ struct Walker {
             }
             cells += min(bp, (int64_t)D * i) - c0 + 1;
             b = bn;
-            record(i, (int32_t)(b >= c0 ? b : c0 - 1));
+            if (rec) rec[i] = (int32_t)(b >= c0 ? b : c0 - 1);
             // cells right of the new divider take their exercise values
+            if (t1 >= 0 && c0 + t1 > b) {
 #pragma unroll
-            for (int r = 0; r < R; r++)
-                if (r == er && c0 + lane + 32 * r > b) val[r] = ex1;
+                for (int r = 0; r < R; r++)
+                    if (r == (int)(t1 >> 5)) val[r] = ex1;
+            }
         }
         if (lane == 0) cnt.loop_cyc += clock64() - lc0;
         if (k <= h) record_range(i0 - h, i0 - k, (int32_t)(c0 - 1));
@@ -916,11 +934,11 @@ struct Walker {
         A::fill(S, (typename A::T *)exw, klo, khi, lane);
         __syncwarp();
         if (lane == 0) cnt.fill_cyc += clock64() - fc0;
-        if (need <= 32) return call_rows<1, A>(i0, c0, b, h, in, out, klo);
-        if (need <= 64) return call_rows<2, A>(i0, c0, b, h, in, out, klo);
-        if (need <= 128) return call_rows<4, A>(i0, c0, b, h, in, out, klo);
-        if (need <= 256) return call_rows<8, A>(i0, c0, b, h, in, out, klo);
-        return call_rows<9, A>(i0, c0, b, h, in, out, klo);
+        if (need <= 32) return call_rows<1, A>(i0, c0, b, h, in, out, klo, khi);
+        if (need <= 64) return call_rows<2, A>(i0, c0, b, h, in, out, klo, khi);
+        if (need <= 128) return call_rows<4, A>(i0, c0, b, h, in, out, klo, khi);
+        if (need <= 256) return call_rows<8, A>(i0, c0, b, h, in, out, klo, khi);
+        return call_rows<9, A>(i0, c0, b, h, in, out, klo, khi);
     }
 
     __device__ int64_t naive_call_body(int64_t i0, int64_t c0, int64_t b, int64_t h, const Buf &in, const Buf &out) {
@@ -975,12 +993,23 @@ struct Walker {
             if (x <= hi) val[r] = (x <= f) ? ext[x - lo] : A::template load<MODE>(in, x);
         }
         long long cells = 0;
+        int32_t *const rec = (lane == 0) ? bnd : nullptr;
+        const int64_t span = hi - lo;
+        auto ld = [&](int64_t x) { return ext[min(max(x - lo, (int64_t)0), span)]; };
+        // exercise values at the cells the next test may take: f, f - 1 and
+        // the row's right end (loaded a row ahead)
+        T p0 = ld(f), p1 = ld(f - 1), p2 = ld(hi);
+        int64_t pf = f;
         int64_t L = lo, Rr = hi;
         for (int64_t k = 1; k <= h; k++) {
             const int64_t nl = L + 1, nr = Rr - 1;
             const int64_t fp = f;
             const bool test = (fp >= nl && fp <= nr);
-            const T te = test ? ext[fp - lo] : A::zero();
+            const T te = (fp == pf) ? p0 : ((fp == pf - 1) ? p1 : p2);
+            pf = fp;
+            p0 = ld(fp);
+            p1 = ld(fp - 1);
+            p2 = ld(nr);
             T prev = A::zero();
 #pragma unroll
             for (int r = 0; r < R; r++) {
@@ -1013,7 +1042,7 @@ struct Walker {
                 }
             }
             f = fn;
-            record(n + k, (f >= nl) ? (int32_t)f : (int32_t)AOP_BOUNDARY_NONE_PUT);
+            if (rec) rec[n + k] = (f >= nl) ? (int32_t)f : (int32_t)AOP_BOUNDARY_NONE_PUT;
             L = nl;
             Rr = nr;
         }
@@ -1352,7 +1381,11 @@ __global__ void __launch_bounds__(kThreadsD, kMinCtasPerSm) dnc_kernel(const __g
     if (threadIdx.x == 0) {
         unsigned smid;
         asm volatile("mov.u32 %0, %%smid;" : "=r"(smid));
-        s_walker = a.sm_slots ? (atomicAdd(&a.sm_slots[smid & 1023], 1) & 3) : 0;
+        // FP64 mode: one walker per SM sub-partition (each issues its FP64
+        // stencil on that partition's FP64 unit).  FP32 modes: all walkers on
+        // sub-partition 0, so that no walker shares issue slots with the
+        // convolution warps.
+        s_walker = (MODE == 0 && a.sm_slots) ? (atomicAdd(&a.sm_slots[smid & 1023], 1) & 3) : 0;
     }
     __syncthreads();
     int walker = 0;
@@ -1566,10 +1599,17 @@ int ctas_per_sm(int method, size_t smem) {
 
 }  // namespace
 
-size_t dnc_workspace_bytes(int method, int64_t n, int64_t T_max, int base_case, int *grid_out, int device)
+// One CTA per option in flight: as many per SM as fit (or `cap`), at most n.
+int64_t dnc_grid(int method, int64_t n, size_t smem, int cap, int device) {
+    int per_sm = ctas_per_sm(method, smem);
+    if (cap > 0 && cap < per_sm) per_sm = cap;
+    return std::min<int64_t>(n, (int64_t)sm_count(device) * per_sm);
+}
+
+size_t dnc_workspace_bytes(int method, int64_t n, int64_t T_max, int base_case, int cap, int *grid_out, int device)
 {
     Layout L = make_layout(method, T_max, base_case, kBigWorkers);
-    int64_t grid = std::min<int64_t>(n, (int64_t)sm_count(device) * ctas_per_sm(method, L.smem));
+    int64_t grid = dnc_grid(method, n, L.smem, cap, device);
     if (grid < 1) grid = 1;
     if (grid_out) *grid_out = (int)grid;
     return (size_t)(grid * L.stride + 8192);
@@ -1578,12 +1618,13 @@ size_t dnc_workspace_bytes(int method, int64_t n, int64_t T_max, int base_case, 
 cudaError_t run_dnc(int method, int64_t n, const Params *d_params, int64_t T_max, int base_case,
                     void *ws, size_t ws_bytes, const void *d_tw, int tw_log2, double *d_prices,
                     int32_t *d_status, int32_t *d_bnd, const int64_t *d_bnd_off,
-                    aop_stats *d_stats, int *d_err, int64_t *d_opt_ns, int flags, int device, cudaStream_t s)
+                    aop_stats *d_stats, int *d_err, int64_t *d_opt_ns, int flags, int cap, int device,
+                    cudaStream_t s)
 {
     if (n == 0) return cudaSuccess;
     Layout L = make_layout(method, T_max, base_case, kBigWorkers);
     if (tw_log2 < L.tw_log2) return cudaErrorInvalidValue;
-    int64_t grid = std::min<int64_t>(n, (int64_t)sm_count(device) * ctas_per_sm(method, L.smem));
+    int64_t grid = dnc_grid(method, n, L.smem, cap, device);
     const size_t need = (size_t)(grid * L.stride) + 8192;
     if (ws_bytes < need) {
         grid = (int64_t)((ws_bytes - 8192) / L.stride);

@@ -45,12 +45,13 @@ cudaError_t run_stencil(int64_t n, const Params *d_params, int64_t T_max, void *
                         const int64_t *d_bnd_off, aop_stats *d_stats, cudaStream_t s);
 
 // dnc.cu -- trapezoidal divide-and-conquer pricer
-size_t dnc_workspace_bytes(int method, int64_t n, int64_t T_max, int base_case, int *grid_out,
+size_t dnc_workspace_bytes(int method, int64_t n, int64_t T_max, int base_case, int cap, int *grid_out,
                            int device);
 cudaError_t run_dnc(int method, int64_t n, const Params *d_params, int64_t T_max, int base_case,
                     void *ws, size_t ws_bytes, const void *d_tw, int tw_log2, double *d_prices,
                     int32_t *d_status, int32_t *d_bnd, const int64_t *d_bnd_off,
-                    aop_stats *d_stats, int *d_err, int64_t *d_opt_ns, int flags, int device, cudaStream_t s);
+                    aop_stats *d_stats, int *d_err, int64_t *d_opt_ns, int flags, int cap, int device,
+                    cudaStream_t s);
 cudaError_t run_linear_advance(int method, int nw, const double *w, int64_t count, int64_t W,
                                int64_t h, const double *d_in, double *d_out, const void *d_tw,
                                int tw_log2, void *ws, size_t ws_bytes, int *d_err,
