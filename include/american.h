@@ -61,14 +61,17 @@ typedef enum {
     AOP_FFT_FP64 = 0,       /* trapezoidal D&C, FFT convolutions in FP64 */
     AOP_FFT_FP32SPLIT = 1,  /* trapezoidal D&C, FFT convolutions in FP32 on
                                hi/lo split inputs with hi/lo twiddles; base
-                               cases, boundary tests and root in FP64 */
+                               cases and boundary tests in doubled FP32 (see
+                               AOP_FFT_DF32), root in FP64 */
     AOP_STENCIL_FP64 = 2,   /* plain Theta(T^2) backward induction (Fig. 1 loop
                                and its trinomial / finite-difference analogues),
                                temporally blocked, FP64 */
     AOP_FFT_DF32 = 3        /* trapezoidal D&C, FFT convolutions in double-float
                                arithmetic (pairs of FP32 numbers, ~48-bit
-                               significands, on the FP32 pipe); base cases,
-                               boundary tests and root in FP64 */
+                               significands, on the FP32 pipe); base cases and
+                               boundary tests likewise (in FP64 where a
+                               window's prices span more than e^80); root in
+                               FP64 */
 } aop_method;
 
 typedef enum {
@@ -100,6 +103,10 @@ typedef struct aop_request {
  * (automatic).  These two bits force the tilt off or on for every call. */
 #define AOP_FLAG_TILT_OFF 2
 #define AOP_FLAG_TILT_ON 4
+/* D&C placement: in the FP32 modes every option's recursion warp runs on the
+ * same SM sub-partition, apart from the convolution warps; this bit spreads
+ * them one per sub-partition instead (the FP64 mode always spreads). */
+#define AOP_FLAG_SPREAD_WALKERS 8
 
 typedef struct aop_options {
     int32_t method;     /* aop_method */
@@ -138,6 +145,12 @@ typedef struct aop_stats {
     int64_t spectrum_bins;      /* D&C: kernel-power bins evaluated */
     int64_t basecase_loop_cycles;  /* D&C: SM cycles in the call base cases' row loops */
     int64_t basecase_fill_cycles;  /* D&C: SM cycles filling their exercise tables */
+    int64_t advance_count_by_log2n[24];  /* D&C: linear advances (worker warps) by
+                                            log2 of their transform length */
+    int64_t advance_ns_by_log2n[24];     /* ... and the worker time they took */
+    int64_t advance_phase_cycles[5];     /* single-tile advances, SM cycles summed over the
+                                            worker warps: spectrum lookup, input staging,
+                                            forward transform + product, inverse, store */
 } aop_stats;
 
 typedef struct aop_ctx aop_ctx;
@@ -225,7 +238,7 @@ aop_status aop_ctx_autotune(aop_ctx *ctx, int64_t n, const aop_request *reqs, in
  * owns the device memory, code that must not take the implicit device-wide
  * synchronisation of cudaMalloc/cudaFree.  It needs no context: its scratch
  * space (FFT work area, kernel-power band, twiddle tables) is one file-scope
- * device array of 6.8 MB (6.5 MiB) that every GPU loading the library keeps until
+ * device array of 7.3 MB (7.0 MiB) that every GPU loading the library keeps until
  * the process exits.  Inputs and outputs are the caller's device buffers, with
  * the same layout and meaning as in aop_linear_advance_device; the call is
  * asynchronous on `stream` (NULL = the legacy default stream) on the current

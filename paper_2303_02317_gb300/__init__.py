@@ -60,7 +60,9 @@ class _Stats(ctypes.Structure):
         ("walker_base_ns", ctypes.c_int64), ("basecase_calls", ctypes.c_int64),
         ("basecase_rows", ctypes.c_int64), ("walker_ns", ctypes.c_int64),
         ("spectrum_ns", ctypes.c_int64), ("spectrum_bins", ctypes.c_int64),
-        ("basecase_loop_cycles", ctypes.c_int64), ("basecase_fill_cycles", ctypes.c_int64)]
+        ("basecase_loop_cycles", ctypes.c_int64), ("basecase_fill_cycles", ctypes.c_int64),
+        ("advance_count_by_log2n", ctypes.c_int64 * 24), ("advance_ns_by_log2n", ctypes.c_int64 * 24),
+        ("advance_phase_cycles", ctypes.c_int64 * 5)]
 
 
 _lock = threading.Lock()
@@ -135,6 +137,8 @@ def _check(code: int, what: str = ""):
 FLAG_OPTION_TIMES = 1
 FLAG_TILT_OFF = 2
 FLAG_TILT_ON = 4
+FLAG_SPREAD_WALKERS = 8
+
 
 
 def _opts(method: int, base_case: int = 0, flags: int = 0, ctas_per_sm: int = 0) -> _Options:
@@ -278,6 +282,8 @@ class Context:
     def stats(self) -> dict:
         s = _Stats()
         _check(load().aop_ctx_get_stats(self._h, ctypes.byref(s)), "aop_ctx_get_stats")
-        out = {k: int(getattr(s, k)) for k, _ in _Stats._fields_ if k != "kernel_ms"}
-        out["kernel_ms"] = float(s.kernel_ms)
+        out = {}
+        for k, _ in _Stats._fields_:
+            v = getattr(s, k)
+            out[k] = float(v) if k == "kernel_ms" else ([int(x) for x in v] if hasattr(v, "__len__") else int(v))
         return out

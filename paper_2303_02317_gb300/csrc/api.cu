@@ -85,8 +85,8 @@ aop_status ensure_twiddles(aop_ctx *c, int log2n) {
     c->tw32 = c->tw64 = nullptr;
     c->tw_log2 = 0;
     size_t half = (size_t)1 << (log2n - 1);
-    CK(cudaMalloc(&c->tw32, half * sizeof(float4)));
-    CK(cudaMalloc(&c->tw64, half * sizeof(double2)));
+    CK(cudaMalloc(&c->tw32, 2 * half * sizeof(float4)));     // levels 1 .. log2n
+    CK(cudaMalloc(&c->tw64, 2 * half * sizeof(double2)));
     CK(launch_twiddles(log2n, c->tw32, c->tw64, c->stream));
     c->tw_log2 = log2n;
     return AOP_OK;

@@ -52,6 +52,7 @@ constexpr int kThreadsD = 32 * kWarps;
 constexpr int kWorkers = kWarps - 1;
 constexpr int kBigWorkers = 2;             // workers 1, 2 may take multi-pass transforms
 constexpr int kSpecSlots = 128;
+constexpr int kSpecLg = 22;                // log2 g and log2 N of directly indexed spectra
 constexpr int kLeftoverCall = 48;          // rows solved naively at the root
 constexpr int kMinCtasPerSm = 4;          // register budget: 4 options in flight per SM
 constexpr double kDfLogRange = 80.0;       // largest log price ratio of a doubled-FP32 base case
@@ -153,6 +154,8 @@ struct DncArgs {
 struct Counters {
     long long convs, fft_points, fft_flops, conv_in, conv_out, base_cells, gbytes, wait_ns, busy_ns, base_ns;
     long long base_calls, base_rows, walker_ns, spec_ns, spec_bins, loop_cyc, fill_cyc;
+    long long hist_n[24], hist_ns[24];   // linear advances by transform size log2 N
+    long long cv_cyc[5];                 // single-tile advances: spectrum, stage, forward+product, inverse, store
 };
 
 // Per-CTA shared state (static shared memory).
@@ -163,6 +166,8 @@ struct Shared {
     SpecEntry spec[kSpecSlots];
     int spec_n;
     int spec_lock;
+    // direct index of the entries with g a power of two: entry + 1 (0 = none)
+    volatile int16_t spec_map[kSpecLg][kSpecLg];
     long long arena_used;
     int opt;
     volatile int done;
@@ -355,6 +360,22 @@ struct Cta {
     // (arena exhausted).  Called by every thread of the group G.
     template <class G>
     __device__ const Sp *spectrum(int64_t g, int lgN, int &mc_out, ConvScale &cs) {
+        // fast path: a ready entry found through the direct index, no lock
+        const bool pow2 = g > 0 && (g & (g - 1)) == 0 && lgN < kSpecLg;
+        const int lgg = pow2 ? 63 - __clzll((unsigned long long)g) : 0;
+        if (pow2 && lgg < kSpecLg) {
+            const int v = S.spec_map[lgg][lgN];
+            if (v > 0) {
+                SpecEntry &e = S.spec[v - 1];
+                if (e.state == SPEC_READY) {
+                    __threadfence_block();
+                    mc_out = e.mc;
+                    cs.n0 = e.n0;
+                    cs.resid = e.resid;
+                    return arena() + e.off;
+                }
+            }
+        }
         int idx = -1, build = 0;
         if (leader<G>()) {
             const uint64_t t0 = gtime();
@@ -379,6 +400,7 @@ struct Cta {
                     S.arena_used += mc + 1;
                     __threadfence_block();
                     S.spec_n = idx + 1;
+                    if (pow2 && lgg < kSpecLg) S.spec_map[lgg][lgN] = (int16_t)(idx + 1);
                     build = 1;
                 } else {
                     idx = -1 - mc;   // no room: evaluate on the fly
@@ -574,20 +596,22 @@ struct Cta {
     // in [x_lo - o_min g, x_hi - (o_min + nw - 1) g].  The group G runs it on its
     // shared tile (2^lg_tile values) and, for longer transforms, on its global
     // scratch `scr`.
+    // returns log2 of the transform length (0: nothing to do)
     template <class G, class ST>
-    __device__ void conv(const Buf &in, int64_t x_lo, int64_t x_hi, const Buf &out, int64_t g, V *tile,
-                         int lg_tile, V *scr, Counters &cnt) {
+    __device__ int conv(const Buf &in, int64_t x_lo, int64_t x_hi, const Buf &out, int64_t g, V *tile,
+                        int lg_tile, V *scr, Counters &cnt) {
         const Params &Pp = P();
         const int64_t W = x_hi - x_lo + 1;
         const int64_t span = (int64_t)(Pp.nw - 1) * g;
         const int64_t y_lo = x_lo - (int64_t)Pp.o_min * g;
         const int64_t nout = W - span;
-        if (nout <= 0) return;
+        if (nout <= 0) return 0;
         int lgN = ilog2_ceil(W);
         if (lgN < 2) lgN = 2;
         const int64_t N = (int64_t)1 << lgN;
         int mc;
         ConvScale cs;
+        const long long q0 = clock64();
         const Sp *sp = spectrum<G>(g, lgN, mc, cs);
         cs.d = __longlong_as_double((long long)(1023 - lgN) << 52);
         cs.f = __int_as_float((127 - lgN) << 23);
@@ -602,16 +626,28 @@ struct Cta {
         const Tw *T = tw();
         const int twl = a.tw_log2;
         if (lgN <= lg_tile) {
+            const long long q1 = clock64();
             stage_input<G, ST>(tile, N, [](int64_t s) { return s; }, in, x_lo, W);
+            const long long q2 = clock64();
             fft::dif_range<MODE, G>(tile, N, lgN - 1, 0, T, twl);
             for (int64_t p = G::rank(); p < N; p += G::size())
                 tile[p] = mul_bin(tile[p], sp, mc, fft::brev_n((uint32_t)p, lgN), (uint32_t)N, g, lgN);
             G::sync();
+            const long long q3 = clock64();
             fft::dit_range<MODE, G>(tile, N, 0, lgN - 1, T, twl);
+            const long long q4 = clock64();
             for (int64_t t = G::rank(); t < nout; t += G::size())
                 store<ST>(out, y_lo + t, untilt<ST>(ST::from_v(tile[off + t], cs), W - 1 - t, cs));
             G::sync();
-            return;
+            if (leader<G>()) {
+                const long long q5 = clock64();
+                cnt.cv_cyc[0] += q1 - q0;
+                cnt.cv_cyc[1] += q2 - q1;
+                cnt.cv_cyc[2] += q3 - q2;
+                cnt.cv_cyc[3] += q4 - q3;
+                cnt.cv_cyc[4] += q5 - q4;
+            }
+            return lgN;
         }
         if (leader<G>()) cnt.gbytes += (int64_t)sizeof(V) * N * 4 + 8 * (W + nout);
         // outer stages lg_tile .. lgN-1 in chunks of at most lg_tile - 2 stages
@@ -645,6 +681,7 @@ struct Cta {
         for (int c = nch - 1; c >= 0; c--)
             tile_pass<G, ST, false>(tile, lg_tile, scr, lgN, ch_lo[c], ch_hi[c], false, c == 0, in, x_lo, W, out, y_lo,
                                 off, nout, cs);
+        return lgN;
     }
 };
 
@@ -848,39 +885,44 @@ struct Walker {
         const int D = P.D;
         const typename A::Wts w = A::weights(S);
         const T *ext = (const T *)exw;
-        // table slot of the exercise value of (row, column), clamped into the
-        // table: the columns past a row's end that can reach it are never read
-        const int64_t alpha = (P.model == AOP_BINOMIAL_CALL) ? 2 : 1;
-        const int64_t kofs = P.T - klo, kmax = khi - klo;
-        int32_t *const rec = (lane == 0) ? bnd : nullptr;
-        auto slot = [&](int64_t row, int64_t x) { return min(max(alpha * x - row + kofs, (int64_t)0), kmax); };
+        // 32-bit arithmetic relative to (i0, c0) inside the base case: column
+        // t = x - c0, row offset k = i0 - i.  The exercise value of (k, t)
+        // sits at slot sbase + alpha t + k of the table, clamped into it (the
+        // columns past a row's end that can reach the clamp are never read).
+        const int alpha = (P.model == AOP_BINOMIAL_CALL) ? 2 : 1;
+        const int sbase = (int)(alpha * c0 - i0 + P.T - klo);
+        const int kmax = (int)(khi - klo);
+        const int clip0 = (int)((int64_t)D * i0 - c0);   // row i0 - k ends at column clip0 - D k
+        const int hh = (int)h;
+        int32_t *const rec = (lane == 0 && bnd) ? bnd + i0 : nullptr;   // rec[-k] = row i0 - k
+        auto slot = [&](int k, int t) { return min(max(sbase + alpha * t + k, 0), kmax); };
+        int bb = (int)(b - c0);
         T val[R];
 #pragma unroll
         for (int r = 0; r < R; r++) {
-            const int64_t x = c0 + lane + 32 * r;
+            const int t = lane + 32 * r;
             val[r] = A::zero();
-            if (x <= b) val[r] = A::template load<MODE>(in, x);
-            else if (x <= b + D) val[r] = ext[slot(i0, x)];
+            if (t <= bb) val[r] = A::template load<MODE>(in, c0 + t);
+            else if (t <= bb + D) val[r] = ext[slot(0, t)];
         }
-        // this lane's column (relative to c0) among bb - 1 .. bb + D, or -1
-        auto cand = [&](int64_t bb) -> int64_t {
-            const int64_t d = bb - 1 - c0;
-            const int64_t t = d + ((lane - d) & 31);
+        // this lane's column among bb - 1 .. bb + D, or -1
+        auto cand = [&](int bq) -> int {
+            const int d = bq - 1;
+            const int t = d + ((lane - d) & 31);
             return (t >= 0 && t <= d + D + 1) ? t : -1;
         };
-        int64_t pt = cand(b);
-        T pre = (pt >= 0) ? ext[slot(i0 - 1, c0 + pt)] : A::zero();
-        long long cells = 0;
+        int pt = cand(bb);
+        T pre = (pt >= 0) ? ext[slot(1, pt)] : A::zero();
+        int cells = 0;
         const long long lc0 = clock64();
-        int64_t k = 1;
-        for (; k <= h; k++) {
-            const int64_t i = i0 - k;
-            const int64_t bp = b;
-            if (bp < c0) break;
-            const T ex1 = pre;           // exercise value of row i at column c0 + t1
-            const int64_t t1 = pt;
-            pt = cand(bp);               // and of row i - 1 for the next row
-            pre = (pt >= 0) ? ext[slot(i - 1, c0 + pt)] : A::zero();
+        int k = 1;
+        for (; k <= hh; k++) {
+            const int bp = bb;
+            if (bp < 0) break;
+            const T ex1 = pre;           // exercise value of row k at column t1
+            const int t1 = pt;
+            pt = cand(bp);               // and of row k + 1 for the next row
+            pre = (pt >= 0) ? ext[slot(k + 1, pt)] : A::zero();
 #pragma unroll
             for (int r = 0; r < R; r++) {
                 const T nx = (r + 1 < R) ? val[(r + 1) % R] : A::zero();
@@ -892,39 +934,39 @@ struct Walker {
                     val[r] = A::dot2(w, val[r], n1);
                 }
             }
-            int64_t bn;
-            if (bp - 1 >= (int64_t)D * i) {
-                bn = (int64_t)D * i;            // the row ends inside the window: all red
+            const int last = clip0 - D * k;          // last column of this row
+            int bn;
+            if (bp - 1 >= last) {
+                bn = last;                           // the row ends inside the window: all red
             } else {
                 // value-versus-payoff test at the previous divider (Cor. 2.7),
                 // taken by the lane that holds it (its ex1 is that cell's)
-                const int64_t d = bp - c0;
                 T tv = A::zero();
 #pragma unroll
                 for (int r = 0; r < R; r++)
-                    if (r == (int)(d >> 5)) tv = val[r];
-                const bool ge = __shfl_sync(0xffffffffu, A::cont_ge(tv, ex1), (int)(d & 31));
+                    if (r == (bp >> 5)) tv = val[r];
+                const bool ge = __shfl_sync(0xffffffffu, A::cont_ge(tv, ex1), bp & 31);
                 bn = ge ? bp : bp - 1;
             }
-            cells += min(bp, (int64_t)D * i) - c0 + 1;
-            b = bn;
-            if (rec) rec[i] = (int32_t)(b >= c0 ? b : c0 - 1);
+            cells += min(bp, last) + 1;
+            bb = bn;
+            if (rec) rec[-k] = (int32_t)(c0 + max(bb, -1));
             // cells right of the new divider take their exercise values
-            if (t1 >= 0 && c0 + t1 > b) {
+            if (t1 > bb) {
 #pragma unroll
                 for (int r = 0; r < R; r++)
-                    if (r == (int)(t1 >> 5)) val[r] = ex1;
+                    if (r == (t1 >> 5)) val[r] = ex1;
             }
         }
         if (lane == 0) cnt.loop_cyc += clock64() - lc0;
-        if (k <= h) record_range(i0 - h, i0 - k, (int32_t)(c0 - 1));
+        if (k <= hh) record_range(i0 - h, i0 - k, (int32_t)(c0 - 1));
 #pragma unroll
         for (int r = 0; r < R; r++) {
-            const int64_t x = c0 + lane + 32 * r;
-            if (x <= b) A::template store<MODE>(out, x, val[r]);
+            const int t = lane + 32 * r;
+            if (t <= bb) A::template store<MODE>(out, c0 + t, val[r]);
         }
         if (lane == 0) cnt.base_cells += cells;
-        return b;
+        return c0 + bb;
     }
 
     template <class A>
@@ -1384,8 +1426,9 @@ __global__ void __launch_bounds__(kThreadsD, kMinCtasPerSm) dnc_kernel(const __g
         // FP64 mode: one walker per SM sub-partition (each issues its FP64
         // stencil on that partition's FP64 unit).  FP32 modes: all walkers on
         // sub-partition 0, so that no walker shares issue slots with the
-        // convolution warps.
-        s_walker = (MODE == 0 && a.sm_slots) ? (atomicAdd(&a.sm_slots[smid & 1023], 1) & 3) : 0;
+        // convolution warps (AOP_FLAG_SPREAD_WALKERS: one per partition).
+        const bool spread = (MODE == 0) || (a.flags & AOP_FLAG_SPREAD_WALKERS);
+        s_walker = (spread && a.sm_slots) ? (atomicAdd(&a.sm_slots[smid & 1023], 1) & 3) : 0;
     }
     __syncthreads();
     int walker = 0;
@@ -1401,6 +1444,7 @@ __global__ void __launch_bounds__(kThreadsD, kMinCtasPerSm) dnc_kernel(const __g
             S.P = a.params[o];
             S.spec_n = 0;
             S.spec_lock = 0;
+            for (int j = 0; j < kSpecLg * kSpecLg; j++) (&S.spec_map[0][0])[j] = 0;
             S.arena_used = 0;
             S.done = 0;
             S.err = 0;
@@ -1477,13 +1521,18 @@ __global__ void __launch_bounds__(kThreadsD, kMinCtasPerSm) dnc_kernel(const __g
                 const uint64_t tb = gtime();
                 __threadfence_block();
                 const Task t = *(const Task *)&S.tasks[pick];
-                c.template conv<fft::WarpGroup, StoreCell<MODE>>(t.in, t.x_lo, t.x_hi, t.out, t.g, tile, a.lg_tile,
-                                                wid < kBigWorkers ? c.scratch(wid) : nullptr, cnt);
+                const int lgN = c.template conv<fft::WarpGroup, StoreCell<MODE>>(
+                    t.in, t.x_lo, t.x_hi, t.out, t.g, tile, a.lg_tile, wid < kBigWorkers ? c.scratch(wid) : nullptr,
+                    cnt);
                 __threadfence_block();
                 __syncwarp();
                 if (lane == 0) S.tasks[pick].state = TASK_DONE;
                 idle0 = gtime();
-                if (lane == 0) cnt.busy_ns += (long long)(idle0 - tb);
+                if (lane == 0) {
+                    cnt.busy_ns += (long long)(idle0 - tb);
+                    cnt.hist_n[min(lgN, 23)]++;
+                    cnt.hist_ns[min(lgN, 23)] += (long long)(idle0 - tb);
+                }
             }
         }
         __syncthreads();
@@ -1520,6 +1569,14 @@ __global__ void __launch_bounds__(kThreadsD, kMinCtasPerSm) dnc_kernel(const __g
         atomicAdd((unsigned long long *)&a.stats->spectrum_bins, (unsigned long long)(cnt.spec_bins + c.cnt_spec_bins));
         atomicAdd((unsigned long long *)&a.stats->basecase_loop_cycles, (unsigned long long)cnt.loop_cyc);
         atomicAdd((unsigned long long *)&a.stats->basecase_fill_cycles, (unsigned long long)cnt.fill_cyc);
+        for (int j = 0; j < 5; j++)
+            if (cnt.cv_cyc[j]) atomicAdd((unsigned long long *)&a.stats->advance_phase_cycles[j], (unsigned long long)cnt.cv_cyc[j]);
+        for (int j = 0; j < 24; j++) {
+            if (cnt.hist_n[j]) {
+                atomicAdd((unsigned long long *)&a.stats->advance_count_by_log2n[j], (unsigned long long)cnt.hist_n[j]);
+                atomicAdd((unsigned long long *)&a.stats->advance_ns_by_log2n[j], (unsigned long long)cnt.hist_ns[j]);
+            }
+        }
     }
 }
 
@@ -1696,6 +1753,7 @@ __global__ void __launch_bounds__(kThreadsD) advance_kernel(const __grid_constan
         S.P = P0;
         S.spec_n = 0;
         S.spec_lock = 0;
+        for (int j = 0; j < kSpecLg * kSpecLg; j++) (&S.spec_map[0][0])[j] = 0;
         S.arena_used = 0;
         S.err = 0;
     }
@@ -1791,7 +1849,7 @@ constexpr int kNoAllocCtas = 16;
 constexpr int kNoAllocTwLog2 = 15;                      // twiddles for N <= 2^15
 constexpr int64_t kNoAllocSpec = kNoAllocNmax / 2 + 2;  // one kernel power per call
 constexpr int64_t kNoAllocStride = kNoAllocNmax * 16 + kNoAllocSpec * 16;   // 16-byte values, worst case
-constexpr int64_t kNoAllocTwEntries = (int64_t)1 << (kNoAllocTwLog2 - 1);
+constexpr int64_t kNoAllocTwEntries = (int64_t)1 << kNoAllocTwLog2;   // levels 1 .. 15
 constexpr int64_t kNoAllocTw32Off = kNoAllocCtas * kNoAllocStride;
 constexpr int64_t kNoAllocTw64Off = kNoAllocTw32Off + kNoAllocTwEntries * 16;
 constexpr int64_t kNoAllocBytes = kNoAllocTw64Off + kNoAllocTwEntries * 16;

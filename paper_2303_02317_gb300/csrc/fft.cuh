@@ -90,16 +90,24 @@ __device__ __forceinline__ double2 cadd(double2 a, double2 b) { return make_doub
 __device__ __forceinline__ double2 csub(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
 __device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
 __device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+// Transform sums keep the low part unnormalised (the exact two-sum error of
+// the high parts plus the low parts): the next twiddle product renormalises,
+// and the extraction adds hi + lo.
+__device__ __forceinline__ void df_add_lazy(float ah, float al, float bh, float bl, float &rh, float &rl) {
+    float e;
+    two_sum(ah, bh, rh, e);
+    rl = e + (al + bl);
+}
 __device__ __forceinline__ df2 cadd(df2 a, df2 b) {
     df2 r;
-    df_add(a.v.x, a.v.z, b.v.x, b.v.z, r.v.x, r.v.z);
-    df_add(a.v.y, a.v.w, b.v.y, b.v.w, r.v.y, r.v.w);
+    df_add_lazy(a.v.x, a.v.z, b.v.x, b.v.z, r.v.x, r.v.z);
+    df_add_lazy(a.v.y, a.v.w, b.v.y, b.v.w, r.v.y, r.v.w);
     return r;
 }
 __device__ __forceinline__ df2 csub(df2 a, df2 b) {
     df2 r;
-    df_add(a.v.x, a.v.z, -b.v.x, -b.v.z, r.v.x, r.v.z);
-    df_add(a.v.y, a.v.w, -b.v.y, -b.v.w, r.v.y, r.v.w);
+    df_add_lazy(a.v.x, a.v.z, -b.v.x, -b.v.z, r.v.x, r.v.z);
+    df_add_lazy(a.v.y, a.v.w, -b.v.y, -b.v.w, r.v.y, r.v.w);
     return r;
 }
 // multiply by -i and by +i
@@ -128,28 +136,39 @@ __device__ __forceinline__ float2 twmul(float2 v, float4 w) {
     float im = fmaf(v.x, sh, fmaf(v.y, w.x, im_lo));
     return make_float2(re, im);
 }
-// double-float complex product with a double-float twiddle (hi.x, hi.y, lo.x, lo.y)
+// double-float complex product with a double-float twiddle (hi.x, hi.y, lo.x, lo.y):
+// each real part is p1 -+ p2 with the high products exact through FMA; the
+// products' low parts are summed unnormalised and the result renormalised once
 template <bool CONJ>
 __device__ __forceinline__ df2 twmul(df2 v, float4 w) {
     const float ch = w.x, cl = w.z;
     const float sh = CONJ ? -w.y : w.y, sl = CONJ ? -w.w : w.w;
-    float a_h, a_l, b_h, b_l, c_h, c_l, d_h, d_l;
-    df_mul(v.v.x, v.v.z, ch, cl, a_h, a_l);   // re * c
-    df_mul(v.v.y, v.v.w, sh, sl, b_h, b_l);   // im * s
-    df_mul(v.v.x, v.v.z, sh, sl, c_h, c_l);   // re * s
-    df_mul(v.v.y, v.v.w, ch, cl, d_h, d_l);   // im * c
+    const float xr = v.v.x, xrl = v.v.z, xi = v.v.y, xil = v.v.w;
+    // re = xr c - xi s
+    const float p1 = __fmul_rn(xr, ch), p2 = __fmul_rn(xi, sh);
+    float e1 = fmaf(xr, ch, -p1), e2 = fmaf(xi, sh, -p2);
+    e1 = fmaf(xr, cl, fmaf(xrl, ch, e1));
+    e2 = fmaf(xi, sl, fmaf(xil, sh, e2));
+    float s, t;
+    two_sum(p1, -p2, s, t);
     df2 r;
-    df_add(a_h, a_l, -b_h, -b_l, r.v.x, r.v.z);
-    df_add(c_h, c_l, d_h, d_l, r.v.y, r.v.w);
+    fast_two_sum(s, t + (e1 - e2), r.v.x, r.v.z);
+    // im = xr s + xi c
+    const float q1 = __fmul_rn(xr, sh), q2 = __fmul_rn(xi, ch);
+    float f1 = fmaf(xr, sh, -q1), f2 = fmaf(xi, ch, -q2);
+    f1 = fmaf(xr, sl, fmaf(xrl, sh, f1));
+    f2 = fmaf(xi, cl, fmaf(xil, ch, f2));
+    two_sum(q1, q2, s, t);
+    fast_two_sum(s, t + (f1 + f2), r.v.y, r.v.w);
     return r;
 }
 
-// Twiddle e^{-2 pi i k / 2^lg} for 0 <= k < 2^(lg-1) from the table of the
-// largest transform 2^tw_log2 (entries k' < 2^(tw_log2-1)).
+// Twiddle e^{-2 pi i k / 2^lg} for 0 <= k < 2^(lg-1): entry 2^(lg-1) + k of the
+// per-level table (levels 1 .. tw_log2).
 template <int MODE>
 __device__ __forceinline__ typename Cx<MODE>::Tw tw_get(const typename Cx<MODE>::Tw *tab, int tw_log2,
                                                        int64_t k, int lg) {
-    return __ldg(&tab[k << (tw_log2 - lg)]);
+    return __ldg(&tab[((int64_t)1 << (lg - 1)) + k]);    // level lg of the table, lg <= tw_log2
 }
 
 __device__ __forceinline__ uint32_t brev_n(uint32_t p, int lgN) {

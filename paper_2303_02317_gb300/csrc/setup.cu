@@ -31,19 +31,27 @@ __global__ void params_kernel(int64_t n, const aop_request *reqs, Params *params
 //   tw64[k]        = (cos, sin) in FP64
 //   tw32[2k], [2k+1] = hi and lo FP32 parts of the same value (the lo part is
 //                    the FP64 residual, so hi + lo carries ~48 bits).
+// Twiddle tables, one level per transform length: entry 2^(L-1) + k holds
+// e^{-2 pi i k / 2^L} for k < 2^(L-1), L = 1 .. log2n (entry 0 unused).  A
+// stage of half-size 2^(L-1) reads a contiguous run, so the short transforms
+// touch only the first few KB of the table.
 __global__ void twiddle_kernel(int log2n, float4 *tw32, double2 *tw64)
 {
-    const int64_t half = (int64_t)1 << (log2n - 1);
-    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < half;
-         k += (int64_t)gridDim.x * blockDim.x) {
-        double s, c;
-        // angle = -2 pi k / N = -pi * (k / (N/2)); sincospi takes the multiple of pi
-        sincospi(-(double)k / (double)half, &s, &c);
-        if (tw64) tw64[k] = make_double2(c, s);
+    const int64_t n = (int64_t)1 << log2n;
+    for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < n;
+         idx += (int64_t)gridDim.x * blockDim.x) {
+        double s = 0.0, c = 1.0;
+        if (idx > 0) {
+            const int L = 64 - __clzll((unsigned long long)idx);       // 2^(L-1) <= idx < 2^L
+            const int64_t half = (int64_t)1 << (L - 1);
+            // angle = -2 pi k / 2^L = -pi * (k / 2^(L-1)); sincospi takes the multiple of pi
+            sincospi(-(double)(idx - half) / (double)half, &s, &c);
+        }
+        if (tw64) tw64[idx] = make_double2(c, s);
         if (tw32) {
             float ch = (float)c, sh = (float)s;
             float cl = (float)(c - (double)ch), sl = (float)(s - (double)sh);
-            tw32[k] = make_float4(ch, sh, cl, sl);
+            tw32[idx] = make_float4(ch, sh, cl, sl);
         }
     }
 }
@@ -69,8 +77,8 @@ cudaError_t launch_params(int64_t n, const aop_request *d_reqs, Params *d_params
 
 cudaError_t launch_twiddles(int log2n, void *d_tw32, void *d_tw64, cudaStream_t s)
 {
-    int64_t half = (int64_t)1 << (log2n - 1);
-    int blocks = (int)std::min<int64_t>((half + 255) / 256, 4096);
+    const int64_t n = (int64_t)1 << log2n;      // entries per table
+    int blocks = (int)std::min<int64_t>((n + 255) / 256, 4096);
     twiddle_kernel<<<blocks, 256, 0, s>>>(log2n, (float4 *)d_tw32, (double2 *)d_tw64);
     return cudaGetLastError();
 }
