@@ -127,6 +127,51 @@ def cpu_oracle_sample(reqs, n_sample, budget_s=25.0):
     return len(done) / dt, dt, threads, desc, done, prices
 
 
+def serve_stream(ctx, aop, wl, method, args):
+    """Replay the serving stream -- n requests, exponential inter-arrival gaps
+    of mean 50 us (20k req/s), 40% binomial call / 40% trinomial call / 20%
+    BSM put, T = round(2^U[10,18]), seed 2317 -- through one serving session
+    (persistent kernel, requests published as they arrive), and serve the
+    stream's first requests with the plain FP64 stencil as one batch for
+    comparison.  Latency = completion seen by the host - scheduled arrival."""
+    T_MAX = 1 << 18
+    reqs, arrivals = wl.request_stream(n=args.serve_n, rate=20000.0, seed=2317)
+    arr = aop.requests_array(reqs)
+    t0 = time.perf_counter()
+    with aop.Server(ctx, capacity=len(reqs), T_max=T_MAX, method=method) as srv:
+        slots = srv.info()["slots"]
+        prices, status, lat = srv.serve_stream(arr, arrivals, timeout_s=1800.0)
+    wall = time.perf_counter() - t0
+    if (status != 0).any():
+        raise SystemExit("serving: status %s" % np.unique(status))
+    done_at = arrivals + lat
+    span = float(done_at.max() - arrivals.min())
+    out = {"requests": len(reqs), "offered_rate_per_s": 20000.0, "method": args.method,
+           "options_per_s": len(reqs) / span, "span_s": span, "wall_s": wall,
+           "latency_ms": {"p50": float(np.percentile(lat, 50) * 1e3), "p99": float(np.percentile(lat, 99) * 1e3),
+                          "max": float(lat.max() * 1e3), "mean": float(lat.mean() * 1e3)},
+           "slots": slots, "T_max": T_MAX,
+           "stream": "Poisson 20k req/s, 40% binomial call, 40% trinomial call, 20% BSM put, "
+                     "T=round(2^U[10,18]), seed 2317"}
+    m = args.serve_stencil_prefix
+    if m > 0:
+        # the stencil prices in batches: the prefix as one batch started when
+        # its last request has arrived
+        ps, ss = ctx.price_batch(arr[:m], method=aop.STENCIL_FP64)
+        kms = ctx.stats()["kernel_ms"]
+        start = float(arrivals[m - 1])
+        slat = (start + kms / 1e3) - arrivals[:m]
+        rel = np.abs(prices[:m] - ps) / np.maximum(np.abs(ps), 1e-300)
+        out["stencil_prefix"] = {
+            "requests": m, "options_per_s": m / (kms / 1e3), "kernel_ms": kms,
+            "latency_ms": {"p50": float(np.percentile(slat, 50) * 1e3), "p99": float(np.percentile(slat, 99) * 1e3)},
+            "fft_latency_ms_same_requests": {"p50": float(np.percentile(lat[:m], 50) * 1e3),
+                                             "p99": float(np.percentile(lat[:m], 99) * 1e3)},
+            "max_rel_fft_vs_stencil": float(rel[ps > 1e-3 * arr["K"][:m]].max()),
+            "what": "the first %d requests of the stream as one plain-stencil batch" % m}
+    return out
+
+
 def run_reference(args):
     """The reference arm: the CPU oracle (plain FP64 backward induction) on
     the host cores, each step a bounded sample of the same book."""
@@ -172,6 +217,10 @@ def main():
     ap.add_argument("--method", default="df32", choices=["fft32", "fft64", "df32"])
     ap.add_argument("--no-tune", action="store_true", help="library default schedule, no autotuning")
     ap.add_argument("--no-fp32", action="store_true", help="skip the split-FP32 side measurement")
+    ap.add_argument("--serve-n", type=int, default=65536,
+                    help="requests of the serving stream (Poisson 20k/s, mixed models, T in [2^10, 2^18]); 0 = skip")
+    ap.add_argument("--serve-stencil-prefix", type=int, default=128,
+                    help="requests of the stream's prefix also served by the plain FP64 stencil")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--stencil-sample", type=int, default=4)
     ap.add_argument("--small", action="store_true",
@@ -361,6 +410,11 @@ def main():
             cpu["max_rel_%s_vs_oracle" % args.method] = float(
                 np.max(np.abs(prices32[ii] - np.array(oprices)) / np.abs(oprices)))
 
+    # ---- serving: the Poisson request stream through a persistent session
+    serving = None
+    if args.serve_n > 0:
+        serving = serve_stream(ctx, aop, wl, method, args)
+
     value = world * n / (ms_step / 1e3)
     line = {
         "metric": "options_per_second", "value": value, "unit": "options/s", "n_gpus": world,
@@ -387,6 +441,7 @@ def main():
         "stencil_fp64": stencil,
         "speedup_vs_stencil_ms_per_option": (stencil["ms_per_option"] / (ms_step / n)) if stencil else None,
         "cpu_baseline": cpu,
+        "serving": serving,
         "kernel_stats": stats,
         "wall_s_timed": t_wall,
     }

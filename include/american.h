@@ -219,6 +219,50 @@ aop_status aop_linear_advance_device(aop_ctx *ctx, int method, int nw, const dou
  * (synchronizes the context's stream). */
 aop_status aop_ctx_get_stats(aop_ctx *ctx, aop_stats *out);
 
+/* ---------------------------------------------------------------- serving
+ * Continuous pricing of requests as they arrive (no counterpart in the
+ * paper, which prices one option per call).  A session runs one persistent
+ * pricing kernel: its CTAs -- one option each, as many as the context's
+ * workspace cap admits for requests up to T_max steps (aop_server_info) --
+ * take the next published request whenever they finish one, so requests that
+ * arrive while others are on the GPU start as soon as a slot frees, and
+ * short and long options of every model overlap on the device.  Requests and
+ * results travel through host memory mapped into the device: no copy or
+ * launch per request.  The kernel exits after 2 s without a request and is
+ * relaunched by the next call that finds published requests undone.
+ *
+ * Results are those of price_american_batch with the same options (each
+ * request is priced by the same kernel code on its own slot).  While a
+ * session lives, the context's batch calls return AOP_EBUSY.  One host thread
+ * drives a session at a time.  Errors: AOP_EINVAL (bad arguments; a method
+ * other than the three D&C pricers; a request with T > T_max gets that status
+ * in its result), AOP_EBUSY (capacity used up, or the context already serves),
+ * AOP_ENOMEM, AOP_ECUDA. */
+typedef struct aop_server aop_server;
+
+/* Start a session on ctx for at most `capacity` requests of up to T_max steps,
+ * priced with *opt (method, base case, flags, options per SM; NULL = FFT_FP64
+ * defaults). */
+aop_status aop_server_create(aop_ctx *ctx, int64_t capacity, int64_t T_max, const aop_options *opt,
+                             aop_server **out);
+/* Publish one request (copied); *id_out (nullable) receives its index. */
+aop_status aop_server_submit(aop_server *srv, const aop_request *req, int64_t *id_out);
+/* *done = 1 once request id is priced; then *price and *status (nullable)
+ * hold its result. */
+aop_status aop_server_poll(aop_server *srv, int64_t id, double *price, aop_status *status, int32_t *done);
+/* Replay a recorded stream: publish reqs[i] at arrival_ns[i] nanoseconds (non-
+ * decreasing) after the call starts, by the host's steady clock, and return
+ * when all n are priced (or AOP_ETIMEOUT timeout_s after the last arrival).
+ * latency_ns[i] (nullable) = completion seen by the host - scheduled arrival.
+ * prices and status (nullable) are host arrays of n. */
+aop_status aop_server_serve_stream(aop_server *srv, int64_t n, const aop_request *reqs,
+                                   const int64_t *arrival_ns, double *prices, aop_status *status,
+                                   int64_t *latency_ns, double timeout_s);
+/* Pricing slots of the session and requests published so far (nullable). */
+aop_status aop_server_info(const aop_server *srv, int64_t *slots, int64_t *published);
+/* Ask the kernel to stop, wait for the options in flight, free the session. */
+aop_status aop_server_destroy(aop_server *srv);
+
 /* Autotuner for the divide-and-conquer methods (no counterpart in the paper,
  * which fixes its base case by hand): prices the n host requests once per
  * schedule -- base-case height in {16, 32, 64} x options in flight per SM in

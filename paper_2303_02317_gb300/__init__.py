@@ -101,12 +101,21 @@ def load(path: Optional[str] = None):
         lib.aop_ctx_get_stats.argtypes = [vp, ctypes.POINTER(_Stats)]
         lib.aop_ctx_get_option_times.argtypes = [vp, i64, vp]
         lib.aop_ctx_autotune.argtypes = [vp, i64, vp, i32, ctypes.POINTER(_Options)]
+        lib.aop_server_create.argtypes = [vp, i64, i64, ctypes.POINTER(_Options), ctypes.POINTER(vp)]
+        lib.aop_server_submit.argtypes = [vp, vp, ctypes.POINTER(i64)]
+        lib.aop_server_poll.argtypes = [vp, i64, ctypes.POINTER(dbl), ctypes.POINTER(ctypes.c_int),
+                                        ctypes.POINTER(i32)]
+        lib.aop_server_serve_stream.argtypes = [vp, i64, vp, vp, vp, vp, vp, dbl]
+        lib.aop_server_info.argtypes = [vp, ctypes.POINTER(i64), ctypes.POINTER(i64)]
+        lib.aop_server_destroy.argtypes = [vp]
         lib.aop_linear_advance_noalloc.argtypes = [ctypes.c_int, ctypes.c_int, vp, i64, i64, i64,
                                                    vp, vp, vp]
         lib.aop_linear_advance_noalloc.restype = ctypes.c_int
         for f in ("aop_ctx_get_option_times", "aop_ctx_create", "aop_ctx_destroy", "price_american", "price_american_ex",
                   "price_american_batch", "price_american_batch_device",
-                  "aop_linear_advance_device", "aop_ctx_get_stats", "aop_ctx_autotune"):
+                  "aop_linear_advance_device", "aop_ctx_get_stats", "aop_ctx_autotune",
+                  "aop_server_create", "aop_server_submit", "aop_server_poll", "aop_server_serve_stream",
+                  "aop_server_info", "aop_server_destroy"):
             getattr(lib, f).restype = ctypes.c_int
         _lib = lib
         return lib
@@ -287,3 +296,66 @@ class Context:
             v = getattr(s, k)
             out[k] = float(v) if k == "kernel_ms" else ([int(x) for x in v] if hasattr(v, "__len__") else int(v))
         return out
+
+
+class Server:
+    """Continuous pricing session on a context (C: aop_server_*): one
+    persistent pricing kernel takes requests as they are published."""
+
+    def __init__(self, ctx: "Context", capacity: int, T_max: int, method: int = FFT_FP64,
+                 base_case: int = 0, flags: int = 0, ctas_per_sm: int = 0):
+        self.ctx = ctx
+        h = ctypes.c_void_p()
+        o = _opts(method, base_case, flags, ctas_per_sm)
+        _check(load().aop_server_create(ctx._h, int(capacity), int(T_max), ctypes.byref(o), ctypes.byref(h)),
+               "aop_server_create")
+        self._h = h
+
+    def submit(self, req) -> int:
+        arr = requests_array([req])
+        i = ctypes.c_int64()
+        _check(load().aop_server_submit(self._h, arr.ctypes.data, ctypes.byref(i)), "aop_server_submit")
+        return int(i.value)
+
+    def poll(self, i: int):
+        """(done, price, status) of request i."""
+        p, st, d = ctypes.c_double(), ctypes.c_int(), ctypes.c_int32()
+        _check(load().aop_server_poll(self._h, int(i), ctypes.byref(p), ctypes.byref(st), ctypes.byref(d)),
+               "aop_server_poll")
+        return bool(d.value), float(p.value), int(st.value)
+
+    def serve_stream(self, reqs, arrival_s, timeout_s: float = 600.0):
+        """Replay requests at their arrival times (seconds from now); returns
+        (prices, status, latency seconds)."""
+        arr = reqs if isinstance(reqs, np.ndarray) else requests_array(reqs)
+        n = len(arr)
+        arrival_ns = np.ascontiguousarray(np.rint(np.asarray(arrival_s, dtype=np.float64) * 1e9).astype(np.int64))
+        prices = np.empty(n, dtype=np.float64)
+        status = np.empty(n, dtype=np.int32)
+        lat = np.empty(n, dtype=np.int64)
+        _check(load().aop_server_serve_stream(self._h, n, arr.ctypes.data, arrival_ns.ctypes.data,
+                                              prices.ctypes.data, status.ctypes.data, lat.ctypes.data,
+                                              float(timeout_s)), "aop_server_serve_stream")
+        return prices, status, lat / 1e9
+
+    def info(self) -> dict:
+        a, b = ctypes.c_int64(), ctypes.c_int64()
+        _check(load().aop_server_info(self._h, ctypes.byref(a), ctypes.byref(b)), "aop_server_info")
+        return {"slots": int(a.value), "published": int(b.value)}
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().aop_server_destroy(self._h)
+            self._h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,5 +1,6 @@
 // api.cu -- the C ABI (include/american.h): contexts, workspace, batches.
 #include <algorithm>
+#include <chrono>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
@@ -39,6 +40,26 @@ struct aop_ctx {
     // autotuned D&C schedule per method (0 = not tuned)
     int tuned_B[4] = {0, 0, 0, 0};
     int tuned_cap[4] = {0, 0, 0, 0};
+    bool serving = false;            // a serving session holds the workspace
+};
+
+struct aop_server {
+    aop_ctx *ctx = nullptr;
+    cudaStream_t stream = nullptr;   // the persistent pricing kernel's stream
+    int method = 0, B = 0, cap = 0, flags = 0, slots = 0;
+    int64_t T_max = 0, capacity = 0;
+    // host memory mapped into the device: requests in, results out
+    aop_request *h_reqs = nullptr;
+    double *h_prices = nullptr;
+    int32_t *h_status = nullptr;
+    int32_t *h_done = nullptr;
+    long long *h_pub = nullptr;      // h_pub[0] = published, h_pub[1] = stop
+    unsigned long long *d_claim = nullptr;
+    aop_stats *d_stats = nullptr;
+    int *d_err = nullptr;
+    int64_t published = 0;
+    int64_t first_undone = 0;        // every request below is done
+    ServeSession sess{};
 };
 
 namespace {
@@ -111,6 +132,7 @@ aop_status run_batch(aop_ctx *c, int64_t n, const aop_request *d_reqs, const aop
 {
     const int method = opt ? opt->method : AOP_FFT_FP64;
     if (method < 0 || method > 3) return AOP_EINVAL;
+    if (c->serving) return AOP_EBUSY;
     if (n == 0 || T_max < 1) return AOP_OK;
     const int B = resolve_base_case(c, opt);
     CK(cudaMemsetAsync(c->d_stats, 0, sizeof(aop_stats), s));
@@ -422,6 +444,197 @@ aop_status aop_ctx_autotune(aop_ctx *c, int64_t n, const aop_request *reqs, int3
     c->tuned_B[method] = bB;
     c->tuned_cap[method] = bCap;
     if (best_out) *best_out = aop_options{method, bB, 0, bCap};
+    return AOP_OK;
+}
+
+// ------------------------------------------------------------ serving
+namespace {
+
+int64_t now_ns() {
+    return std::chrono::duration_cast<std::chrono::nanoseconds>(
+               std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+
+aop_status server_launch(aop_server *s) {
+    aop_ctx *c = s->ctx;
+    const void *tw = (s->method == AOP_FFT_FP64) ? c->tw64 : c->tw32;
+    CK(run_dnc(s->method, s->capacity, nullptr, s->T_max, s->B, c->ws, c->ws_size, tw, c->tw_log2, nullptr,
+               nullptr, nullptr, nullptr, s->d_stats, s->d_err, nullptr, s->flags, s->cap, c->device, s->stream,
+               &s->sess));
+    return AOP_OK;
+}
+
+bool server_done(const aop_server *s, int64_t id) {
+    return __atomic_load_n(&s->h_done[id], __ATOMIC_ACQUIRE) != 0;
+}
+
+// The persistent kernel exits after kIdleNs without a published request (and
+// on stop); relaunch it while published requests are still undone.
+aop_status server_ensure_running(aop_server *s) {
+    while (s->first_undone < s->published && server_done(s, s->first_undone)) s->first_undone++;
+    if (s->first_undone >= s->published) return AOP_OK;
+    const cudaError_t q = cudaStreamQuery(s->stream);
+    if (q == cudaErrorNotReady) return AOP_OK;
+    if (q != cudaSuccess) return cuda_fail(q);
+    if (__atomic_load_n(&s->h_pub[1], __ATOMIC_ACQUIRE)) return AOP_OK;
+    return server_launch(s);
+}
+
+}  // namespace
+
+aop_status aop_server_create(aop_ctx *c, int64_t capacity, int64_t T_max, const aop_options *opt,
+                             aop_server **out) {
+    if (!c || !out || capacity < 1 || T_max < 1 || T_max > AOP_MAX_T) return AOP_EINVAL;
+    const int method = opt ? opt->method : AOP_FFT_FP64;
+    if (method < 0 || method > 3 || method == AOP_STENCIL_FP64) return AOP_EINVAL;
+    if (c->serving) return AOP_EBUSY;
+    CK(cudaSetDevice(c->device));
+    aop_server *s = new aop_server;
+    s->ctx = c;
+    s->method = method;
+    s->B = resolve_base_case(c, opt);
+    s->cap = (opt && opt->ctas_per_sm > 0) ? opt->ctas_per_sm : c->tuned_cap[method];
+    s->flags = opt ? (opt->flags & ~AOP_FLAG_OPTION_TIMES) : 0;
+    s->T_max = T_max;
+    s->capacity = capacity;
+    aop_status st = AOP_OK;
+    auto fail = [&](aop_status e) {
+        aop_server_destroy(s);
+        return e;
+    };
+    int lg = ilog2_ceil(2 * T_max + 1);
+    if (lg < 13) lg = 13;
+    if ((st = ensure_twiddles(c, lg))) return fail(st);
+    int grid = 0;
+    size_t need = dnc_workspace_bytes(method, capacity, T_max, s->B, s->cap, &grid, c->device);
+    if (c->cap && need > c->cap) need = c->cap;     // admission: the slots the cap holds
+    if ((st = ensure(&c->ws, &c->ws_size, need, c->cap))) return fail(st);
+    s->slots = grid;
+    const size_t per = sizeof(aop_request) + sizeof(double) + 2 * sizeof(int32_t);
+    char *h = nullptr;
+    if (cudaHostAlloc((void **)&h, (size_t)capacity * per + 256, cudaHostAllocMapped | cudaHostAllocPortable) !=
+        cudaSuccess) {
+        cudaGetLastError();
+        return fail(AOP_ENOMEM);
+    }
+    memset(h, 0, (size_t)capacity * per + 256);
+    s->h_pub = (long long *)h;
+    s->h_reqs = (aop_request *)(h + 64);
+    s->h_prices = (double *)(s->h_reqs + capacity);
+    s->h_status = (int32_t *)(s->h_prices + capacity);
+    s->h_done = s->h_status + capacity;
+    char *d = nullptr;
+    if (cudaHostGetDevicePointer((void **)&d, h, 0) != cudaSuccess) return fail(AOP_ECUDA);
+    s->sess.pub = (const volatile long long *)d;
+    s->sess.stop = (const volatile int *)(d + sizeof(long long));
+    s->sess.reqs = (const aop_request *)(d + 64);
+    s->sess.prices = (double *)(d + 64 + capacity * sizeof(aop_request));
+    s->sess.status = (int32_t *)(d + 64 + capacity * (sizeof(aop_request) + sizeof(double)));
+    s->sess.done = (volatile int32_t *)(d + 64 + capacity * (sizeof(aop_request) + sizeof(double) +
+                                                               sizeof(int32_t)));
+    s->sess.capacity = capacity;
+    if (cudaMalloc(&s->d_claim, 64) != cudaSuccess || cudaMalloc(&s->d_stats, sizeof(aop_stats)) != cudaSuccess ||
+        cudaMalloc(&s->d_err, sizeof(int)) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(AOP_ENOMEM);
+    }
+    s->sess.claim = s->d_claim;
+    if (cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking) != cudaSuccess) return fail(AOP_ECUDA);
+    CK(cudaMemsetAsync(s->d_claim, 0, 64, s->stream));
+    CK(cudaMemsetAsync(s->d_stats, 0, sizeof(aop_stats), s->stream));
+    CK(cudaMemsetAsync(s->d_err, 0, sizeof(int), s->stream));
+    c->serving = true;
+    if ((st = server_launch(s))) return fail(st);
+    *out = s;
+    return AOP_OK;
+}
+
+aop_status aop_server_submit(aop_server *s, const aop_request *req, int64_t *id_out) {
+    if (!s || !req) return AOP_EINVAL;
+    if (s->published >= s->capacity) return AOP_EBUSY;
+    const int64_t id = s->published;
+    s->h_reqs[id] = *req;
+    __atomic_store_n(&s->h_pub[0], (long long)(id + 1), __ATOMIC_RELEASE);
+    s->published = id + 1;
+    if (id_out) *id_out = id;
+    return server_ensure_running(s);
+}
+
+aop_status aop_server_poll(aop_server *s, int64_t id, double *price, aop_status *status, int32_t *done) {
+    if (!s || !done || id < 0 || id >= s->published) return AOP_EINVAL;
+    *done = server_done(s, id) ? 1 : 0;
+    if (*done) {
+        if (price) *price = s->h_prices[id];
+        if (status) *status = (aop_status)s->h_status[id];
+    }
+    return server_ensure_running(s);
+}
+
+aop_status aop_server_serve_stream(aop_server *s, int64_t n, const aop_request *reqs, const int64_t *arrival_ns,
+                                   double *prices, aop_status *status, int64_t *latency_ns, double timeout_s) {
+    if (!s || n < 0 || (n > 0 && (!reqs || !arrival_ns))) return AOP_EINVAL;
+    if (s->published + n > s->capacity) return AOP_EBUSY;
+    const int64_t base = s->published;
+    std::vector<int64_t> pending;
+    pending.reserve(4096);
+    std::vector<int64_t> t_done((size_t)n, -1);
+    const int64_t t0 = now_ns();
+    const int64_t limit = t0 + (int64_t)(timeout_s * 1e9) + (n ? arrival_ns[n - 1] : 0);
+    int64_t next = 0, left = n;
+    aop_status st = AOP_OK;
+    auto sweep = [&]() {
+        const int64_t t = now_ns();
+        size_t w = 0;
+        for (size_t k = 0; k < pending.size(); k++) {
+            const int64_t i = pending[k];
+            if (server_done(s, base + i)) {
+                t_done[(size_t)i] = t;
+                left--;
+            } else {
+                pending[w++] = i;
+            }
+        }
+        pending.resize(w);
+    };
+    while (left > 0) {
+        const int64_t t = now_ns();
+        while (next < n && t - t0 >= arrival_ns[next]) {
+            if ((st = aop_server_submit(s, &reqs[next], nullptr))) return st;
+            pending.push_back(next);
+            next++;
+        }
+        sweep();
+        if ((st = server_ensure_running(s))) return st;
+        if (now_ns() > limit) return AOP_ETIMEOUT;
+    }
+    for (int64_t i = 0; i < n; i++) {
+        if (prices) prices[i] = s->h_prices[base + i];
+        if (status) status[i] = (aop_status)s->h_status[base + i];
+        if (latency_ns) latency_ns[i] = t_done[(size_t)i] - (t0 + arrival_ns[i]);
+    }
+    return AOP_OK;
+}
+
+aop_status aop_server_info(const aop_server *s, int64_t *slots, int64_t *published) {
+    if (!s) return AOP_EINVAL;
+    if (slots) *slots = s->slots;
+    if (published) *published = s->published;
+    return AOP_OK;
+}
+
+aop_status aop_server_destroy(aop_server *s) {
+    if (!s) return AOP_EINVAL;
+    if (s->h_pub) __atomic_store_n(&s->h_pub[1], 1ll, __ATOMIC_RELEASE);
+    if (s->stream) {
+        cudaStreamSynchronize(s->stream);
+        cudaStreamDestroy(s->stream);
+    }
+    if (s->h_pub) cudaFreeHost(s->h_pub);
+    if (s->d_claim) cudaFree(s->d_claim);
+    if (s->d_stats) cudaFree(s->d_stats);
+    if (s->d_err) cudaFree(s->d_err);
+    if (s->ctx) s->ctx->serving = false;
+    delete s;
     return AOP_OK;
 }
 

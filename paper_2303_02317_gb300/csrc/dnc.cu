@@ -149,7 +149,39 @@ struct DncArgs {
     aop_stats *stats;
     int64_t *opt_ns;       // per-option device time (nullable)
     int flags;             // AOP_FLAG_* bits
+    // serving session (sreq == nullptr in batch mode): requests are read from
+    // host memory as the host publishes them; prices, status and a done flag
+    // go back to host memory per request
+    const aop_request *sreq;
+    const volatile long long *spub;    // requests published so far
+    const volatile int *sstop;         // the host asks the kernel to exit
+    unsigned long long *sclaim;        // requests claimed so far (device memory)
+    volatile int32_t *sdone;           // 1 once request o's result is written
+    int64_t sT_max;                    // longest T the session's workspace holds
 };
+
+// Serving: claim the next published request, or -1 when the host asks the
+// kernel to stop or nothing is published for kIdleNs (the host relaunches the
+// kernel on its next request).  A request is claimed only once published, so
+// an exit never strands one.
+constexpr uint64_t kIdleNs = 2000000000ull;
+__device__ int64_t claim_published(const DncArgs &a) {
+    const uint64_t t0 = gtime();
+    for (;;) {
+        const unsigned long long q = *(volatile unsigned long long *)a.sclaim;
+        const long long p = *a.spub;
+        if ((long long)q < p) {
+            if (atomicCAS(a.sclaim, q, q + 1) == q) {
+                __threadfence_system();      // the request's fields after its publication
+                return (int64_t)q;
+            }
+            continue;
+        }
+        if (*a.sstop) return -1;
+        if (gtime() - t0 > kIdleNs) return -1;
+        __nanosleep(1000);
+    }
+}
 
 struct Counters {
     long long convs, fft_points, fft_flops, conv_in, conv_out, base_cells, gbytes, wait_ns, busy_ns, base_ns;
@@ -1149,7 +1181,7 @@ struct Walker {
                     sp--;
                     continue;
                 }
-                if (F.h <= c.a.B || F.depth + 1 >= kMaxDepth) {
+                if ((F.h <= c.a.B && F.b - F.c0 + 1 + D <= kRegCells) || F.h < 2 || F.depth + 1 >= kMaxDepth) {
                     ret = naive_call(F.i0, F.c0, F.b, F.h, F.in, F.out);
                     sp--;
                     continue;
@@ -1436,12 +1468,23 @@ __global__ void __launch_bounds__(kThreadsD, kMinCtasPerSm) dnc_kernel(const __g
         if (s_sub[w] == s_walker) { walker = w; break; }
     const int role = (warp - walker + kWarps) % kWarps;    // 0 = walker, 1..3 = workers
     for (;;) {
-        if (threadIdx.x == 0) S.opt = atomicAdd(a.queue, 1);
+        if (threadIdx.x == 0) S.opt = a.sreq ? claim_published(a) : atomicAdd(a.queue, 1);
         __syncthreads();
         const int64_t o = S.opt;
-        if (o >= a.n) break;
+        if (o < 0 || o >= a.n) break;
         if (threadIdx.x == 0) {
-            S.P = a.params[o];
+            if (a.sreq) {
+                // fresh (uncached) loads of the request from host memory
+                static_assert(sizeof(aop_request) % 8 == 0, "request is whole 8-byte words");
+                aop_request rq;
+                const unsigned long long *src = (const unsigned long long *)&a.sreq[o];
+                unsigned long long *dst = (unsigned long long *)&rq;
+                for (int k = 0; k < (int)(sizeof(aop_request) / 8); k++) dst[k] = __ldcv(src + k);
+                S.P = make_params(rq);
+                if (S.P.status == AOP_OK && S.P.T > a.sT_max) S.P.status = AOP_EINVAL;
+            } else {
+                S.P = a.params[o];
+            }
             S.spec_n = 0;
             S.spec_lock = 0;
             for (int j = 0; j < kSpecLg * kSpecLg; j++) (&S.spec_map[0][0])[j] = 0;
@@ -1452,7 +1495,14 @@ __global__ void __launch_bounds__(kThreadsD, kMinCtasPerSm) dnc_kernel(const __g
         }
         __syncthreads();
         if (S.P.status != AOP_OK) {
-            if (threadIdx.x == 0) a.prices[o] = __longlong_as_double(0x7ff8000000000000ll);
+            if (threadIdx.x == 0) {
+                a.prices[o] = __longlong_as_double(0x7ff8000000000000ll);
+                if (a.sreq) {
+                    a.status[o] = S.P.status;
+                    __threadfence_system();
+                    a.sdone[o] = 1;
+                }
+            }
             __syncthreads();
             continue;
         }
@@ -1547,6 +1597,11 @@ __global__ void __launch_bounds__(kThreadsD, kMinCtasPerSm) dnc_kernel(const __g
                 uint64_t t_end;
                 asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t_end));
                 a.opt_ns[o] = (int64_t)(t_end - t_start);
+            }
+            if (a.sreq) {
+                a.status[o] = err ? err : AOP_OK;
+                __threadfence_system();
+                a.sdone[o] = 1;
             }
         }
         __syncthreads();
@@ -1676,8 +1731,9 @@ cudaError_t run_dnc(int method, int64_t n, const Params *d_params, int64_t T_max
                     void *ws, size_t ws_bytes, const void *d_tw, int tw_log2, double *d_prices,
                     int32_t *d_status, int32_t *d_bnd, const int64_t *d_bnd_off,
                     aop_stats *d_stats, int *d_err, int64_t *d_opt_ns, int flags, int cap, int device,
-                    cudaStream_t s)
+                    cudaStream_t s, const ServeSession *srv)
 {
+    if (srv) n = srv->capacity;
     if (n == 0) return cudaSuccess;
     Layout L = make_layout(method, T_max, base_case, kBigWorkers);
     if (tw_log2 < L.tw_log2) return cudaErrorInvalidValue;
@@ -1720,6 +1776,17 @@ cudaError_t run_dnc(int method, int64_t n, const Params *d_params, int64_t T_max
     a.stats = d_stats;
     a.opt_ns = d_opt_ns;
     a.flags = flags;
+    if (srv) {
+        a.sreq = srv->reqs;
+        a.spub = srv->pub;
+        a.sstop = srv->stop;
+        a.sclaim = srv->claim;
+        a.sdone = srv->done;
+        a.sT_max = T_max;
+        a.prices = srv->prices;
+        a.status = srv->status;
+        a.params = nullptr;
+    }
     switch (method) {
     case AOP_FFT_FP64:
         dnc_kernel<0><<<(unsigned)grid, kThreadsD, L.smem, s>>>(a);

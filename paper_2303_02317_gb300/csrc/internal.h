@@ -47,11 +47,26 @@ cudaError_t run_stencil(int64_t n, const Params *d_params, int64_t T_max, void *
 // dnc.cu -- trapezoidal divide-and-conquer pricer
 size_t dnc_workspace_bytes(int method, int64_t n, int64_t T_max, int base_case, int cap, int *grid_out,
                            int device);
+// A serving session's host-shared state (see aop_server_* in the header):
+// requests and results live in mapped host memory, the claim counter on the
+// device.  run_dnc with a session prices the published requests in order of
+// claim instead of a batch of Params.
+struct ServeSession {
+    const aop_request *reqs;        // capacity entries (device view of host memory)
+    const volatile long long *pub;  // requests published by the host
+    const volatile int *stop;       // set by the host to end the kernel
+    unsigned long long *claim;      // device counter of claimed requests
+    volatile int32_t *done;         // per request: 1 once its result is written
+    double *prices;                 // per request (device view of host memory)
+    int32_t *status;
+    int64_t capacity;
+};
+
 cudaError_t run_dnc(int method, int64_t n, const Params *d_params, int64_t T_max, int base_case,
                     void *ws, size_t ws_bytes, const void *d_tw, int tw_log2, double *d_prices,
                     int32_t *d_status, int32_t *d_bnd, const int64_t *d_bnd_off,
                     aop_stats *d_stats, int *d_err, int64_t *d_opt_ns, int flags, int cap, int device,
-                    cudaStream_t s);
+                    cudaStream_t s, const ServeSession *srv = nullptr);
 cudaError_t run_linear_advance(int method, int nw, const double *w, int64_t count, int64_t W,
                                int64_t h, const double *d_in, double *d_out, const void *d_tw,
                                int tw_log2, void *ws, size_t ws_bytes, int *d_err,

@@ -83,6 +83,19 @@ def test_base_case_heights(ctx, method, B):
         _check(r, method, base_case=B)
 
 
+@pytest.mark.parametrize("method", [aop.FFT_FP64, aop.FFT_FP32SPLIT, aop.FFT_DF32], ids=["fft64", "fft32", "df32"])
+def test_wide_rows_at_the_largest_base_case(ctx, method):
+    """Whole rows red (no yield) with the largest base case: the chain's last
+    trapezoids are as wide as the lattice rows (up to 2 x 175 cells), wider
+    than one base case holds, and must be cut further."""
+    for T in (150, 170, 240):
+        for r in (wl.Request(1, 100.0, 100.0, 0.05, 0.0, 0.3, 1.0, T, math.sqrt(3)),
+                  wl.Request(1, 120.0, 100.0, 0.08, 1e-4, 0.2, 2.0, T, 0.0, 1),
+                  wl.Request(0, 100.0, 100.0, 0.05, 0.0, 0.3, 1.0, T),
+                  wl.Request(2, 100.0, 100.0, 0.05, 0.0, 0.3, 1.0, T)):
+            _check(r, method, base_case=64)
+
+
 @pytest.mark.parametrize("method", METHODS, ids=[MNAME[m] for m in METHODS])
 @pytest.mark.parametrize("T", [4095, 8192])
 def test_configs_mid_size(ctx, method, T):
