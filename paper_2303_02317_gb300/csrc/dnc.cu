@@ -47,14 +47,24 @@ namespace aop {
 
 namespace {
 
-constexpr int kWarps = 4;                  // walker + 3 workers
-constexpr int kThreadsD = 32 * kWarps;
-constexpr int kWorkers = kWarps - 1;
-constexpr int kBigWorkers = 2;             // workers 1, 2 may take multi-pass transforms
+// CTA shape: one walker warp plus three worker warps, up to four options in
+// flight per SM (min_ctas keeps 128 registers a thread).  Workers below `big`
+// may take multi-pass transforms (each owns a global scratch area).  Seven
+// workers per option (two options per SM) lost to this shape in the
+// doubled-FP32 mode: shorter waits, but slower base cases.
+template <int MODE> struct Shape {
+    static constexpr int warps = 4;
+    static constexpr int threads = 32 * warps;
+    static constexpr int workers = warps - 1;
+    static constexpr int big = 2;
+    static constexpr int min_ctas = 4;
+};
+inline int shape_workers(int) { return Shape<0>::workers; }
+inline int shape_big(int) { return Shape<0>::big; }
+constexpr int kThreadsA = 128;             // linear-advance entry points (block-level transforms)
 constexpr int kSpecSlots = 128;
 constexpr int kSpecLg = 22;                // log2 g and log2 N of directly indexed spectra
 constexpr int kLeftoverCall = 48;          // rows solved naively at the root
-constexpr int kMinCtasPerSm = 4;          // register budget: 4 options in flight per SM
 constexpr double kDfLogRange = 80.0;       // largest log price ratio of a doubled-FP32 base case
 constexpr int kRegCells = 288;             // widest base-case window: 9 registers per lane
 constexpr int kNaiveCap = 512;             // widest base-case window (cells) and exercise table
@@ -1429,7 +1439,8 @@ __device__ int64_t first_rows_put(Cta<MODE> &c, int32_t *bnd) {
 
 // ------------------------------------------------------------------ kernel
 template <int MODE>
-__global__ void __launch_bounds__(kThreadsD, kMinCtasPerSm) dnc_kernel(const __grid_constant__ DncArgs a)
+__global__ void __launch_bounds__(Shape<MODE>::threads, Shape<MODE>::min_ctas)
+dnc_kernel(const __grid_constant__ DncArgs a)
 {
     using V = typename fft::Cx<MODE>::V;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -1446,6 +1457,7 @@ __global__ void __launch_bounds__(kThreadsD, kMinCtasPerSm) dnc_kernel(const __g
     // one another.  The k-th CTA to arrive on an SM walks with the warp whose
     // hardware slot lies in sub-partition k mod 4.
     __shared__ int s_walker;
+    constexpr int kWarps = Shape<MODE>::warps;
     __shared__ int s_sub[kWarps];
     if (lane == 0) {
         unsigned wid_hw;
@@ -1466,7 +1478,7 @@ __global__ void __launch_bounds__(kThreadsD, kMinCtasPerSm) dnc_kernel(const __g
     int walker = 0;
     for (int w = 0; w < kWarps; w++)
         if (s_sub[w] == s_walker) { walker = w; break; }
-    const int role = (warp - walker + kWarps) % kWarps;    // 0 = walker, 1..3 = workers
+    const int role = (warp - walker + kWarps) % kWarps;    // 0 = walker, 1.. = workers
     for (;;) {
         if (threadIdx.x == 0) S.opt = a.sreq ? claim_published(a) : atomicAdd(a.queue, 1);
         __syncthreads();
@@ -1550,7 +1562,7 @@ __global__ void __launch_bounds__(kThreadsD, kMinCtasPerSm) dnc_kernel(const __g
                     else {
                         for (int d = kMaxDepth - 1; d >= 0; d--) {
                             if (S.tasks[d].state != TASK_POSTED) continue;
-                            if (wid >= kBigWorkers && S.tasks[d].lgN > a.lg_tile) continue;
+                            if (wid >= Shape<MODE>::big && S.tasks[d].lgN > a.lg_tile) continue;
                             if (atomicCAS((int *)&S.tasks[d].state, TASK_POSTED, TASK_CLAIMED) == TASK_POSTED) {
                                 pick = d;
                                 break;
@@ -1572,7 +1584,7 @@ __global__ void __launch_bounds__(kThreadsD, kMinCtasPerSm) dnc_kernel(const __g
                 __threadfence_block();
                 const Task t = *(const Task *)&S.tasks[pick];
                 const int lgN = c.template conv<fft::WarpGroup, StoreCell<MODE>>(
-                    t.in, t.x_lo, t.x_hi, t.out, t.g, tile, a.lg_tile, wid < kBigWorkers ? c.scratch(wid) : nullptr,
+                    t.in, t.x_lo, t.x_hi, t.out, t.g, tile, a.lg_tile, wid < Shape<MODE>::big ? c.scratch(wid) : nullptr,
                     cnt);
                 __threadfence_block();
                 __syncwarp();
@@ -1674,7 +1686,7 @@ Layout make_layout(int method, int64_t T_max, int B, int scratch_units) {
     L.off_spec = off;
     off += (L.spec_cap * 16 + 255) & ~255ll;
     L.stride = off;
-    L.smem = kNaiveCap * sizeof(double) + (size_t)kWorkers * ((size_t)L.vsz << L.lg_tile);
+    L.smem = kNaiveCap * sizeof(double) + (size_t)shape_workers(method) * ((size_t)L.vsz << L.lg_tile);
     return L;
 }
 
@@ -1694,7 +1706,8 @@ template <int MODE>
 int resident_ctas(size_t smem) {
     int per_sm = 0;
     cudaFuncSetAttribute(dnc_kernel<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, dnc_kernel<MODE>, kThreadsD, smem) != cudaSuccess) {
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, dnc_kernel<MODE>, Shape<MODE>::threads, smem) !=
+        cudaSuccess) {
         cudaGetLastError();
         per_sm = 2;
     }
@@ -1709,18 +1722,59 @@ int ctas_per_sm(int method, size_t smem) {
     }
 }
 
+// Dynamic shared memory that lets at most `want` CTAs share an SM, so that a
+// grid of SMs x want CTAs spreads evenly (the block scheduler may otherwise
+// fill some SMs up to the occupancy limit and leave others idle).
+template <int MODE>
+size_t spread_smem(size_t smem, int want, int device) {
+    if (resident_ctas<MODE>(smem) <= want) return smem;
+    int sm_bytes = 0, reserved = 0, optin = 0;
+    cudaDeviceGetAttribute(&sm_bytes, cudaDevAttrMaxSharedMemoryPerMultiprocessor, device);
+    cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, device);
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device);
+    cudaFuncAttributes fa;
+    if (cudaFuncGetAttributes(&fa, dnc_kernel<MODE>) != cudaSuccess) {
+        cudaGetLastError();
+        return smem;
+    }
+    size_t dyn = (size_t)(sm_bytes / want) - (size_t)reserved - fa.sharedSizeBytes;
+    dyn = std::min(dyn, (size_t)optin - fa.sharedSizeBytes) & ~(size_t)127;
+    while (dyn > smem && resident_ctas<MODE>(dyn) > want) dyn += 1024;     // rounding margin
+    while (dyn > smem && resident_ctas<MODE>(dyn) < want) dyn -= 1024;
+    dyn = std::max(dyn, smem);
+    cudaFuncSetAttribute(dnc_kernel<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
+    return dyn;
+}
+
+size_t spread_smem_any(int method, size_t smem, int want, int device) {
+    switch (method) {
+    case AOP_FFT_FP64: return spread_smem<0>(smem, want, device);
+    case AOP_FFT_FP32SPLIT: return spread_smem<1>(smem, want, device);
+    default: return spread_smem<2>(smem, want, device);
+    }
+}
+
 }  // namespace
 
-// One CTA per option in flight: as many per SM as fit (or `cap`), at most n.
-int64_t dnc_grid(int method, int64_t n, size_t smem, int cap, int device) {
+// Options in flight per SM: as many as fit, at most `cap`, and no more than
+// needed to give every SM its share of n options.
+int dnc_per_sm(int method, int64_t n, size_t smem, int cap, int device) {
     int per_sm = ctas_per_sm(method, smem);
     if (cap > 0 && cap < per_sm) per_sm = cap;
-    return std::min<int64_t>(n, (int64_t)sm_count(device) * per_sm);
+    const int64_t sms = sm_count(device);
+    const int64_t share = (n + sms - 1) / sms;
+    if (share >= 1 && share < per_sm) per_sm = (int)share;
+    return std::max(1, per_sm);
+}
+
+// One CTA per option in flight, at most n.
+int64_t dnc_grid(int method, int64_t n, size_t smem, int cap, int device) {
+    return std::min<int64_t>(n, (int64_t)sm_count(device) * dnc_per_sm(method, n, smem, cap, device));
 }
 
 size_t dnc_workspace_bytes(int method, int64_t n, int64_t T_max, int base_case, int cap, int *grid_out, int device)
 {
-    Layout L = make_layout(method, T_max, base_case, kBigWorkers);
+    Layout L = make_layout(method, T_max, base_case, shape_big(method));
     int64_t grid = dnc_grid(method, n, L.smem, cap, device);
     if (grid < 1) grid = 1;
     if (grid_out) *grid_out = (int)grid;
@@ -1735,7 +1789,7 @@ cudaError_t run_dnc(int method, int64_t n, const Params *d_params, int64_t T_max
 {
     if (srv) n = srv->capacity;
     if (n == 0) return cudaSuccess;
-    Layout L = make_layout(method, T_max, base_case, kBigWorkers);
+    Layout L = make_layout(method, T_max, base_case, shape_big(method));
     if (tw_log2 < L.tw_log2) return cudaErrorInvalidValue;
     int64_t grid = dnc_grid(method, n, L.smem, cap, device);
     const size_t need = (size_t)(grid * L.stride) + 8192;
@@ -1787,15 +1841,18 @@ cudaError_t run_dnc(int method, int64_t n, const Params *d_params, int64_t T_max
         a.status = srv->status;
         a.params = nullptr;
     }
+    // spread the grid: at most grid / SMs (rounded up) CTAs on any SM
+    const int64_t sms = sm_count(device);
+    const size_t smem = spread_smem_any(method, L.smem, (int)((grid + sms - 1) / sms), device);
     switch (method) {
     case AOP_FFT_FP64:
-        dnc_kernel<0><<<(unsigned)grid, kThreadsD, L.smem, s>>>(a);
+        dnc_kernel<0><<<(unsigned)grid, Shape<0>::threads, smem, s>>>(a);
         break;
     case AOP_FFT_FP32SPLIT:
-        dnc_kernel<1><<<(unsigned)grid, kThreadsD, L.smem, s>>>(a);
+        dnc_kernel<1><<<(unsigned)grid, Shape<1>::threads, smem, s>>>(a);
         break;
     default:
-        dnc_kernel<2><<<(unsigned)grid, kThreadsD, L.smem, s>>>(a);
+        dnc_kernel<2><<<(unsigned)grid, Shape<2>::threads, smem, s>>>(a);
         break;
     }
     return cudaGetLastError();
@@ -1805,7 +1862,7 @@ cudaError_t run_dnc(int method, int64_t n, const Params *d_params, int64_t T_max
 namespace {
 
 template <int MODE>
-__global__ void __launch_bounds__(kThreadsD) advance_kernel(const __grid_constant__ DncArgs a,
+__global__ void __launch_bounds__(kThreadsA) advance_kernel(const __grid_constant__ DncArgs a,
                                                             const __grid_constant__ Params P0, int64_t count,
                                                             int64_t W, int64_t h, const double *in, double *out)
 {
@@ -1837,7 +1894,7 @@ template <int MODE>
 void launch_advance(const DncArgs &a, const Params &P, int64_t grid, size_t smem, int64_t count, int64_t W,
                     int64_t h, const double *d_in, double *d_out, cudaStream_t s) {
     cudaFuncSetAttribute(advance_kernel<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    advance_kernel<MODE><<<(unsigned)grid, kThreadsD, smem, s>>>(a, P, count, W, h, d_in, d_out);
+    advance_kernel<MODE><<<(unsigned)grid, kThreadsA, smem, s>>>(a, P, count, W, h, d_in, d_out);
 }
 
 void launch_advance_any(int method, const DncArgs &a, const Params &P, int64_t grid, size_t smem, int64_t count,
