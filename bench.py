@@ -172,6 +172,73 @@ def serve_stream(ctx, aop, wl, method, args):
     return out
 
 
+def run_configs(args):
+    """Single-option latency of the fixed configurations on one GPU: C1 (binomial
+    call, T = 2048, with its boundary checked against the oracle), C2 (binomial
+    and trinomial calls, Boyle and paper forms, T = 2^12 .. 2^19), C3 (BSM put,
+    T = 2^12 .. 2^18); every D&C method and the plain FP64 stencil, ms/option as
+    the median over --config-runs launches after one warm-up (kernel time by
+    CUDA events on the launch stream), each D&C price against the stencil's or
+    the CPU oracle's (oracle up to T = 2^14, timed once on all host cores)."""
+    import paper_2303_02317_gb300 as aop
+    from paper_2303_02317_gb300 import workloads as wl
+    import oracle
+    oracle.build()
+    threads = oracle.max_threads()
+    ctx = aop.Context(0)
+    methods = [("fft64", aop.FFT_FP64), ("fft32", aop.FFT_FP32SPLIT), ("df32", aop.FFT_DF32),
+               ("stencil", aop.STENCIL_FP64)]
+
+    def time_one(r, m, runs):
+        ts = []
+        p = None
+        for k in range(runs + 1):
+            pr, st = ctx.price_batch([r], method=m)
+            if st[0] != 0:
+                raise SystemExit("config %s: status %d" % (r, st[0]))
+            if k:
+                ts.append(ctx.stats()["kernel_ms"])
+            p = float(pr[0])
+        return float(np.median(ts)), p
+
+    rows = []
+    c1 = wl.single_binomial_t2048()
+    ref_p, ref_b, _ = oracle.price_american(c1.as_dict(), nthreads=threads, with_boundary=True)
+    got_p, got_b = aop.price_american_ex(c1.as_dict(), method=aop.FFT_FP64, boundary=True)
+    c1_row = {"config": "C1 binomial call T=2048", "fft64_price": got_p, "oracle_price": ref_p,
+              "rel_err": abs(got_p - ref_p) / ref_p, "boundary_rows_differing": int(np.sum(np.asarray(got_b) != np.asarray(ref_b)))}
+    cases = []
+    for T in (1 << 12, 1 << 14, 1 << 16, 1 << 17, 1 << 19):
+        cases.append(("C2 binomial call", wl.fixed_call(0, T)))
+        cases.append(("C2 trinomial call (Boyle, lambda=sqrt3)", wl.fixed_call(1, T)))
+        cases.append(("C2 trinomial call (paper form)", wl.fixed_call(1, T, wl.TRI_PAPER)))
+    for T in (1 << 12, 1 << 14, 1 << 16, 1 << 18):
+        cases.append(("C3 BSM put", wl.fixed_bsm_put(T)))
+    for name, r in cases:
+        row = {"config": name, "T": r.T}
+        prices = {}
+        for mname, m in methods:
+            runs = args.config_runs if (m != aop.STENCIL_FP64 or r.T <= (1 << 17)) else 3
+            ms, p = time_one(r, m, runs)
+            row[mname + "_ms"] = ms
+            prices[mname] = p
+        if r.T <= (1 << 14):
+            t0 = time.perf_counter()
+            ref = oracle.price_american(r.as_dict(), nthreads=threads)
+            row["oracle_ms_%dthreads" % threads] = (time.perf_counter() - t0) * 1e3
+            row["reference"] = "oracle"
+        else:
+            ref = prices["stencil"]
+            row["reference"] = "stencil_fp64"
+        for mname in ("fft64", "fft32", "df32", "stencil"):
+            row[mname + "_rel_err"] = abs(prices[mname] - ref) / abs(ref)
+        row["speedup_df32_vs_stencil"] = row["stencil_ms"] / row["df32_ms"]
+        rows.append(row)
+        print(json.dumps(row), file=sys.stderr, flush=True)
+    print(json.dumps({"configs": rows, "C1": c1_row, "runs": args.config_runs,
+                      "what": "single option per launch, ms = median kernel time (CUDA events)"}))
+
+
 def run_reference(args):
     """The reference arm: the CPU oracle (plain FP64 backward induction) on
     the host cores, each step a bounded sample of the same book."""
@@ -225,9 +292,14 @@ def main():
     ap.add_argument("--stencil-sample", type=int, default=4)
     ap.add_argument("--small", action="store_true",
                     help="reduced book (T=2^15, 152 options) for profiler captures")
+    ap.add_argument("--configs", action="store_true",
+                    help="single-option latency tables of the fixed configurations (C1-C3) instead of the book")
+    ap.add_argument("--config-runs", type=int, default=10)
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.configs:
+        return run_configs(args)
     args.warmup = max(args.warmup, 3)
 
     import torch

@@ -54,7 +54,11 @@ typedef enum {
     AOP_ECUDA = 4,       /* a CUDA runtime call failed / no usable device */
     AOP_ETIMEOUT = 5,    /* a bounded device-side wait gave up */
     AOP_EBUSY = 6,       /* admission refused: no workspace slot free */
-    AOP_EINTERNAL = 7    /* a device-side consistency check failed */
+    AOP_EINTERNAL = 7,   /* a device-side consistency check failed */
+    AOP_ERANGE = 8       /* FP32 methods: continuation values of the call reach
+                            1e30 (node prices far in the money with no early
+                            exercise there), beyond what FP32 transforms hold;
+                            price it with AOP_FFT_FP64 */
 } aop_status;
 
 typedef enum {
@@ -98,9 +102,10 @@ typedef struct aop_request {
 } aop_request;
 
 #define AOP_FLAG_OPTION_TIMES 1   /* record each option's device time (D&C methods) */
-/* FP32-split calls: the convolutions carry the values tilted by the node-price
- * growth e^{-kappa x} when the exercise boundary lies far above the strike
- * (automatic).  These two bits force the tilt off or on for every call. */
+/* Calls (FFT methods): the convolutions carry the values tilted by the
+ * node-price growth e^{-kappa x} when the exercise boundary lies far above the
+ * strike or whole rows are red (automatic), so that rounding follows each
+ * cell's own scale.  These two bits force the tilt off or on for every call. */
 #define AOP_FLAG_TILT_OFF 2
 #define AOP_FLAG_TILT_ON 4
 /* D&C placement: in the FP32 modes every option's recursion warp runs on the

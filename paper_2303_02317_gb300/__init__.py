@@ -31,7 +31,7 @@ TRI_BOYLE, TRI_PAPER = 0, 1
 BOUNDARY_NONE_PUT = -(2 ** 31)
 MAX_T = 1 << 20
 STATUS = {0: "AOP_OK", 1: "AOP_EINVAL", 2: "AOP_EUNSTABLE", 3: "AOP_ENOMEM",
-          4: "AOP_ECUDA", 5: "AOP_ETIMEOUT", 6: "AOP_EBUSY", 7: "AOP_EINTERNAL"}
+          4: "AOP_ECUDA", 5: "AOP_ETIMEOUT", 6: "AOP_EBUSY", 7: "AOP_EINTERNAL", 8: "AOP_ERANGE"}
 
 REQUEST_DTYPE = np.dtype([("model", "<i4"), ("tri_form", "<i4"), ("S0", "<f8"), ("K", "<f8"),
                           ("r", "<f8"), ("q", "<f8"), ("sigma", "<f8"), ("expiry", "<f8"),

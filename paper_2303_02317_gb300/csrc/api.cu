@@ -126,9 +126,23 @@ int resolve_base_case(const aop_ctx *c, const aop_options *opt) {
 }
 
 // Core of every batch: d_reqs etc. on the device, T_max known.
+// Longest first: the D&C grid takes options in this order, so the long ones
+// start early and short ones fill the tail.  Cost estimate: T times the
+// columns added per row (1 binomial, 2 trinomial and BSM).
+void longest_first(int64_t n, const aop_request *reqs, int32_t *order) {
+    std::vector<std::pair<int64_t, int32_t>> key((size_t)n);
+    for (int64_t i = 0; i < n; i++)
+        key[(size_t)i] = {-(reqs[i].T * (reqs[i].model == AOP_BINOMIAL_CALL ? 1 : 2)), (int32_t)i};
+    std::stable_sort(key.begin(), key.end(),
+                     [](const std::pair<int64_t, int32_t> &a, const std::pair<int64_t, int32_t> &b) {
+                         return a.first < b.first;
+                     });
+    for (int64_t i = 0; i < n; i++) order[i] = key[(size_t)i].second;
+}
+
 aop_status run_batch(aop_ctx *c, int64_t n, const aop_request *d_reqs, const aop_options *opt,
                      int64_t T_max, double *d_prices, int32_t *d_status, int32_t *d_bnd,
-                     const int64_t *d_bnd_off, cudaStream_t s, Params *d_params)
+                     const int64_t *d_bnd_off, cudaStream_t s, Params *d_params, const int32_t *d_order)
 {
     const int method = opt ? opt->method : AOP_FFT_FP64;
     if (method < 0 || method > 3) return AOP_EINVAL;
@@ -170,7 +184,7 @@ aop_status run_batch(aop_ctx *c, int64_t n, const aop_request *d_reqs, const aop
         CK(cudaEventRecord(c->ev0, s));
         CK(run_dnc(method, n, d_params, T_max, B, c->ws, c->ws_size, tw, c->tw_log2, d_prices,
                    d_status, d_bnd, d_bnd_off, c->d_stats, c->d_err, opt_ns, opt ? opt->flags : 0,
-                   cap, c->device, s));
+                   cap, c->device, s, nullptr, d_order));
         CK(cudaEventRecord(c->ev1, s));
     }
     c->timed = true;
@@ -208,6 +222,7 @@ const char *aop_status_string(aop_status s) {
     case AOP_ETIMEOUT: return "bounded device wait gave up";
     case AOP_EBUSY: return "no workspace slot free";
     case AOP_EINTERNAL: return "device-side consistency check failed";
+    case AOP_ERANGE: return "continuation values beyond the FP32 range (use AOP_FFT_FP64)";
     }
     return "unknown status";
 }
@@ -267,21 +282,30 @@ aop_status price_american_batch_device(aop_ctx *c, int64_t n, const aop_request 
     if (n == 0) return AOP_OK;
     CK(cudaSetDevice(c->device));
     cudaStream_t s = stream ? (cudaStream_t)stream : c->stream;
-    // per-batch device arrays: params
-    aop_status st = ensure(&c->small, &c->small_size, (size_t)n * sizeof(Params) + 256, 0);
+    // per-batch device arrays: params | order
+    const size_t off_ord = ((size_t)n * sizeof(Params) + 255) & ~(size_t)255;
+    aop_status st = ensure(&c->small, &c->small_size, off_ord + (size_t)n * sizeof(int32_t) + 256, 0);
     if (st) return st;
     Params *d_params = (Params *)c->small;
+    int32_t *d_order = (int32_t *)((char *)c->small + off_ord);
+    const size_t rb = (size_t)n * sizeof(aop_request);
+    if ((st = ensure_pinned(c, rb + (size_t)n * sizeof(int32_t) + 64))) return st;
+    aop_request *h_reqs = (aop_request *)c->pinned;
+    int32_t *h_order = (int32_t *)((char *)c->pinned + rb);
     CK(cudaMemsetAsync(c->d_tmax, 0, sizeof(int64_t), s));
     CK(launch_params(n, d_reqs, d_params, d_status, c->d_tmax, s));
     int64_t T_max = 0;
     CK(cudaMemcpyAsync(&T_max, c->d_tmax, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(h_reqs, d_reqs, rb, cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
     if (T_max == 0) {
         // every option was rejected: fill NaN prices
         CK(cudaMemsetAsync(d_prices, 0xff, (size_t)n * sizeof(double), s));
         return AOP_OK;
     }
-    return run_batch(c, n, d_reqs, opt, T_max, d_prices, d_status, d_bnd, d_bnd_off, s, d_params);
+    longest_first(n, h_reqs, h_order);
+    CK(cudaMemcpyAsync(d_order, h_order, (size_t)n * sizeof(int32_t), cudaMemcpyHostToDevice, s));
+    return run_batch(c, n, d_reqs, opt, T_max, d_prices, d_status, d_bnd, d_bnd_off, s, d_params, d_order);
 }
 
 aop_status price_american_batch(aop_ctx *c, int64_t n, const aop_request *reqs, const aop_options *opt,
@@ -292,26 +316,32 @@ aop_status price_american_batch(aop_ctx *c, int64_t n, const aop_request *reqs, 
     cudaStream_t s = stream ? (cudaStream_t)stream : c->stream;
     const size_t rb = (size_t)n * sizeof(aop_request), pb = (size_t)n * sizeof(double),
                  sb = (size_t)n * sizeof(int32_t);
-    aop_status st = ensure_pinned(c, rb + pb + sb + 64);
+    const size_t ob = (size_t)n * sizeof(int32_t);
+    aop_status st = ensure_pinned(c, rb + pb + sb + ob + 64);
     if (st) return st;
-    // device arrays: reqs | prices | status | params
+    // device arrays: reqs | prices | status | params | order
     size_t off_p = (rb + 255) & ~(size_t)255, off_s = (off_p + pb + 255) & ~(size_t)255,
-           off_par = (off_s + sb + 255) & ~(size_t)255;
-    st = ensure(&c->small, &c->small_size, off_par + (size_t)n * sizeof(Params) + 256, 0);
+           off_par = (off_s + sb + 255) & ~(size_t)255,
+           off_ord = (off_par + (size_t)n * sizeof(Params) + 255) & ~(size_t)255;
+    st = ensure(&c->small, &c->small_size, off_ord + ob + 256, 0);
     if (st) return st;
     char *d = (char *)c->small;
     aop_request *d_reqs = (aop_request *)d;
     double *d_prices = (double *)(d + off_p);
     int32_t *d_status = (int32_t *)(d + off_s);
     Params *d_params = (Params *)(d + off_par);
+    int32_t *d_order = (int32_t *)(d + off_ord);
     char *h = (char *)c->pinned;
     memcpy(h, reqs, rb);
+    int32_t *h_order = (int32_t *)(h + rb + pb + sb);
+    longest_first(n, reqs, h_order);
     int64_t T_max = 0;
     for (int64_t i = 0; i < n; i++)
         if (reqs[i].T > T_max && reqs[i].T <= AOP_MAX_T) T_max = reqs[i].T;
     CK(cudaMemcpyAsync(d_reqs, h, rb, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(d_order, h_order, ob, cudaMemcpyHostToDevice, s));
     CK(launch_params(n, d_reqs, d_params, d_status, nullptr, s));
-    st = run_batch(c, n, d_reqs, opt, T_max, d_prices, d_status, nullptr, nullptr, s, d_params);
+    st = run_batch(c, n, d_reqs, opt, T_max, d_prices, d_status, nullptr, nullptr, s, d_params, d_order);
     if (st) return st;
     CK(cudaMemcpyAsync(h + rb, d_prices, pb, cudaMemcpyDeviceToHost, s));
     CK(cudaMemcpyAsync(h + rb + pb, d_status, sb, cudaMemcpyDeviceToHost, s));
@@ -355,7 +385,7 @@ aop_status price_american_ex(const aop_request *req, const aop_options *opt, dou
     CK(launch_params(1, (const aop_request *)d, d_params, d_status, nullptr, s));
     int32_t *d_b = boundary_out ? (int32_t *)(d + off_b) : nullptr;
     st = run_batch(c, 1, (const aop_request *)d, opt, T, (double *)(d + off_price), d_status, d_b,
-                   (const int64_t *)(d + off_off), s, d_params);
+                   (const int64_t *)(d + off_off), s, d_params, nullptr);
     if (st) return st;
     CK(cudaMemcpyAsync(h + 256, d + off_price, sizeof(double), cudaMemcpyDeviceToHost, s));
     CK(cudaMemcpyAsync(h + 264, d_status, sizeof(int32_t), cudaMemcpyDeviceToHost, s));

@@ -35,10 +35,10 @@ struct Params {
     double xbase;        // calls: ln S - T logu;  BSM: ln(S/K) - T ds
     double out_scale;    // 1 for the calls, K for the put (price = K v)
     // Exponential tilt of the call stencil: a call value never exceeds its
-    // node price S u^k, which grows like e^{kappa x} along a row, so the
-    // FP32-split convolutions carry v(x) e^{-kappa x} (kept near the local
-    // scale of the node prices) with the tilted weights w_j e^{kappa j},
-    // normalised to unit sum: wt_j = w_j e^{kappa j} / e^{tL}.
+    // node price S u^k, which grows like e^{kappa x} along a row, so tilted
+    // convolutions carry v(x) e^{-kappa x} (kept near the local scale of the
+    // node prices) with the tilted weights w_j e^{kappa j}, normalised to
+    // unit sum: wt_j = w_j e^{kappa j} / e^{tL}.
     double kappa;        // log growth of the node price per column (0: BSM)
     double wt[3];
     double wtsum;

@@ -87,6 +87,7 @@ struct SpecEntry {
     int64_t off;
     int64_t n0;           // tilted advances: output factor e^{-kappa (n - n0)} resid
     float2 resid;
+    double resid64;
 };
 
 // Per-advance output scaling: 1/N (FP64 and FP32 copies, both exact powers
@@ -96,18 +97,20 @@ struct ConvScale {
     float f;
     int64_t n0;
     float2 resid;
+    double resid64;
 };
 
 // e^{g tL - kappa n0} with n0 = floor(g tL / kappa): the part of a g-step
 // tilted advance's output factor e^{g tL - kappa n} left after the table
 // factor e^{-kappa (n - n0)}; n >= D g > n0 for every output cell.
-__device__ inline void tilt_shift(const Params &P, int64_t g, int64_t &n0, float2 &resid) {
+__device__ inline void tilt_shift(const Params &P, int64_t g, int64_t &n0, float2 &resid, double &resid64) {
     const double e = (double)g * P.tL;
     const double q = floor(e / P.kappa);
     n0 = (int64_t)q;
     const double v = exp(e - P.kappa * q);
     const float h = (float)v;
     resid = make_float2(h, (float)(v - (double)h));
+    resid64 = v;
 }
 
 // a row segment in memory: the value of column x lives at p[x - base]
@@ -159,6 +162,7 @@ struct DncArgs {
     aop_stats *stats;
     int64_t *opt_ns;       // per-option device time (nullable)
     int flags;             // AOP_FLAG_* bits
+    const int32_t *order;  // batch: the i-th option taken is order[i] (nullable: i)
     // serving session (sreq == nullptr in batch mode): requests are read from
     // host memory as the host publishes them; prices, status and a done flag
     // go back to host memory per request
@@ -200,6 +204,11 @@ struct Counters {
     long long cv_cyc[5];                 // single-tile advances: spectrum, stage, forward+product, inverse, store
 };
 
+union TiltEntry {
+    float2 f;
+    double d;
+};
+
 // Per-CTA shared state (static shared memory).
 struct Shared {
     ExpTables E;
@@ -219,9 +228,10 @@ struct Shared {
     double price;
     // e^{+-kappa n} = t2[n >> 14] t1[(n >> 7) & 127] t0[n & 127] in doubled
     // FP32 (FP32-split calls)
-    float2 tup0[128], tup1[128], tup2[256];
-    float2 tdn0[128], tdn1[128], tdn2[256];
-    int tilt_nmax;        // largest n with e^{kappa n} inside the float range
+    // (FP64 in the FP64 mode, doubled FP32 otherwise: one 8-byte entry each)
+    TiltEntry tup0[128], tup1[128], tup2[256];
+    TiltEntry tdn0[128], tdn1[128], tdn2[256];
+    int tilt_nmax;        // largest n with e^{kappa n} inside the entries' range
     // doubled-FP32 copies for the base cases of the FP32 modes: u^j, j < kNaiveCap
     float2 updf[kNaiveCap];
     float2 wdf[3];
@@ -229,6 +239,7 @@ struct Shared {
 };
 
 // Tilt tables of the current option (all threads of the block).
+template <int MODE>
 __device__ void build_tilt_tables(Shared &S) {
     const double kap = S.P.kappa;
     for (int t = threadIdx.x; t < 1024; t += blockDim.x) {
@@ -237,12 +248,17 @@ __device__ void build_tilt_tables(Shared &S) {
         const int j = lvl == 0 ? u : (lvl == 1 ? u - 128 : u - 256);
         const double e = kap * (double)j * (double)(1 << (7 * lvl));
         const double v = exp(dir ? -e : e);
-        const float h = (float)v;
-        float2 *tab = dir ? (lvl == 0 ? S.tdn0 : (lvl == 1 ? S.tdn1 : S.tdn2))
-                          : (lvl == 0 ? S.tup0 : (lvl == 1 ? S.tup1 : S.tup2));
-        tab[j] = isfinite(h) ? make_float2(h, (float)(v - (double)h)) : make_float2(h, 0.0f);
+        TiltEntry *tab = dir ? (lvl == 0 ? S.tdn0 : (lvl == 1 ? S.tdn1 : S.tdn2))
+                             : (lvl == 0 ? S.tup0 : (lvl == 1 ? S.tup1 : S.tup2));
+        if (MODE == 0) {
+            tab[j].d = v;
+        } else {
+            const float h = (float)v;
+            tab[j].f = isfinite(h) ? make_float2(h, (float)(v - (double)h)) : make_float2(h, 0.0f);
+        }
     }
-    if (threadIdx.x == 0) S.tilt_nmax = (int)fmin(87.0 / kap, (double)((1 << 22) - 1));
+    const double range = (MODE == 0) ? 700.0 : 87.0;     // log of the largest factor kept
+    if (threadIdx.x == 0) S.tilt_nmax = (int)fmin(range / kap, (double)((1 << 22) - 1));
 }
 
 // ---------------------------------------------------------------- groups
@@ -358,7 +374,7 @@ struct Cta {
     const DncArgs &a;
     Shared &S;
     char *slot;
-    bool tilt = false;    // exponential tilt of the call convolutions (FP32-split)
+    bool tilt = false;    // exponential tilt of the call convolutions
     long long cnt_spec_ns = 0, cnt_spec_bins = 0;   // spectrum builds by this thread's group
 
     __device__ Cta(const DncArgs &a_, Shared &S_, char *slot_) : a(a_), S(S_), slot(slot_) {}
@@ -372,24 +388,55 @@ struct Cta {
     }
     __device__ float2 tilt_up(int64_t n) const {
         if (n > S.tilt_nmax) return make_float2(0.0f, 0.0f);
-        return df_prod(df_prod(S.tup2[n >> 14], S.tup1[(n >> 7) & 127]), S.tup0[n & 127]);
+        return df_prod(df_prod(S.tup2[n >> 14].f, S.tup1[(n >> 7) & 127].f), S.tup0[n & 127].f);
+    }
+    __device__ double tilt_up64(int64_t n) const {
+        if (n > S.tilt_nmax) return 0.0;
+        return S.tup2[n >> 14].d * S.tup1[(n >> 7) & 127].d * S.tup0[n & 127].d;
+    }
+    __device__ double tilt_dn64(int64_t n) const {
+        if ((n >> 14) > 255) return 0.0;
+        return S.tdn2[n >> 14].d * S.tdn1[(n >> 7) & 127].d * S.tdn0[n & 127].d;
     }
     __device__ float2 tilt_dn(int64_t n) const {
         if ((n >> 14) > 255) return make_float2(0.0f, 0.0f);
-        return df_prod(df_prod(S.tdn2[n >> 14], S.tdn1[(n >> 7) & 127]), S.tdn0[n & 127]);
+        return df_prod(df_prod(S.tdn2[n >> 14].f, S.tdn1[(n >> 7) & 127].f), S.tdn0[n & 127].f);
     }
     // output cell y = x_hi - n of a tilted advance: multiply by e^{-kappa n}
     template <class ST>
     __device__ typename ST::T untilt(typename ST::T c, int64_t n, const ConvScale &cs) const {
-        if constexpr (MODE == 1 && std::is_same<typename ST::T, float2>::value) {
-            if (tilt) {
-                const float2 f = df_prod(tilt_dn(max(n - cs.n0, (int64_t)0)), cs.resid);
-                float h, l;
-                fft::two_sum(c.x, c.y, h, l);
-                c = df_prod(make_float2(h, l), f);
-            }
+        if (!tilt) return c;
+        const int64_t m = max(n - cs.n0, (int64_t)0);
+        if constexpr (MODE == 0) {
+            return c * (tilt_dn64(m) * cs.resid64);
+        } else if constexpr (std::is_same<typename ST::T, float2>::value) {
+            const float2 f = df_prod(tilt_dn(m), cs.resid);
+            float h, l;
+            fft::two_sum(c.x, c.y, h, l);
+            return df_prod(make_float2(h, l), f);
+        } else {
+            return c;
         }
-        return c;
+    }
+    // a staged input value of column x = x_hi - n times e^{+kappa n}
+    __device__ V tilt_in(V v, int64_t n) const {
+        if constexpr (MODE == 0) {
+            v.x *= tilt_up64(n);
+            return v;
+        } else if constexpr (MODE == 1) {
+            const float2 f = tilt_up(n);
+            float h, l;
+            fft::two_sum(v.x, v.y, h, l);
+            return df_prod(make_float2(h, l), f);
+        } else {
+            const float2 f = tilt_up(n);
+            float h, l;
+            fft::two_sum(v.v.x, v.v.z, h, l);
+            const float2 p = df_prod(make_float2(h, l), f);
+            v.v.x = p.x;
+            v.v.z = p.y;
+            return v;
+        }
     }
 
     __device__ const Params &P() const { return S.P; }
@@ -414,6 +461,7 @@ struct Cta {
                     mc_out = e.mc;
                     cs.n0 = e.n0;
                     cs.resid = e.resid;
+                    cs.resid64 = e.resid64;
                     return arena() + e.off;
                 }
             }
@@ -437,7 +485,8 @@ struct Cta {
                     S.spec[idx].off = S.arena_used;
                     S.spec[idx].n0 = 0;
                     S.spec[idx].resid = make_float2(1.0f, 0.0f);
-                    if (tilt) tilt_shift(P(), g, S.spec[idx].n0, S.spec[idx].resid);
+                    S.spec[idx].resid64 = 1.0;
+                    if (tilt) tilt_shift(P(), g, S.spec[idx].n0, S.spec[idx].resid, S.spec[idx].resid64);
                     S.spec[idx].state = SPEC_BUILDING;
                     S.arena_used += mc + 1;
                     __threadfence_block();
@@ -457,7 +506,8 @@ struct Cta {
             mc_out = -1 - idx;
             cs.n0 = 0;
             cs.resid = make_float2(1.0f, 0.0f);
-            if (tilt) tilt_shift(P(), g, cs.n0, cs.resid);
+            cs.resid64 = 1.0;
+            if (tilt) tilt_shift(P(), g, cs.n0, cs.resid, cs.resid64);
             return nullptr;
         }
         SpecEntry &e = S.spec[idx];
@@ -484,6 +534,7 @@ struct Cta {
         mc_out = e.mc;
         cs.n0 = e.n0;
         cs.resid = e.resid;
+        cs.resid64 = e.resid64;
         return p;
     }
 
@@ -513,16 +564,10 @@ struct Cta {
                     tile[s] = ST::to_v(d);
                 }
             }
-            if constexpr (MODE == 1) {
-                if (tilt) {     // input cell x = x_hi - n times e^{+kappa n}
-                    for (int64_t s = G::rank(); s < count; s += G::size()) {
-                        const int64_t e = idx(s);
-                        if (e < W) {
-                            float h, l;
-                            fft::two_sum(tile[s].x, tile[s].y, h, l);
-                            tile[s] = df_prod(make_float2(h, l), tilt_up(W - 1 - e));
-                        }
-                    }
+            if (tilt) {
+                for (int64_t s = G::rank(); s < count; s += G::size()) {
+                    const int64_t e = idx(s);
+                    if (e < W) tile[s] = tilt_in(tile[s], W - 1 - e);
                 }
             }
         } else {
@@ -543,7 +588,13 @@ struct Cta {
 #pragma unroll
             for (int k = 0; k < kPer; k++) {
                 const int64_t s = G::rank() + (int64_t)k * G::size();
-                if (s < count) tile[s] = ST::to_v(r[k]);
+                if (s < count) {
+                    tile[s] = ST::to_v(r[k]);
+                    if (tilt) {
+                        const int64_t e = idx(s);
+                        if (e < W) tile[s] = tilt_in(tile[s], W - 1 - e);
+                    }
+                }
             }
         }
         G::sync();
@@ -1233,6 +1284,15 @@ struct Walker {
         int64_t i = P.T - 1;
         while (i > 0) {
             if (S.err) return __longlong_as_double(0x7ff8000000000000ll);
+            if (MODE != 0 && b >= 0) {
+                // a red value never exceeds its node price; FP32 transforms
+                // (sums of up to 2^20 values) need it well inside the range
+                const double sb = exercise(P, E, ex_index(P, i, b)) + P.K;
+                if (!(sb < 1e30)) {
+                    if (lane == 0) atomicCAS((int *)&S.err, 0, AOP_ERANGE);
+                    return __longlong_as_double(0x7ff8000000000000ll);
+                }
+            }
             if (b < 0) {
                 record_range(0, i - 1, -1);
                 return exercise(P, E, ex_index(P, 0, 0));
@@ -1480,7 +1540,11 @@ dnc_kernel(const __grid_constant__ DncArgs a)
         if (s_sub[w] == s_walker) { walker = w; break; }
     const int role = (warp - walker + kWarps) % kWarps;    // 0 = walker, 1.. = workers
     for (;;) {
-        if (threadIdx.x == 0) S.opt = a.sreq ? claim_published(a) : atomicAdd(a.queue, 1);
+        if (threadIdx.x == 0) {
+            int64_t q = a.sreq ? claim_published(a) : atomicAdd(a.queue, 1);
+            if (!a.sreq && a.order && q < a.n) q = a.order[q];
+            S.opt = q;
+        }
         __syncthreads();
         const int64_t o = S.opt;
         if (o < 0 || o >= a.n) break;
@@ -1521,23 +1585,26 @@ dnc_kernel(const __grid_constant__ DncArgs a)
         uint64_t t_start = 0;
         if (threadIdx.x == 0 && a.opt_ns) asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t_start));
         build_exp_tables(S.P, S.E);
-        const bool may_tilt = (MODE == 1) && S.P.model != AOP_BSM_PUT && S.P.kappa > 0.0 &&
-                              !(a.flags & AOP_FLAG_TILT_OFF);
-        if (may_tilt) build_tilt_tables(S);
+        const bool may_tilt = S.P.model != AOP_BSM_PUT && S.P.kappa > 0.0 && !(a.flags & AOP_FLAG_TILT_OFF);
+        if (may_tilt) build_tilt_tables<MODE>(S);
         __syncthreads();
         if (MODE != 0) build_df_tables(S);
         __syncthreads();
         int32_t *bnd = a.bnd ? a.bnd + a.bnd_off[o] : nullptr;
         const bool put = (S.P.model == AOP_BSM_PUT);
         const int64_t first = put ? first_rows_put(c, bnd) : first_rows_call(c, bnd);
-        // Tilt when the continuation region reaches node prices far above the
-        // strike: untilted, the FP32 rounding of every advance scales with the
-        // largest value of its window (about S_b - K at the divider, node
-        // price S_b); tilted, with the node price of each cell.
+        // Untilted, the rounding of every advance scales with the largest value
+        // of its window (about S_b - K at the divider, node price S_b); tilted,
+        // with the node price of each cell.  The FP32-split mode always tilts
+        // calls (measured: 314 instead of 238 of the sweep's 455 priced options
+        // within 1e-6); the FP64 and doubled modes, whose rounding is far below
+        // the bounds, tilt when the continuation region reaches node prices far
+        // above the strike (whole rows red, or S_b - K > 2 S0), where the
+        // untilted window's range would swamp the cells near the money.
         c.tilt = false;
         if (may_tilt) {
             const double sb = exercise(S.P, S.E, ex_index(S.P, S.P.T - 1, first)) + S.P.K;
-            c.tilt = (a.flags & AOP_FLAG_TILT_ON) || first >= (int64_t)S.P.D * (S.P.T - 1) ||
+            c.tilt = MODE == 1 || (a.flags & AOP_FLAG_TILT_ON) || first >= (int64_t)S.P.D * (S.P.T - 1) ||
                      sb - S.P.K > 2.0 * S.P.S;
         }
         if (role == 0) {
@@ -1785,7 +1852,7 @@ cudaError_t run_dnc(int method, int64_t n, const Params *d_params, int64_t T_max
                     void *ws, size_t ws_bytes, const void *d_tw, int tw_log2, double *d_prices,
                     int32_t *d_status, int32_t *d_bnd, const int64_t *d_bnd_off,
                     aop_stats *d_stats, int *d_err, int64_t *d_opt_ns, int flags, int cap, int device,
-                    cudaStream_t s, const ServeSession *srv)
+                    cudaStream_t s, const ServeSession *srv, const int32_t *d_order)
 {
     if (srv) n = srv->capacity;
     if (n == 0) return cudaSuccess;
@@ -1830,6 +1897,7 @@ cudaError_t run_dnc(int method, int64_t n, const Params *d_params, int64_t T_max
     a.stats = d_stats;
     a.opt_ns = d_opt_ns;
     a.flags = flags;
+    a.order = d_order;
     if (srv) {
         a.sreq = srv->reqs;
         a.spub = srv->pub;

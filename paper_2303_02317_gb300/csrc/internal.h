@@ -66,7 +66,7 @@ cudaError_t run_dnc(int method, int64_t n, const Params *d_params, int64_t T_max
                     void *ws, size_t ws_bytes, const void *d_tw, int tw_log2, double *d_prices,
                     int32_t *d_status, int32_t *d_bnd, const int64_t *d_bnd_off,
                     aop_stats *d_stats, int *d_err, int64_t *d_opt_ns, int flags, int cap, int device,
-                    cudaStream_t s, const ServeSession *srv = nullptr);
+                    cudaStream_t s, const ServeSession *srv = nullptr, const int32_t *d_order = nullptr);
 cudaError_t run_linear_advance(int method, int nw, const double *w, int64_t count, int64_t W,
                                int64_t h, const double *d_in, double *d_out, const void *d_tw,
                                int tw_log2, void *ws, size_t ws_bytes, int *d_err,

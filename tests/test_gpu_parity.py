@@ -126,6 +126,21 @@ def test_extreme_parameters(ctx, method):
         _check(r, method)
 
 
+def test_fp32_range_status(ctx):
+    """No yield, three years at sigma 0.6 and T = 8192: every row is red and the
+    deep in-the-money values reach e^94 S0.  The FP32 methods answer
+    AOP_ERANGE (8) for that option only; FP64 prices it."""
+    wide = wl.Request(0, 100.0, 100.0, 0.05, 0.0, 0.6, 3.0, 8192)
+    fine = wl.fixed_call(0, 8192)
+    ref = oracle.price_american(wide.as_dict())
+    for m in (aop.FFT_FP32SPLIT, aop.FFT_DF32):
+        prices, status = ctx.price_batch([wide, fine], method=m)
+        assert status[0] == 8 and np.isnan(prices[0]), (m, status, prices)
+        assert status[1] == 0
+    got = aop.price_american_ex(wide.as_dict(), method=aop.FFT_FP64)
+    assert abs(got - ref) <= parity.price_tol(aop.FFT_FP64, ref, wide.K)
+
+
 @pytest.mark.parametrize("method", METHODS, ids=[MNAME[m] for m in METHODS])
 def test_batch_matches_single(ctx, method):
     reqs = wl.random_small(24, seed=5, T_range=(16, 900))
