@@ -47,17 +47,19 @@ namespace aop {
 
 namespace {
 
-// CTA shape: one walker warp plus three worker warps, up to four options in
-// flight per SM (min_ctas keeps 128 registers a thread).  Workers below `big`
+// CTA shape: one walker warp plus three worker warps.  Workers below `big`
 // may take multi-pass transforms (each owns a global scratch area).  Seven
 // workers per option (two options per SM) lost to this shape in the
-// doubled-FP32 mode: shorter waits, but slower base cases.
+// doubled-FP32 mode: shorter waits, but slower base cases.  min_ctas sets the
+// register budget: 128 a thread for four options per SM (FP32-split), 255 for
+// two (doubled FP32 and FP64, whose transforms need the registers and whose
+// best schedules keep two options per SM).
 template <int MODE> struct Shape {
     static constexpr int warps = 4;
     static constexpr int threads = 32 * warps;
     static constexpr int workers = warps - 1;
     static constexpr int big = 2;
-    static constexpr int min_ctas = 4;
+    static constexpr int min_ctas = (MODE == 1) ? 4 : 2;
 };
 inline int shape_workers(int) { return Shape<0>::workers; }
 inline int shape_big(int) { return Shape<0>::big; }
