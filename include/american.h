@@ -55,10 +55,10 @@ typedef enum {
     AOP_ETIMEOUT = 5,    /* a bounded device-side wait gave up */
     AOP_EBUSY = 6,       /* admission refused: no workspace slot free */
     AOP_EINTERNAL = 7,   /* a device-side consistency check failed */
-    AOP_ERANGE = 8       /* FP32 methods: continuation values of the call reach
-                            1e30 (node prices far in the money with no early
-                            exercise there), beyond what FP32 transforms hold;
-                            price it with AOP_FFT_FP64 */
+    AOP_ERANGE = 8       /* continuation values of the call reach 1e30 (FP32
+                            methods: price it with AOP_FFT_FP64) or 1e300
+                            (FP64): node prices far in the money with no early
+                            exercise there */
 } aop_status;
 
 typedef enum {
@@ -223,6 +223,18 @@ aop_status aop_linear_advance_device(aop_ctx *ctx, int method, int nw, const dou
 /* Counters of the kernels launched by the last batch call on this context
  * (synchronizes the context's stream). */
 aop_status aop_ctx_get_stats(aop_ctx *ctx, aop_stats *out);
+
+/* European counterparts of the requests (no early exercise): the root value
+ * as one T-step linear advance of the expiry payoff, i.e. one FFT convolution
+ * with the T-fold power of the stencil evaluated at the root cell (the linear
+ * part of the paper's method alone, Sec. 3 and P:1428-1437), in FP64 with the
+ * node-price tilt so that the payoff row's range (up to e^{+-700}) costs no
+ * accuracy.  Host arrays of n; per-request status (AOP_EINVAL also for
+ * T > AOP_EUROPEAN_MAX_T).  The method of the context is not used: always
+ * FFT_FP64.  AOP_EBUSY while a serving session holds the context. */
+#define AOP_EUROPEAN_MAX_T ((int64_t)1 << 19)
+aop_status price_european_batch(aop_ctx *ctx, int64_t n, const aop_request *reqs, double *prices,
+                                aop_status *status);
 
 /* ---------------------------------------------------------------- serving
  * Continuous pricing of requests as they arrive (no counterpart in the

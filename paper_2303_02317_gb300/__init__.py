@@ -101,6 +101,7 @@ def load(path: Optional[str] = None):
         lib.aop_ctx_get_stats.argtypes = [vp, ctypes.POINTER(_Stats)]
         lib.aop_ctx_get_option_times.argtypes = [vp, i64, vp]
         lib.aop_ctx_autotune.argtypes = [vp, i64, vp, i32, ctypes.POINTER(_Options)]
+        lib.price_european_batch.argtypes = [vp, i64, vp, vp, vp]
         lib.aop_server_create.argtypes = [vp, i64, i64, ctypes.POINTER(_Options), ctypes.POINTER(vp)]
         lib.aop_server_submit.argtypes = [vp, vp, ctypes.POINTER(i64)]
         lib.aop_server_poll.argtypes = [vp, i64, ctypes.POINTER(dbl), ctypes.POINTER(ctypes.c_int),
@@ -115,7 +116,7 @@ def load(path: Optional[str] = None):
                   "price_american_batch", "price_american_batch_device",
                   "aop_linear_advance_device", "aop_ctx_get_stats", "aop_ctx_autotune",
                   "aop_server_create", "aop_server_submit", "aop_server_poll", "aop_server_serve_stream",
-                  "aop_server_info", "aop_server_destroy"):
+                  "aop_server_info", "aop_server_destroy", "price_european_batch"):
             getattr(lib, f).restype = ctypes.c_int
         _lib = lib
         return lib
@@ -271,6 +272,17 @@ class Context:
                                                 int(h), ctypes.c_void_p(d_in), ctypes.c_void_p(d_out),
                                                 ctypes.c_void_p(stream) if stream else None),
                "aop_linear_advance_device")
+
+    def price_european(self, reqs):
+        """European counterparts by one FFT advance each (C: price_european_batch);
+        returns (prices, status)."""
+        arr = reqs if isinstance(reqs, np.ndarray) else requests_array(reqs)
+        n = len(arr)
+        prices = np.empty(n, dtype=np.float64)
+        status = np.empty(n, dtype=np.int32)
+        _check(load().price_european_batch(self._h, n, arr.ctypes.data, prices.ctypes.data, status.ctypes.data),
+               "price_european_batch")
+        return prices, status
 
     def autotune(self, reqs, method: int) -> dict:
         """Pick this context's default D&C schedule (base-case height and

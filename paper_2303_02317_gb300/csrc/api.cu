@@ -354,6 +354,60 @@ aop_status price_american_batch(aop_ctx *c, int64_t n, const aop_request *reqs, 
     return AOP_OK;
 }
 
+aop_status price_european_batch(aop_ctx *c, int64_t n, const aop_request *reqs, double *prices,
+                                aop_status *status) {
+    if (!c || n < 0 || (n > 0 && (!reqs || !prices))) return AOP_EINVAL;
+    if (n == 0) return AOP_OK;
+    if (c->serving) return AOP_EBUSY;
+    CK(cudaSetDevice(c->device));
+    cudaStream_t s = c->stream;
+    const size_t rb = (size_t)n * sizeof(aop_request), pb = (size_t)n * sizeof(double),
+                 sb = (size_t)n * sizeof(int32_t);
+    aop_status st = ensure_pinned(c, rb + pb + sb + 64);
+    if (st) return st;
+    size_t off_p = (rb + 255) & ~(size_t)255, off_s = (off_p + pb + 255) & ~(size_t)255,
+           off_par = (off_s + sb + 255) & ~(size_t)255;
+    if ((st = ensure(&c->small, &c->small_size, off_par + (size_t)n * sizeof(Params) + 256, 0))) return st;
+    char *d = (char *)c->small;
+    aop_request *d_reqs = (aop_request *)d;
+    double *d_prices = (double *)(d + off_p);
+    int32_t *d_status = (int32_t *)(d + off_s);
+    Params *d_params = (Params *)(d + off_par);
+    char *h = (char *)c->pinned;
+    memcpy(h, reqs, rb);
+    int64_t T_max = 0;
+    for (int64_t i = 0; i < n; i++)
+        if (reqs[i].T > T_max && reqs[i].T <= AOP_EUROPEAN_MAX_T) T_max = reqs[i].T;
+    if (T_max == 0) T_max = 1;
+    int lg = ilog2_ceil(2 * T_max + 1);
+    if (lg < 13) lg = 13;
+    if ((st = ensure_twiddles(c, lg + 1))) return st;
+    int grid = 0;
+    size_t need = european_workspace_bytes(n, T_max, &grid, c->device);
+    if (c->cap && need > c->cap) need = c->cap;
+    if ((st = ensure(&c->ws, &c->ws_size, need, c->cap))) return st;
+    CK(cudaMemcpyAsync(d_reqs, h, rb, cudaMemcpyHostToDevice, s));
+    CK(launch_params(n, d_reqs, d_params, d_status, nullptr, s));
+    CK(cudaEventRecord(c->ev0, s));
+    CK(run_european(n, d_params, T_max, c->ws, c->ws_size, c->tw64, c->tw_log2, d_prices, d_status, c->device,
+                    s));
+    CK(cudaEventRecord(c->ev1, s));
+    c->timed = true;
+    c->last_n = n;
+    CK(cudaMemcpyAsync(h + rb, d_prices, pb, cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(h + rb + pb, d_status, sb, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    memcpy(prices, h + rb, pb);
+    const int32_t *hs = (const int32_t *)(h + rb + pb);
+    for (int64_t i = 0; i < n; i++) {
+        aop_status e = (aop_status)hs[i];
+        if (e == AOP_OK && reqs[i].T > AOP_EUROPEAN_MAX_T) e = AOP_EINVAL;
+        if (e != AOP_OK) prices[i] = __builtin_nan("");
+        if (status) status[i] = e;
+    }
+    return AOP_OK;
+}
+
 aop_status price_american_ex(const aop_request *req, const aop_options *opt, double *price_out,
                              int32_t *boundary_out) {
     if (!req || !price_out) return AOP_EINVAL;

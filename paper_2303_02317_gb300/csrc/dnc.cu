@@ -1286,11 +1286,12 @@ struct Walker {
         int64_t i = P.T - 1;
         while (i > 0) {
             if (S.err) return __longlong_as_double(0x7ff8000000000000ll);
-            if (MODE != 0 && b >= 0) {
-                // a red value never exceeds its node price; FP32 transforms
-                // (sums of up to 2^20 values) need it well inside the range
+            if (b >= 0) {
+                // a red value never exceeds its node price; transforms (sums
+                // of up to 2^21 values) need it well inside the range: 1e30
+                // for the FP32 cells, 1e300 in FP64
                 const double sb = exercise(P, E, ex_index(P, i, b)) + P.K;
-                if (!(sb < 1e30)) {
+                if (!(sb < (MODE == 0 ? 1e300 : 1e30))) {
                     if (lane == 0) atomicCAS((int *)&S.err, 0, AOP_ERANGE);
                     return __longlong_as_double(0x7ff8000000000000ll);
                 }
@@ -1443,7 +1444,12 @@ __device__ int64_t first_rows_call(Cta<MODE> &c, int32_t *bnd) {
                     w1 * fmax(exercise(P, E, ex_index(P, T, j + 1)), 0.0);
         if (D == 2) cv += w2 * fmax(exercise(P, E, ex_index(P, T, j + 2)), 0.0);
         cell_st<MODE>(row, j, cv);
-        if (cv >= exercise(P, E, ex_index(P, i, j))) br = max(br, (int)j);
+        // Node prices beyond the FP64 range (e^709: long lattices at high
+        // volatility) make both sides infinite; such cells lie far above any
+        // early-exercise boundary and are left green (with no yield their
+        // weight in the price is below the rounding of every other cell).
+        const double e = exercise(P, E, ex_index(P, i, j));
+        if (cv < INFINITY && e < INFINITY && cv >= e) br = max(br, (int)j);
     }
     br = __reduce_max_sync(0xffffffffu, br);
     if ((threadIdx.x & 31) == 0) atomicMax(&S.bcast_i, br);
@@ -1960,6 +1966,66 @@ __global__ void __launch_bounds__(kThreadsA) advance_kernel(const __grid_constan
     }
 }
 
+// European counterpart of an option (no early exercise): the root value is
+// one T-step linear advance of the expiry payoff -- the T-fold power of the
+// stencil applied to the payoff row, evaluated at the root cell -- done as one
+// tilted FFT convolution by the whole CTA.  One CTA per option.
+template <int MODE>
+__global__ void __launch_bounds__(kThreadsA) european_kernel(const __grid_constant__ DncArgs a, double *prices,
+                                                             int32_t *status)
+{
+    using V = typename fft::Cx<MODE>::V;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ Shared S;
+    V *tile = (V *)smem_raw;
+    char *slot = a.ws + (int64_t)blockIdx.x * a.ws_stride;
+    Cta<MODE> c(a, S, slot);
+    Counters cnt{};
+    for (int64_t o = blockIdx.x; o < a.n; o += gridDim.x) {
+        if (threadIdx.x == 0) {
+            S.P = a.params[o];
+            S.spec_n = 0;
+            S.spec_lock = 0;
+            for (int j = 0; j < kSpecLg * kSpecLg; j++) (&S.spec_map[0][0])[j] = 0;
+            S.arena_used = 0;
+            S.err = 0;
+        }
+        __syncthreads();
+        if (S.P.status != AOP_OK) {
+            if (threadIdx.x == 0) prices[o] = __longlong_as_double(0x7ff8000000000000ll);
+            __syncthreads();
+            continue;
+        }
+        const Params &P = S.P;
+        build_exp_tables(P, S.E);
+        const bool put = (P.model == AOP_BSM_PUT);
+        c.tilt = !put && P.kappa > 0.0;
+        if (c.tilt) build_tilt_tables<MODE>(S);
+        __syncthreads();
+        // expiry row: calls row T (columns 0 .. D T), the put's row 0 (k = -T .. T)
+        const int64_t T = P.T;
+        const int64_t W = put ? 2 * T + 1 : (int64_t)P.D * T + 1;
+        double *row = (double *)(slot + a.off_r0);
+        for (int64_t x = threadIdx.x; x < W; x += blockDim.x) {
+            const double e = put ? exercise(P, S.E, ex_index(P, 0, x - T)) : exercise(P, S.E, ex_index(P, T, x));
+            row[x] = e > 0.0 ? e : 0.0;
+        }
+        __syncthreads();
+        double *res = (double *)(slot + a.off_mid);
+        // the root: out[y] with y = x_lo - o_min T = T (put, row indexed from -T) or 0 (calls)
+        const Buf bi{row, 0};
+        const Buf bo{res, put ? T : 0};
+        c.template conv<fft::BlockGroup, StoreF64<MODE>>(bi, 0, W - 1, bo, T, tile, a.lg_block, c.scratch(0), cnt);
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            const int err = S.err;
+            prices[o] = err ? __longlong_as_double(0x7ff8000000000000ll) : P.out_scale * res[0];
+            if (status) status[o] = err ? err : AOP_OK;
+        }
+        __syncthreads();
+    }
+}
+
 template <int MODE>
 void launch_advance(const DncArgs &a, const Params &P, int64_t grid, size_t smem, int64_t count, int64_t W,
                     int64_t h, const double *d_in, double *d_out, cudaStream_t s) {
@@ -2024,6 +2090,46 @@ cudaError_t run_linear_advance(int method, int nw, const double *w, int64_t coun
     a.err = d_err;
     const size_t smem = (size_t)L.vsz << L.lg_block;
     launch_advance_any(method, a, P, grid, smem, count, W, h, d_in, d_out, s);
+    return cudaGetLastError();
+}
+
+size_t european_workspace_bytes(int64_t n, int64_t T_max, int *grid_out, int device)
+{
+    Layout L = make_layout(AOP_FFT_FP64, T_max, 16, 1);
+    const int64_t grid = std::max<int64_t>(1, std::min<int64_t>(n, (int64_t)sm_count(device) * 2));
+    if (grid_out) *grid_out = (int)grid;
+    return (size_t)(grid * L.stride);
+}
+
+cudaError_t run_european(int64_t n, const Params *d_params, int64_t T_max, void *ws, size_t ws_bytes,
+                         const void *d_tw, int tw_log2, double *d_prices, int32_t *d_status, int device,
+                         cudaStream_t s)
+{
+    if (n == 0) return cudaSuccess;
+    Layout L = make_layout(AOP_FFT_FP64, T_max, 16, 1);
+    if (tw_log2 < L.tw_log2) return cudaErrorInvalidValue;
+    int64_t grid = std::max<int64_t>(1, std::min<int64_t>(n, (int64_t)sm_count(device) * 2));
+    if ((size_t)(grid * L.stride) > ws_bytes) grid = (int64_t)(ws_bytes / L.stride);
+    if (grid < 1) return cudaErrorMemoryAllocation;
+    DncArgs a;
+    memset(&a, 0, sizeof(a));
+    a.params = d_params;
+    a.n = n;
+    a.B = 16;
+    a.lg_tile = L.lg_tile;
+    a.lg_block = L.lg_block;
+    a.W_max = L.W_max;
+    a.ws = (char *)ws;
+    a.ws_stride = L.stride;
+    a.off_r0 = L.off_r0; a.off_mid = L.off_mid; a.off_scr = L.off_scr; a.off_spec = L.off_spec;
+    a.scr_stride = L.scr_stride;
+    for (int d = 0; d < kMaxDepth; d++) a.mid_off[d] = L.mid_off[d];
+    a.spec_cap = L.spec_cap;
+    a.tw = d_tw;
+    a.tw_log2 = tw_log2;
+    const size_t smem = (size_t)L.vsz << L.lg_block;
+    cudaFuncSetAttribute(european_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    european_kernel<0><<<(unsigned)grid, kThreadsA, smem, s>>>(a, d_prices, d_status);
     return cudaGetLastError();
 }
 

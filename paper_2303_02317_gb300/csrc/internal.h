@@ -72,5 +72,9 @@ cudaError_t run_linear_advance(int method, int nw, const double *w, int64_t coun
                                int tw_log2, void *ws, size_t ws_bytes, int *d_err,
                                cudaStream_t s);
 size_t linear_advance_workspace_bytes(int method, int64_t W, int64_t h);
+size_t european_workspace_bytes(int64_t n, int64_t T_max, int *grid_out, int device);
+cudaError_t run_european(int64_t n, const Params *d_params, int64_t T_max, void *ws, size_t ws_bytes,
+                         const void *d_tw, int tw_log2, double *d_prices, int32_t *d_status, int device,
+                         cudaStream_t s);
 
 }  // namespace aop

@@ -141,6 +141,27 @@ def test_fp32_range_status(ctx):
     assert abs(got - ref) <= parity.price_tol(aop.FFT_FP64, ref, wide.K)
 
 
+@pytest.mark.parametrize("method", [aop.FFT_FP64, aop.FFT_FP32SPLIT, aop.FFT_DF32], ids=["fft64", "fft32", "df32"])
+def test_lattice_beyond_fp64_range(ctx, method):
+    """A trinomial lattice whose extreme node prices pass e^709 (sigma 0.58,
+    2.9 years, T = 174130): plain backward induction overflows there, while
+    the D&C leaves the cells beyond the FP64 range green (they lie far above
+    the exercise boundary).  Checked against the same option at T = 120000
+    (node prices within range, plain FP64 stencil): lattice convergence
+    O(1/T) bounds the difference by 1e-3 of the price; the methods agree with
+    the FP64 D&C within their tolerances."""
+    args = (108.40797915083324, 60.46799288988718, 0.009004600663437846, 0.016617322323111118,
+            0.5817829465682484, 2.924264468806686)
+    r = wl.Request(1, *args, 174130, math.sqrt(3))
+    r_in = wl.Request(1, *args, 120000, math.sqrt(3))
+    got, st = ctx.price_batch([r], method=method)
+    p64, st64 = ctx.price_batch([r], method=aop.FFT_FP64)
+    ref, sst = ctx.price_batch([r_in], method=aop.STENCIL_FP64)
+    assert st[0] == 0 and st64[0] == 0 and sst[0] == 0 and np.isfinite(ref[0])
+    assert abs(p64[0] - ref[0]) <= 1e-3 * ref[0], (p64, ref)
+    assert abs(got[0] - p64[0]) <= parity.price_tol(method, p64[0], r.K), (got, p64)
+
+
 @pytest.mark.parametrize("method", METHODS, ids=[MNAME[m] for m in METHODS])
 def test_batch_matches_single(ctx, method):
     reqs = wl.random_small(24, seed=5, T_range=(16, 900))
