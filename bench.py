@@ -53,6 +53,16 @@ def _peaks():
         return {}
 
 
+def gpu_energy_mj(index: int):
+    """The GPU's energy counter (millijoules since the driver loaded), or None."""
+    try:
+        out = subprocess.run(["nvidia-smi", "-i", str(index), "--query-gpu=total_energy_consumption",
+                              "--format=csv,noheader,nounits"], capture_output=True, text=True, timeout=10)
+        return float(out.stdout.strip().splitlines()[0])
+    except Exception:
+        return None
+
+
 class ClockSampler:
     """nvidia-smi clock/throttle sampling during the timed region."""
 
@@ -358,6 +368,7 @@ def main():
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize(dev)
+    e_start = gpu_energy_mj(local)
     t_wall = time.perf_counter()
     opt_ms = []
     for k in range(args.steps):
@@ -368,8 +379,9 @@ def main():
         kernel_ms.append(ctx.stats()["kernel_ms"])
         opt_ms.append(ctx.option_times_ns(n) / 1e6)
     torch.cuda.synchronize(dev)
-    opt_ms = np.concatenate(opt_ms)
     t_wall = time.perf_counter() - t_wall
+    e_end = gpu_energy_mj(local)
+    opt_ms = np.concatenate(opt_ms)
     clocks = sampler.stop()
     step_ms = [a.elapsed_time(b) for a, b in ev]
     ms_step = float(np.mean(step_ms))
@@ -440,7 +452,9 @@ def main():
         samp = [reqs[i] for i in range(args.stencil_sample // 2)] + \
                [reqs[N_BINOMIAL + i] for i in range(args.stencil_sample - args.stencil_sample // 2)]
         sarr = aop.requests_array(samp)
+        se0 = gpu_energy_mj(local)
         ps, ss = ctx.price_batch(sarr, method=aop.STENCIL_FP64)
+        se1 = gpu_energy_mj(local)
         sstats = ctx.stats()
         stencil_ms = sstats["kernel_ms"]
         stencil = {"sample": "%d options of the book (%d binomial, %d trinomial)" % (
@@ -451,6 +465,8 @@ def main():
         idx = [i for i in range(args.stencil_sample // 2)] + \
               [N_BINOMIAL + i for i in range(args.stencil_sample - args.stencil_sample // 2)]
         stencil["max_rel_fft64_vs_stencil"] = float(np.max(np.abs(p64[idx] - ps) / np.abs(ps)))
+        if se0 is not None and se1 is not None:
+            stencil["joules_per_option"] = (se1 - se0) / 1e3 / len(samp)
 
     # ---- roofline of the pricing kernel: FFT flops (FP32 or FP64) over time
     flops = stats["fft_flops"]
@@ -487,6 +503,15 @@ def main():
     if args.serve_n > 0:
         serving = serve_stream(ctx, aop, wl, method, args)
 
+    energy = None
+    if e_start is not None and e_end is not None:
+        energy = {"joules_per_option": (e_end - e_start) / 1e3 / (n * args.steps),
+                  "what": "GPU energy counter (nvidia-smi total_energy_consumption) over the timed steps, "
+                          "L2 flushes included, per option"}
+        if stencil and "joules_per_option" in stencil:
+            energy["stencil_joules_per_option"] = stencil["joules_per_option"]
+            energy["saving_vs_stencil"] = 1.0 - energy["joules_per_option"] / stencil["joules_per_option"]
+
     value = world * n / (ms_step / 1e3)
     line = {
         "metric": "options_per_second", "value": value, "unit": "options/s", "n_gpus": world,
@@ -514,6 +539,7 @@ def main():
         "speedup_vs_stencil_ms_per_option": (stencil["ms_per_option"] / (ms_step / n)) if stencil else None,
         "cpu_baseline": cpu,
         "serving": serving,
+        "energy": energy,
         "kernel_stats": stats,
         "wall_s_timed": t_wall,
     }
