@@ -53,6 +53,24 @@ def _peaks():
         return {}
 
 
+def reduce_max(x: float, world: int, device=None) -> float:
+    """Max of a per-rank number over the ranks (the step time of the slowest
+    rank); identity on one rank."""
+    if world <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(options_per_rank: int, world: int, ms: float) -> float:
+    """Options per second of the whole job: every rank prices its own book in
+    ms (the slowest rank's time)."""
+    return world * options_per_rank / (ms / 1e3)
+
+
 def gpu_energy_mj(index: int):
     """The GPU's energy counter (millijoules since the driver loaded), or None."""
     try:
@@ -384,11 +402,7 @@ def main():
     opt_ms = np.concatenate(opt_ms)
     clocks = sampler.stop()
     step_ms = [a.elapsed_time(b) for a, b in ev]
-    ms_step = float(np.mean(step_ms))
-    if world > 1:
-        t = torch.tensor([ms_step], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_step = float(t.item())
+    ms_step = reduce_max(float(np.mean(step_ms)), world, dev)
     prices32 = d_prices.cpu().numpy().copy()
     stats = ctx.stats()
     kms = float(np.mean(kernel_ms))
@@ -401,7 +415,7 @@ def main():
         t0 = time.perf_counter()
         hp, hs = ctx.price_batch(arr, method=method)
         e2e_times.append(time.perf_counter() - t0)
-    e2e_ms = float(np.mean(e2e_times)) * 1e3
+    e2e_ms = reduce_max(float(np.mean(e2e_times)) * 1e3, world, dev)
 
     if rank != 0:
         if world > 1:
@@ -512,7 +526,7 @@ def main():
             energy["stencil_joules_per_option"] = stencil["joules_per_option"]
             energy["saving_vs_stencil"] = 1.0 - energy["joules_per_option"] / stencil["joules_per_option"]
 
-    value = world * n / (ms_step / 1e3)
+    value = whole_job_rate(n, world, ms_step)
     line = {
         "metric": "options_per_second", "value": value, "unit": "options/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
@@ -528,7 +542,7 @@ def main():
                    "method": args.method, "schedule": tuned or "library default",
                    "l2": "512 MB buffer written between timed steps",
                    "parallelism": "independent options per rank"},
-        "e2e": {"value": world * n / (e2e_ms / 1e3), "unit": "options/s",
+        "e2e": {"value": whole_job_rate(n, world, e2e_ms), "unit": "options/s",
                 "h2d_bytes_per_step": int(arr.nbytes), "d2h_bytes_per_step": int(n * (8 + 4))},
         "gpu_launches": 2 * args.steps,
         "clocks": clocks,
