@@ -6,8 +6,11 @@ this module only marshals arguments.  If the shared library is missing or no
 CUDA device is usable the calls raise -- there is no CPU fallback.
 
 Method codes: FFT_FP64 (trapezoidal divide-and-conquer with FP64 FFT
-convolutions), FFT_FP32SPLIT (the same with FP32 hi/lo-split convolutions and
-FP64 base cases), STENCIL_FP64 (plain Theta(T^2) backward induction).
+convolutions and FP64 base cases), FFT_FP32SPLIT (the same with FP32
+hi/lo-split convolutions), FFT_DF32 (doubled-FP32 convolutions; both FP32
+methods evaluate base cases in doubled FP32, in FP64 where the exercise
+values span too wide a range), STENCIL_FP64 (plain Theta(T^2) backward
+induction).
 """
 from __future__ import annotations
 

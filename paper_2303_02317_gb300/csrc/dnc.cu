@@ -25,7 +25,7 @@
 //
 // Execution inside the CTA follows the paper's observation that each FFT
 // advance can run in parallel with the recursion beside it (proof of Thm 2.8):
-// warp 0 (the walker) runs the recursion and the FP64 base cases and posts
+// warp 0 (the walker) runs the recursion and the base cases and posts
 // every linear advance as a task in a per-depth slot; warps 1..3 (workers)
 // execute the tasks (warp-level FFT convolutions) while the walker continues
 // down the sub-trapezoid, and the walker waits for a task only when its

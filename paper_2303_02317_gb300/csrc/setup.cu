@@ -27,14 +27,12 @@ __global__ void params_kernel(int64_t n, const aop_request *reqs, Params *params
     }
 }
 
-// Twiddles w^k = e^{-2 pi i k / N} for k < N/2, N = 2^log2n.
-//   tw64[k]        = (cos, sin) in FP64
-//   tw32[2k], [2k+1] = hi and lo FP32 parts of the same value (the lo part is
-//                    the FP64 residual, so hi + lo carries ~48 bits).
 // Twiddle tables, one level per transform length: entry 2^(L-1) + k holds
 // e^{-2 pi i k / 2^L} for k < 2^(L-1), L = 1 .. log2n (entry 0 unused).  A
 // stage of half-size 2^(L-1) reads a contiguous run, so the short transforms
-// touch only the first few KB of the table.
+// touch only the first few KB of the table.  tw64 holds (cos, sin) in FP64;
+// tw32 holds (cos hi, sin hi, cos lo, sin lo), the lo parts being the FP64
+// residuals of the FP32 hi parts, so hi + lo carries ~48 bits.
 __global__ void twiddle_kernel(int log2n, float4 *tw32, double2 *tw64)
 {
     const int64_t n = (int64_t)1 << log2n;
