@@ -71,14 +71,78 @@ def whole_job_rate(options_per_rank: int, world: int, ms: float) -> float:
     return world * options_per_rank / (ms / 1e3)
 
 
-def gpu_energy_mj(index: int):
-    """The GPU's energy counter (millijoules since the driver loaded), or None."""
-    try:
-        out = subprocess.run(["nvidia-smi", "-i", str(index), "--query-gpu=total_energy_consumption",
-                              "--format=csv,noheader,nounits"], capture_output=True, text=True, timeout=10)
-        return float(out.stdout.strip().splitlines()[0])
-    except Exception:
-        return None
+class EnergyMeter:
+    """GPU energy over a region, read through NVML (read-only queries):
+    the driver's total-energy counter when the device exposes it, else the
+    integral of power readings taken every 5 ms by a background thread
+    (trapezoid rule).  measure() returns (joules, how) or (None, reason)."""
+
+    def __init__(self, index: int):
+        import ctypes
+        self.ct = ctypes
+        self.lib = None
+        self.handle = None
+        self.why = ""
+        try:
+            lib = ctypes.CDLL("libnvidia-ml.so.1")
+            if lib.nvmlInit_v2() != 0:
+                raise RuntimeError("nvmlInit failed")
+            h = ctypes.c_void_p()
+            if lib.nvmlDeviceGetHandleByIndex_v2(ctypes.c_uint(index), ctypes.byref(h)) != 0:
+                raise RuntimeError("no NVML handle for device %d" % index)
+            self.lib, self.handle = lib, h
+        except Exception as e:                      # no driver library here
+            self.why = str(e)
+
+    def _counter_mj(self):
+        v = self.ct.c_ulonglong()
+        if self.lib.nvmlDeviceGetTotalEnergyConsumption(self.handle, self.ct.byref(v)) != 0:
+            return None
+        return float(v.value)
+
+    def _power_w(self):
+        v = self.ct.c_uint()
+        if self.lib.nvmlDeviceGetPowerUsage(self.handle, self.ct.byref(v)) != 0:
+            return None
+        return v.value / 1e3
+
+    def start(self):
+        import threading
+        self.e0 = self.t0 = None
+        self.samples = []
+        if self.lib is None:
+            return
+        self.e0 = self._counter_mj()
+        if self.e0 is None:
+            self.stop_flag = False
+
+            def run():
+                while not self.stop_flag:
+                    p = self._power_w()
+                    if p is not None:
+                        self.samples.append((time.perf_counter(), p))
+                    time.sleep(0.005)
+            self.th = threading.Thread(target=run, daemon=True)
+            self.th.start()
+        self.t0 = time.perf_counter()
+
+    def measure(self):
+        if self.lib is None:
+            return None, "NVML unavailable: " + self.why
+        if self.e0 is not None:
+            e1 = self._counter_mj()
+            if e1 is not None and e1 >= self.e0:
+                return (e1 - self.e0) / 1e3, "NVML total energy counter"
+            return None, "NVML energy counter unreadable"
+        self.stop_flag = True
+        self.th.join()
+        pts = self.samples
+        if len(pts) < 2:
+            return None, "too few NVML power samples"
+        joules = sum(0.5 * (pts[i][1] + pts[i - 1][1]) * (pts[i][0] - pts[i - 1][0])
+                     for i in range(1, len(pts)))
+        return joules, "NVML power readings every 5 ms, integrated (%d samples, mean %.0f W)" % (
+            len(pts), sum(p for _, p in pts) / len(pts))
 
 
 class ClockSampler:
@@ -386,7 +450,8 @@ def main():
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize(dev)
-    e_start = gpu_energy_mj(local)
+    meter = EnergyMeter(local)
+    meter.start()
     t_wall = time.perf_counter()
     opt_ms = []
     for k in range(args.steps):
@@ -398,7 +463,7 @@ def main():
         opt_ms.append(ctx.option_times_ns(n) / 1e6)
     torch.cuda.synchronize(dev)
     t_wall = time.perf_counter() - t_wall
-    e_end = gpu_energy_mj(local)
+    e_joules, e_how = meter.measure()
     opt_ms = np.concatenate(opt_ms)
     clocks = sampler.stop()
     step_ms = [a.elapsed_time(b) for a, b in ev]
@@ -466,9 +531,10 @@ def main():
         samp = [reqs[i] for i in range(args.stencil_sample // 2)] + \
                [reqs[N_BINOMIAL + i] for i in range(args.stencil_sample - args.stencil_sample // 2)]
         sarr = aop.requests_array(samp)
-        se0 = gpu_energy_mj(local)
+        smeter = EnergyMeter(local)
+        smeter.start()
         ps, ss = ctx.price_batch(sarr, method=aop.STENCIL_FP64)
-        se1 = gpu_energy_mj(local)
+        se_joules, se_how = smeter.measure()
         sstats = ctx.stats()
         stencil_ms = sstats["kernel_ms"]
         stencil = {"sample": "%d options of the book (%d binomial, %d trinomial)" % (
@@ -479,8 +545,9 @@ def main():
         idx = [i for i in range(args.stencil_sample // 2)] + \
               [N_BINOMIAL + i for i in range(args.stencil_sample - args.stencil_sample // 2)]
         stencil["max_rel_fft64_vs_stencil"] = float(np.max(np.abs(p64[idx] - ps) / np.abs(ps)))
-        if se0 is not None and se1 is not None:
-            stencil["joules_per_option"] = (se1 - se0) / 1e3 / len(samp)
+        if se_joules is not None:
+            stencil["joules_per_option"] = se_joules / len(samp)
+        stencil["energy_how"] = se_how
 
     # ---- roofline of the pricing kernel: FFT flops (FP32 or FP64) over time
     flops = stats["fft_flops"]
@@ -517,11 +584,12 @@ def main():
     if args.serve_n > 0:
         serving = serve_stream(ctx, aop, wl, method, args)
 
-    energy = None
-    if e_start is not None and e_end is not None:
-        energy = {"joules_per_option": (e_end - e_start) / 1e3 / (n * args.steps),
-                  "what": "GPU energy counter (nvidia-smi total_energy_consumption) over the timed steps, "
-                          "L2 flushes included, per option"}
+    energy = {"joules_per_option": None, "how": e_how}
+    if e_joules is not None:
+        energy = {"joules_per_option": e_joules / (n * args.steps),
+                  "mean_watts": e_joules / t_wall, "how": e_how,
+                  "what": "whole-GPU energy over the timed steps (L2 flushes and idle power included), "
+                          "per option"}
         if stencil and "joules_per_option" in stencil:
             energy["stencil_joules_per_option"] = stencil["joules_per_option"]
             energy["saving_vs_stencil"] = 1.0 - energy["joules_per_option"] / stencil["joules_per_option"]

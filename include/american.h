@@ -35,18 +35,28 @@ extern "C" {
  *   AOP_BSM_PUT        -- Sec. 5: explicit finite differences for the
  *       nondimensional Black-Scholes-Merton put (scheme bsmG) on the shrinking
  *       triangle k in [-(T-n), T-n], dtau = sigma^2 expiry/(2T),
- *       ds = sqrt(3 dtau), s_k = ln(S0/K) + k ds; q must be 0. */
+ *       ds = sqrt(3 dtau), s_k = ln(S0/K) + k ds.  A dividend yield q (not in
+ *       the paper) sets the first-derivative coefficient to 2(r-q)/sigma^2 - 1;
+ *       the discount term keeps omega = 2r/sigma^2.
+ *   AOP_BINOMIAL_PUT, AOP_TRINOMIAL_PUT -- the two lattices above with the
+ *       put's exercise value K - S0 u^x (Sec. 3.1 states it; the paper's
+ *       method is given for calls).  Priced exactly as the call of the
+ *       mirrored lattice: spot K, strike S0, the put's weights times the
+ *       child/parent price ratio, read right to left (lattice put-call
+ *       symmetry), so the same divider lemma and kernels apply. */
 typedef enum {
     AOP_BINOMIAL_CALL = 0,
     AOP_TRINOMIAL_CALL = 1,
-    AOP_BSM_PUT = 2
+    AOP_BSM_PUT = 2,
+    AOP_BINOMIAL_PUT = 3,
+    AOP_TRINOMIAL_PUT = 4
 } aop_model;
 
 typedef enum {
     AOP_OK = 0,
     AOP_EINVAL = 1,      /* bad argument: S0, K, sigma or expiry <= 0, T < 1,
-                            T > AOP_MAX_T, unknown model/method, q != 0 for the
-                            BSM put, NULL where a pointer is required */
+                            T > AOP_MAX_T, unknown model/method, NULL where a
+                            pointer is required */
     AOP_EUNSTABLE = 2,   /* a lattice probability or FD weight is negative
                             (binomial p outside [0,1], trinomial p_x < 0,
                             BSM a, b or c < 0) */
@@ -182,7 +192,9 @@ aop_status price_american(int model, double S0, double K, double r, double q,
  *   calls: boundary[i] = largest column j in [0, D i] whose continuation value
  *          is >= its exercise value (Cor. 2.7), -1 if none (D = 1 binomial,
  *          2 trinomial);
- *   put:   boundary[n] = largest spatial index k in [-(T-n), T-n] whose
+ *   binomial/trinomial puts: boundary[i] = largest column j in [0, D i] whose
+ *          exercise value exceeds its continuation value, -1 if none;
+ *   BSM put: boundary[n] = largest spatial index k in [-(T-n), T-n] whose
  *          exercise value exceeds its continuation value (BSM boundary
  *          theorem), AOP_BOUNDARY_NONE_PUT if none. */
 aop_status price_american_ex(const aop_request *req, const aop_options *opt,
@@ -196,6 +208,28 @@ aop_status price_american_ex(const aop_request *req, const aop_options *opt,
 aop_status price_american_batch(aop_ctx *ctx, int64_t n, const aop_request *reqs,
                                 const aop_options *opt, double *prices,
                                 aop_status *status, void *stream);
+
+/* Price and sensitivities of n options (host arrays, as price_american_batch)
+ * with a divide-and-conquer method (AOP_FFT_*; AOP_STENCIL_FP64 gives
+ * AOP_EINVAL).  greeks (host, double[3n]) receives per option delta (dV/dS0),
+ * gamma (d2V/dS0^2) and theta (dV/dt, per year, t calendar time) from the
+ * lattice rows next to the root, the standard lattice estimates:
+ *   binomial:  delta = (G11 - G10)/(S0 u - S0 d),
+ *              gamma = [(G22 - G21)/(S0 u^2 - S0) - (G21 - G20)/(S0 - S0 d^2)]
+ *                      / ((S0 u^2 - S0 d^2)/2),
+ *              theta = (G21 - G00)/(2 dt);
+ *   trinomial: the same centred differences on row 1 (nodes S0 d, S0, S0 u),
+ *              theta = (G11 - G00)/dt;
+ *   BSM put:   the same on the grid row next to the root (spots S0 e^{-ds},
+ *              S0, S0 e^{ds}), theta = K (v^{T-1}_0 - v^T_0)/dt;
+ * with dt = expiry/T.  Rows 1-2 are evaluated in FP64 by the kernel that
+ * prices the option (the chain stops two rows early); prices agree with
+ * price_american_batch to rounding.  Options with T < 3 or a failed status get
+ * NaN sensitivities.  The FP32-split method's value error (~1e-6 relative)
+ * makes its gamma and theta unreliable; use AOP_FFT_FP64 or AOP_FFT_DF32. */
+aop_status price_american_greeks_batch(aop_ctx *ctx, int64_t n, const aop_request *reqs,
+                                       const aop_options *opt, double *prices, double *greeks,
+                                       aop_status *status, void *stream);
 
 /* Device-resident batch: d_reqs (aop_request[n]), d_prices (double[n]) and
  * d_status (int32[n], nullable) are device pointers; enqueued on `stream`,

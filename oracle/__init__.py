@@ -6,9 +6,10 @@ with the CUDA library and the library never imports it.
 
 The C source (``oracle.c``) is the plain definition the fast method must
 reproduce: Fig. 1's nested loop for the binomial call (Sec. 3.1, Def. 2.1), the
-trinomial call of Sec. 4 and its appendix, and the explicit finite-difference
-scheme for the Black-Scholes-Merton put of Sec. 5.  This wrapper only marshals
-arguments through ctypes.
+trinomial call of Sec. 4 and its appendix, the same two lattices with the put's
+exercise value, and the explicit finite-difference scheme for the
+Black-Scholes-Merton put of Sec. 5 (with an optional dividend yield).  This
+wrapper only marshals arguments through ctypes.
 
 Requests are plain mappings (or objects with attributes) with the fields
 ``model, S0, K, r, q, sigma, expiry, T`` and optionally ``lam`` and
@@ -27,7 +28,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 SRC = os.path.join(HERE, "oracle.c")
 LIB = os.path.join(HERE, "_oracle.so")
 
-BOPM, TOPM, BSM = 0, 1, 2
+BOPM, TOPM, BSM, BOPM_PUT, TOPM_PUT = 0, 1, 2, 3, 4
 OK, EINVAL, EUNSTABLE, ENOMEM = 0, 1, 2, 3
 INT32_MIN = -(2 ** 31)
 
@@ -65,6 +66,7 @@ class _Params(ctypes.Structure):
         ("po", ctypes.c_double),
         ("pd", ctypes.c_double),
         ("m", ctypes.c_double),
+        ("omega_y", ctypes.c_double),
     ]
 
 
@@ -99,6 +101,8 @@ def _load():
                                               ctypes.POINTER(ctypes.c_double)]
             lib.or_grid.argtypes = [ctypes.POINTER(_Req), ctypes.c_int, ctypes.c_void_p,
                                     ctypes.c_void_p]
+            lib.or_greeks.argtypes = [ctypes.POINTER(_Req), ctypes.c_int, ctypes.c_int,
+                                      ctypes.c_void_p, ctypes.c_void_p]
             lib.or_price_many.argtypes = [ctypes.c_int64, ctypes.c_void_p, ctypes.c_int,
                                           ctypes.c_void_p, ctypes.c_void_p]
             lib.or_max_threads.restype = ctypes.c_int
@@ -126,7 +130,7 @@ def _to_c(req) -> _Req:
 def columns(req) -> int:
     """Number of stored columns of the widest row: T+1 (BOPM) or 2T+1."""
     T = int(_field(req, "T"))
-    return T + 1 if int(_field(req, "model")) == BOPM else 2 * T + 1
+    return T + 1 if int(_field(req, "model")) in (BOPM, BOPM_PUT) else 2 * T + 1
 
 
 def params(req) -> dict:
@@ -138,7 +142,7 @@ def params(req) -> dict:
         raise ValueError("oracle rejected request (status %d)" % st)
     return {"model": P.model, "D": P.D, "w": [P.w[i] for i in range(P.nw)],
             "o_min": P.o_min, "u": P.u, "logu": P.logu, "dt": P.dt, "dtau": P.dtau, "ds": P.ds,
-            "omega": P.omega, "p": P.p, "pu": P.pu, "po": P.po, "pd": P.pd, "m": P.m}
+            "omega": P.omega, "omega_y": P.omega_y, "p": P.p, "pu": P.pu, "po": P.po, "pd": P.pd, "m": P.m}
 
 
 def status_of(req) -> int:
@@ -177,8 +181,8 @@ def price_european(req, nthreads: int = 1) -> float:
 
 
 def grid(req, american: bool = True):
-    """Every row of the lattice (small T only).  Calls: shape (T+1, D*T+1),
-    entry [i, j]; put: shape (T+1, 2T+1), entry [n, k+T].  Cells outside a
+    """Every row of the lattice (small T only).  Lattices: shape (T+1, D*T+1),
+    entry [i, j]; BSM put: shape (T+1, 2T+1), entry [n, k+T].  Cells outside a
     row are NaN.  Also returns the boundary array."""
     lib = _load()
     T = int(_field(req, "T"))
@@ -188,6 +192,21 @@ def grid(req, american: bool = True):
     if st:
         raise ValueError("oracle status %d" % st)
     return g, b
+
+
+def greeks(req, american: bool = True, nthreads: int = 1):
+    """(price, delta, gamma, theta) from the nodes next to the root, and those
+    nodes' values: lattices: row 1 at [0:D+1], row 2 at [3:3+2D+1]; BSM put:
+    row T-1 (k = -1..1) at [0:3], row T-2 (k = -2..2) at [3:8] (units of K).
+    T >= 3."""
+    lib = _load()
+    out = np.empty(4, dtype=np.float64)
+    near = np.full(8, np.nan, dtype=np.float64)
+    st = lib.or_greeks(ctypes.byref(_to_c(req)), 1 if american else 0, int(nthreads),
+                       out.ctypes.data, near.ctypes.data)
+    if st:
+        raise ValueError("oracle status %d" % st)
+    return tuple(float(x) for x in out), near
 
 
 def price_many(reqs, nthreads: int = 0):
@@ -212,6 +231,6 @@ def tie_band(req) -> float:
     return 1e-12 * (1.0 if int(_field(req, "model")) == BSM else float(_field(req, "K")))
 
 
-__all__ = ["build", "params", "status_of", "price_american", "price_european", "grid",
+__all__ = ["build", "params", "status_of", "price_american", "price_european", "grid", "greeks",
            "price_many", "max_threads", "columns", "tie_band", "BOPM", "TOPM", "BSM",
-           "INT32_MIN"]
+           "BOPM_PUT", "TOPM_PUT", "INT32_MIN"]

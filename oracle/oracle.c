@@ -31,6 +31,10 @@
  *       p_u u + p_o + p_d/u = e^{(R-Y)dt},
  *       p_u u^2 + p_o + p_d/u^2 = e^{(2(R-Y)+V^2)dt}.
  *
+ *   BOPM put, TOPM put  (the exercise value of a put, Sec. 3.1)
+ *     the same lattices, weights and rows as the calls, with exercise value
+ *     K - S u^{2j-i} (binomial) or K - S u^{j-i} (trinomial).
+ *
  *   BSM put  (Sec. 5, explicit scheme bsmG)
  *     dtau = V^2 E/(2T), omega = 2R/V^2, ds = sqrt(3 dtau),
  *     a = dtau/ds^2 + (omega-1) dtau/(2 ds) on k+1,
@@ -39,15 +43,23 @@
  *     s_k = ln(S/K) + k ds, v^0_k = max(1 - e^{s_k}, 0),
  *     v^{n+1}_k = max(a v^n_{k+1} + c v^n_k + b v^n_{k-1}, 1 - e^{s_k})
  *     on the shrinking triangle |k| <= T-n-1; price = K v^T_0.
+ *     With a dividend yield Y (absent from the paper, whose Sec. 5 sets none):
+ *     the substitution that yields Sec. 5's nondimensional equation gives
+ *     v_tau = v_ss + (omega_Y - 1) v_s - omega v with omega_Y = 2(R-Y)/V^2,
+ *     so omega_Y replaces omega in the first-derivative term of a and b while
+ *     omega stays in c; Y = 0 is the paper's scheme unchanged.
  *
  * Boundary outputs (Cor. 2.7 and the BSM boundary theorem):
  *   call: boundary[i] = largest j in [0, D i] whose continuation value is >=
  *         its exercise value (row T: continuation 0), -1 if none.
- *   put:  boundary[n] = largest k in [-(T-n), T-n] whose exercise value is >
+ *   BOPM/TOPM put: boundary[i] = largest j in [0, D i] whose exercise value
+ *         is > its continuation value (row T: continuation 0), -1 if none.
+ *   BSM put: boundary[n] = largest k in [-(T-n), T-n] whose exercise value is >
  *         its continuation value (row 0: continuation 0), INT32_MIN if none.
- *   margin[row] (optional) = min |continuation - exercise| over the last red
- *         and the first green cell of that row (in price units for the call,
- *         in units of K for the put); it measures how close a row is to a tie.
+ *   margin[row] (optional) = min |continuation - exercise| over the divider
+ *         cell and its right neighbour in that row (in price units for the
+ *         lattices, in units of K for the BSM put); it measures how close a row
+ *         is to a tie.
  */
 #include <math.h>
 #include <stdint.h>
@@ -57,7 +69,7 @@
 #include <omp.h>
 #endif
 
-enum { OR_BOPM = 0, OR_TOPM = 1, OR_BSM = 2 };
+enum { OR_BOPM = 0, OR_TOPM = 1, OR_BSM = 2, OR_BOPM_PUT = 3, OR_TOPM_PUT = 4 };
 enum { OR_OK = 0, OR_EINVAL = 1, OR_EUNSTABLE = 2, OR_ENOMEM = 3 };
 
 typedef struct {
@@ -77,7 +89,10 @@ typedef struct {
     double u;           /* price factor per column (calls) or e^{ds} (BSM) */
     double logu;        /* exact log of u as defined (V sqrt(dt), ...) */
     double dt, dtau, ds, omega, p, pu, po, pd, m;
+    double omega_y;     /* BSM: 2(R-Y)/V^2, the drift coefficient */
 } or_params;
+
+static int is_lattice_put(int model) { return model == OR_BOPM_PUT || model == OR_TOPM_PUT; }
 
 int or_params_compute(const or_req *q, or_params *P)
 {
@@ -86,7 +101,7 @@ int or_params_compute(const or_req *q, or_params *P)
         return OR_EINVAL;
     P->model = q->model;
     const double T = (double)q->T;
-    if (q->model == OR_BOPM) {
+    if (q->model == OR_BOPM || q->model == OR_BOPM_PUT) {
         double dt = q->E / T;
         double u = exp(q->V * sqrt(dt));
         double d = 1.0 / u;
@@ -99,7 +114,7 @@ int or_params_compute(const or_req *q, or_params *P)
         P->u = u; P->logu = q->V * sqrt(dt); P->dt = dt; P->p = p; P->m = m;
         return OR_OK;
     }
-    if (q->model == OR_TOPM) {
+    if (q->model == OR_TOPM || q->model == OR_TOPM_PUT) {
         double dt = q->E / T;
         double m = exp(-q->R * dt);
         double u, logu, pu, pd, po;
@@ -137,18 +152,19 @@ int or_params_compute(const or_req *q, or_params *P)
         return OR_OK;
     }
     if (q->model == OR_BSM) {
-        if (q->Y != 0.0) return OR_EINVAL;   /* the paper's BSM has no yield term */
         double dtau = q->V * q->V * q->E / (2.0 * T);
         double omega = 2.0 * q->R / (q->V * q->V);
+        double omega_y = 2.0 * (q->R - q->Y) / (q->V * q->V);
         double ds = sqrt(3.0 * dtau);
         double al = dtau / (ds * ds);
-        double be = (omega - 1.0) * dtau / (2.0 * ds);
+        double be = (omega_y - 1.0) * dtau / (2.0 * ds);
         double a = al + be, b = al - be;
         double c = 1.0 - a - b - omega * dtau;
         if (!(a >= 0 && b >= 0 && c >= 0)) return OR_EUNSTABLE;
         P->D = 2; P->nw = 3; P->o_min = -1;
         P->w[0] = b; P->w[1] = c; P->w[2] = a;   /* on k-1, k, k+1 */
         P->u = exp(ds); P->logu = ds; P->dtau = dtau; P->ds = ds; P->omega = omega;
+        P->omega_y = omega_y;
         return OR_OK;
     }
     return OR_EINVAL;
@@ -156,8 +172,8 @@ int or_params_compute(const or_req *q, or_params *P)
 
 /* exercise value table ex[k + T] for k in [-T, T]:
    calls: S u^k - K with u^k evaluated as e^{k log u} from the exact log u of
-   the model (Sec. 3.1: node price S u^{N_u - N_d}); put: 1 - e^{ln(S/K) + k ds}
-   (units of K). */
+   the model (Sec. 3.1: node price S u^{N_u - N_d}); lattice puts: K - S u^k;
+   BSM put: 1 - e^{ln(S/K) + k ds} (units of K). */
 static double *exercise_table(const or_req *q, const or_params *P)
 {
     int64_t T = q->T;
@@ -166,6 +182,8 @@ static double *exercise_table(const or_req *q, const or_params *P)
     for (int64_t k = -T; k <= T; k++) {
         if (P->model == OR_BSM)
             ex[k + T] = 1.0 - exp(log(q->S / q->K) + (double)k * P->ds);
+        else if (is_lattice_put(P->model))
+            ex[k + T] = q->K - q->S * exp((double)k * P->logu);
         else
             ex[k + T] = q->S * exp((double)k * P->logu) - q->K;
     }
@@ -176,9 +194,12 @@ static double *exercise_table(const or_req *q, const or_params *P)
  * Core backward induction.  american = 0 drops the max (European value on the
  * same lattice).  grid (optional) receives every row: row r of the call grid is
  * at grid[r*(D*T+1) + j]; row n of the put grid at grid[n*(2T+1) + (k+T)].
+ * near (optional, 8 doubles) receives the rows next to the root: lattices:
+ * row 1 (j = 0..D) at near[0..], row 2 (j = 0..2D) at near[3..]; BSM: row
+ * T-1 (k = -1..1) at near[0..2], row T-2 (k = -2..2) at near[3..7].
  */
 static int lattice(const or_req *q, int american, int nthreads, double *price,
-                   int32_t *boundary, double *margin, double *grid)
+                   int32_t *boundary, double *margin, double *grid, double *near)
 {
     or_params P;
     int st = or_params_compute(q, &P);
@@ -197,20 +218,22 @@ static int lattice(const or_req *q, int american, int nthreads, double *price,
 
     if (P.model != OR_BSM) {
         const int D = P.D;
+        const int put = is_lattice_put(P.model);
         const double w0 = P.w[0], w1 = P.w[1], w2 = P.w[2];
-        /* leaves, row T: continuation 0 */
-        int64_t last_red = -1;
+        /* leaves, row T: continuation 0.  The divider is the last red cell
+           (call) or the last green cell (put). */
+        int64_t last = -1;
         for (int64_t j = 0; j <= D * T; j++) {
             int64_t k = (D == 1) ? 2 * j - T : j - T;
             double e = ex[k + T];
             cur[j] = e > 0.0 ? e : 0.0;
-            if (0.0 >= e) last_red = j;
+            if (put ? (e > 0.0) : (0.0 >= e)) last = j;
         }
-        if (boundary) boundary[T] = (int32_t)last_red;
+        if (boundary) boundary[T] = (int32_t)last;
         if (margin) {
             double mg = INFINITY;
-            if (last_red >= 0) mg = fmin(mg, fabs(0.0 - ex[((D == 1) ? 2 * last_red - T : last_red - T) + T]));
-            if (last_red + 1 <= D * T) mg = fmin(mg, fabs(0.0 - ex[((D == 1) ? 2 * (last_red + 1) - T : last_red + 1 - T) + T]));
+            if (last >= 0) mg = fmin(mg, fabs(0.0 - ex[((D == 1) ? 2 * last - T : last - T) + T]));
+            if (last + 1 <= D * T) mg = fmin(mg, fabs(0.0 - ex[((D == 1) ? 2 * (last + 1) - T : last + 1 - T) + T]));
             margin[T] = mg;
         }
         if (grid) memcpy(grid + (size_t)T * W, cur, sizeof(double) * (size_t)W);
@@ -225,13 +248,14 @@ static int lattice(const or_req *q, int american, int nthreads, double *price,
                 nxt[j] = (american && e > cont) ? e : cont;
             }
             if (boundary || margin) {
-                /* largest j with continuation >= exercise, found by rescanning */
+                /* largest j with continuation >= exercise (call) or with
+                   exercise > continuation (put), found by rescanning */
                 int64_t br = -1;
                 for (int64_t j = n; j >= 0; j--) {
                     double cont = (D == 1) ? w0 * cur[j] + w1 * cur[j + 1]
                                            : w0 * cur[j] + w1 * cur[j + 1] + w2 * cur[j + 2];
                     int64_t k = (D == 1) ? 2 * j - i : j - i;
-                    if (cont >= ex[k + T]) { br = j; break; }
+                    if (put ? (ex[k + T] > cont) : (cont >= ex[k + T])) { br = j; break; }
                 }
                 if (boundary) boundary[i] = (int32_t)br;
                 if (margin) {
@@ -247,6 +271,8 @@ static int lattice(const or_req *q, int american, int nthreads, double *price,
                 }
             }
             double *t = cur; cur = nxt; nxt = t;
+            if (near && i == 1) for (int j = 0; j <= D; j++) near[j] = cur[j];
+            if (near && i == 2) for (int j = 0; j <= 2 * D; j++) near[3 + j] = cur[j];
             if (grid) {
                 memcpy(grid + (size_t)i * W, cur, sizeof(double) * (size_t)(n + 1));
                 for (int64_t j = n + 1; j < W; j++) grid[(size_t)i * W + j] = NAN;
@@ -298,6 +324,8 @@ static int lattice(const or_req *q, int american, int nthreads, double *price,
                 }
             }
             double *t = cur; cur = nxt; nxt = t;
+            if (near && n == T - 1) for (int k = -1; k <= 1; k++) near[k + 1] = cur[k + T];
+            if (near && n == T - 2) for (int k = -2; k <= 2; k++) near[k + 5] = cur[k + T];
             /* cells outside [-R, R] keep stale values; they are never read again */
             if (grid) {
                 for (int64_t k = -T; k <= T; k++)
@@ -312,19 +340,67 @@ static int lattice(const or_req *q, int american, int nthreads, double *price,
 
 int or_price_american(const or_req *q, int nthreads, double *price, int32_t *boundary, double *margin)
 {
-    return lattice(q, 1, nthreads, price, boundary, margin, NULL);
+    return lattice(q, 1, nthreads, price, boundary, margin, NULL, NULL);
 }
 
 int or_price_european(const or_req *q, int nthreads, double *price)
 {
-    return lattice(q, 0, nthreads, price, NULL, NULL, NULL);
+    return lattice(q, 0, nthreads, price, NULL, NULL, NULL, NULL);
+}
+
+/*
+ * Sensitivities from the nodes next to the root (textbook lattice estimates,
+ * e.g. Hull, "Options, Futures and Other Derivatives", binomial trees):
+ *   binomial:  delta = (G[1][1] - G[1][0]) / (S u - S d)
+ *              gamma = ((G[2][2] - G[2][1]) / (S u^2 - S) - (G[2][1] - G[2][0]) / (S - S d^2))
+ *                      / ((S u^2 - S d^2) / 2)
+ *              theta = (G[2][1] - G[0][0]) / (2 dt)
+ *   trinomial: the same differences on row 1 (spots S d, S, S u),
+ *              theta = (G[1][1] - G[0][0]) / dt
+ *   BSM put:   the same on row T-1 (spots S e^{-ds}, S, S e^{ds}), values K v,
+ *              theta = K (v^{T-1}_0 - v^T_0) / dt
+ * with dt = E/T and node spots S e^{x log u}.  out = {price, delta, gamma,
+ * theta}; near (optional, 8 doubles) as in lattice().  Needs T >= 3.
+ */
+int or_greeks(const or_req *q, int american, int nthreads, double *out, double *near_out)
+{
+    if (q->T < 3) return OR_EINVAL;
+    or_params P;
+    int st = or_params_compute(q, &P);
+    if (st) return st;
+    double near[8], price;
+    st = lattice(q, american, nthreads, &price, NULL, NULL, NULL, near);
+    if (st) return st;
+    const double S = q->S, dt = q->E / (double)q->T;
+    double delta, gamma, theta;
+    if (P.model == OR_BSM) {
+        const double su = S * exp(P.ds), s0 = S, sd = S * exp(-P.ds);
+        const double vd = q->K * near[0], v0 = q->K * near[1], vu = q->K * near[2];
+        delta = (vu - vd) / (su - sd);
+        gamma = ((vu - v0) / (su - s0) - (v0 - vd) / (s0 - sd)) / ((su - sd) / 2.0);
+        theta = (v0 - price) / dt;
+    } else if (P.D == 1) {
+        const double s1u = S * exp(P.logu), s1d = S * exp(-P.logu);
+        const double s2u = S * exp(2.0 * P.logu), s2d = S * exp(-2.0 * P.logu);
+        delta = (near[1] - near[0]) / (s1u - s1d);
+        gamma = ((near[5] - near[4]) / (s2u - S) - (near[4] - near[3]) / (S - s2d)) / ((s2u - s2d) / 2.0);
+        theta = (near[4] - price) / (2.0 * dt);
+    } else {
+        const double s1u = S * exp(P.logu), s1d = S * exp(-P.logu);
+        delta = (near[2] - near[0]) / (s1u - s1d);
+        gamma = ((near[2] - near[1]) / (s1u - S) - (near[1] - near[0]) / (S - s1d)) / ((s1u - s1d) / 2.0);
+        theta = (near[1] - price) / dt;
+    }
+    out[0] = price; out[1] = delta; out[2] = gamma; out[3] = theta;
+    if (near_out) memcpy(near_out, near, sizeof(near));
+    return OR_OK;
 }
 
 /* Full grid for small T (tests of the structural lemmas). */
 int or_grid(const or_req *q, int american, double *grid, int32_t *boundary)
 {
     double price;
-    return lattice(q, american, 1, &price, boundary, NULL, grid);
+    return lattice(q, american, 1, &price, boundary, NULL, grid, NULL);
 }
 
 /* Price many options one after another (the timed CPU baseline). */

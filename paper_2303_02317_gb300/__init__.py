@@ -28,7 +28,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libamerican.so")
 HEADER = os.path.join(os.path.dirname(HERE), "include", "american.h")
 
-BINOMIAL_CALL, TRINOMIAL_CALL, BSM_PUT = 0, 1, 2
+BINOMIAL_CALL, TRINOMIAL_CALL, BSM_PUT, BINOMIAL_PUT, TRINOMIAL_PUT = 0, 1, 2, 3, 4
 FFT_FP64, FFT_FP32SPLIT, STENCIL_FP64, FFT_DF32 = 0, 1, 2, 3
 TRI_BOYLE, TRI_PAPER = 0, 1
 BOUNDARY_NONE_PUT = -(2 ** 31)
@@ -97,6 +97,7 @@ def load(path: Optional[str] = None):
                                        ctypes.POINTER(dbl)]
         lib.price_american_ex.argtypes = [vp, ctypes.POINTER(_Options), ctypes.POINTER(dbl), vp]
         lib.price_american_batch.argtypes = [vp, i64, vp, ctypes.POINTER(_Options), vp, vp, vp]
+        lib.price_american_greeks_batch.argtypes = [vp, i64, vp, ctypes.POINTER(_Options), vp, vp, vp, vp]
         lib.price_american_batch_device.argtypes = [vp, i64, vp, ctypes.POINTER(_Options), vp,
                                                     vp, vp, vp, vp]
         lib.aop_linear_advance_device.argtypes = [vp, ctypes.c_int, ctypes.c_int, vp, i64, i64,
@@ -116,7 +117,7 @@ def load(path: Optional[str] = None):
                                                    vp, vp, vp]
         lib.aop_linear_advance_noalloc.restype = ctypes.c_int
         for f in ("aop_ctx_get_option_times", "aop_ctx_create", "aop_ctx_destroy", "price_american", "price_american_ex",
-                  "price_american_batch", "price_american_batch_device",
+                  "price_american_batch", "price_american_batch_device", "price_american_greeks_batch",
                   "aop_linear_advance_device", "aop_ctx_get_stats", "aop_ctx_autotune",
                   "aop_server_create", "aop_server_submit", "aop_server_poll", "aop_server_serve_stream",
                   "aop_server_info", "aop_server_destroy", "price_european_batch"):
@@ -254,6 +255,24 @@ class Context:
                                            ctypes.c_void_p(stream) if stream else None),
                "price_american_batch")
         return prices, status
+
+    def price_greeks(self, reqs, method: int = FFT_FP64, base_case: int = 0, stream: int = 0,
+                     flags: int = 0, ctas_per_sm: int = 0):
+        """Prices and (delta, gamma, theta) per option from the lattice rows
+        next to the root (C: price_american_greeks_batch); returns
+        (prices[n], greeks[n, 3], status[n])."""
+        arr = reqs if isinstance(reqs, np.ndarray) else requests_array(reqs)
+        n = len(arr)
+        prices = np.empty(n, dtype=np.float64)
+        greeks = np.empty((n, 3), dtype=np.float64)
+        status = np.empty(n, dtype=np.int32)
+        o = _opts(method, base_case, flags, ctas_per_sm)
+        _check(load().price_american_greeks_batch(self._h, n, arr.ctypes.data, ctypes.byref(o),
+                                                  prices.ctypes.data, greeks.ctypes.data,
+                                                  status.ctypes.data,
+                                                  ctypes.c_void_p(stream) if stream else None),
+               "price_american_greeks_batch")
+        return prices, greeks, status
 
     # device pointers (C: price_american_batch_device)
     def price_batch_device(self, n: int, d_reqs: int, d_prices: int, d_status: int = 0,

@@ -132,7 +132,8 @@ int resolve_base_case(const aop_ctx *c, const aop_options *opt) {
 void longest_first(int64_t n, const aop_request *reqs, int32_t *order) {
     std::vector<std::pair<int64_t, int32_t>> key((size_t)n);
     for (int64_t i = 0; i < n; i++)
-        key[(size_t)i] = {-(reqs[i].T * (reqs[i].model == AOP_BINOMIAL_CALL ? 1 : 2)), (int32_t)i};
+        key[(size_t)i] = {-(reqs[i].T * ((reqs[i].model == AOP_BINOMIAL_CALL ||
+                                          reqs[i].model == AOP_BINOMIAL_PUT) ? 1 : 2)), (int32_t)i};
     std::stable_sort(key.begin(), key.end(),
                      [](const std::pair<int64_t, int32_t> &a, const std::pair<int64_t, int32_t> &b) {
                          return a.first < b.first;
@@ -142,10 +143,12 @@ void longest_first(int64_t n, const aop_request *reqs, int32_t *order) {
 
 aop_status run_batch(aop_ctx *c, int64_t n, const aop_request *d_reqs, const aop_options *opt,
                      int64_t T_max, double *d_prices, int32_t *d_status, int32_t *d_bnd,
-                     const int64_t *d_bnd_off, cudaStream_t s, Params *d_params, const int32_t *d_order)
+                     const int64_t *d_bnd_off, cudaStream_t s, Params *d_params, const int32_t *d_order,
+                     double *d_greeks = nullptr)
 {
     const int method = opt ? opt->method : AOP_FFT_FP64;
     if (method < 0 || method > 3) return AOP_EINVAL;
+    if (d_greeks && method == AOP_STENCIL_FP64) return AOP_EINVAL;
     if (c->serving) return AOP_EBUSY;
     if (n == 0 || T_max < 1) return AOP_OK;
     const int B = resolve_base_case(c, opt);
@@ -184,9 +187,11 @@ aop_status run_batch(aop_ctx *c, int64_t n, const aop_request *d_reqs, const aop
         CK(cudaEventRecord(c->ev0, s));
         CK(run_dnc(method, n, d_params, T_max, B, c->ws, c->ws_size, tw, c->tw_log2, d_prices,
                    d_status, d_bnd, d_bnd_off, c->d_stats, c->d_err, opt_ns, opt ? opt->flags : 0,
-                   cap, c->device, s, nullptr, d_order));
+                   cap, c->device, s, nullptr, d_order, d_greeks));
         CK(cudaEventRecord(c->ev1, s));
     }
+    // lattice puts ran as mirrored calls: map their dividers back
+    if (d_bnd) CK(launch_mirror_boundaries(n, d_params, d_bnd, d_bnd_off, s));
     c->timed = true;
     c->last_n = n;
     return AOP_OK;
@@ -308,8 +313,9 @@ aop_status price_american_batch_device(aop_ctx *c, int64_t n, const aop_request 
     return run_batch(c, n, d_reqs, opt, T_max, d_prices, d_status, d_bnd, d_bnd_off, s, d_params, d_order);
 }
 
-aop_status price_american_batch(aop_ctx *c, int64_t n, const aop_request *reqs, const aop_options *opt,
-                                double *prices, aop_status *status, void *stream) {
+// Host-array batch, with optional sensitivities (greeks: 3 doubles per option).
+static aop_status host_batch(aop_ctx *c, int64_t n, const aop_request *reqs, const aop_options *opt,
+                             double *prices, double *greeks, aop_status *status, void *stream) {
     if (!c || n < 0 || (n > 0 && (!reqs || !prices))) return AOP_EINVAL;
     if (n == 0) return AOP_OK;
     CK(cudaSetDevice(c->device));
@@ -317,13 +323,15 @@ aop_status price_american_batch(aop_ctx *c, int64_t n, const aop_request *reqs, 
     const size_t rb = (size_t)n * sizeof(aop_request), pb = (size_t)n * sizeof(double),
                  sb = (size_t)n * sizeof(int32_t);
     const size_t ob = (size_t)n * sizeof(int32_t);
-    aop_status st = ensure_pinned(c, rb + pb + sb + ob + 64);
+    const size_t gb = greeks ? 3 * (size_t)n * sizeof(double) : 0;
+    aop_status st = ensure_pinned(c, rb + pb + sb + ob + gb + 64);
     if (st) return st;
-    // device arrays: reqs | prices | status | params | order
+    // device arrays: reqs | prices | status | params | order | greeks
     size_t off_p = (rb + 255) & ~(size_t)255, off_s = (off_p + pb + 255) & ~(size_t)255,
            off_par = (off_s + sb + 255) & ~(size_t)255,
-           off_ord = (off_par + (size_t)n * sizeof(Params) + 255) & ~(size_t)255;
-    st = ensure(&c->small, &c->small_size, off_ord + ob + 256, 0);
+           off_ord = (off_par + (size_t)n * sizeof(Params) + 255) & ~(size_t)255,
+           off_g = (off_ord + ob + 255) & ~(size_t)255;
+    st = ensure(&c->small, &c->small_size, off_g + gb + 256, 0);
     if (st) return st;
     char *d = (char *)c->small;
     aop_request *d_reqs = (aop_request *)d;
@@ -331,9 +339,11 @@ aop_status price_american_batch(aop_ctx *c, int64_t n, const aop_request *reqs, 
     int32_t *d_status = (int32_t *)(d + off_s);
     Params *d_params = (Params *)(d + off_par);
     int32_t *d_order = (int32_t *)(d + off_ord);
+    double *d_greeks = greeks ? (double *)(d + off_g) : nullptr;
     char *h = (char *)c->pinned;
     memcpy(h, reqs, rb);
     int32_t *h_order = (int32_t *)(h + rb + pb + sb);
+    double *h_greeks = (double *)(h + rb + pb + sb + ob);
     longest_first(n, reqs, h_order);
     int64_t T_max = 0;
     for (int64_t i = 0; i < n; i++)
@@ -341,17 +351,32 @@ aop_status price_american_batch(aop_ctx *c, int64_t n, const aop_request *reqs, 
     CK(cudaMemcpyAsync(d_reqs, h, rb, cudaMemcpyHostToDevice, s));
     CK(cudaMemcpyAsync(d_order, h_order, ob, cudaMemcpyHostToDevice, s));
     CK(launch_params(n, d_reqs, d_params, d_status, nullptr, s));
-    st = run_batch(c, n, d_reqs, opt, T_max, d_prices, d_status, nullptr, nullptr, s, d_params, d_order);
+    if (d_greeks) CK(cudaMemsetAsync(d_greeks, 0xff, gb, s));     // NaN for rejected options
+    st = run_batch(c, n, d_reqs, opt, T_max, d_prices, d_status, nullptr, nullptr, s, d_params, d_order,
+                   d_greeks);
     if (st) return st;
     CK(cudaMemcpyAsync(h + rb, d_prices, pb, cudaMemcpyDeviceToHost, s));
     CK(cudaMemcpyAsync(h + rb + pb, d_status, sb, cudaMemcpyDeviceToHost, s));
+    if (d_greeks) CK(cudaMemcpyAsync(h_greeks, d_greeks, gb, cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
     memcpy(prices, h + rb, pb);
+    if (greeks) memcpy(greeks, h_greeks, gb);
     if (status) {
         const int32_t *hs = (const int32_t *)(h + rb + pb);
         for (int64_t i = 0; i < n; i++) status[i] = (aop_status)hs[i];
     }
     return AOP_OK;
+}
+
+aop_status price_american_batch(aop_ctx *c, int64_t n, const aop_request *reqs, const aop_options *opt,
+                                double *prices, aop_status *status, void *stream) {
+    return host_batch(c, n, reqs, opt, prices, nullptr, status, stream);
+}
+
+aop_status price_american_greeks_batch(aop_ctx *c, int64_t n, const aop_request *reqs, const aop_options *opt,
+                                       double *prices, double *greeks, aop_status *status, void *stream) {
+    if (n > 0 && !greeks) return AOP_EINVAL;
+    return host_batch(c, n, reqs, opt, prices, greeks, status, stream);
 }
 
 aop_status price_european_batch(aop_ctx *c, int64_t n, const aop_request *reqs, double *prices,

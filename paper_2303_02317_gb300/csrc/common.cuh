@@ -6,6 +6,8 @@
 //   trinomial call  Sec. 4 and its appendix (weights m p_d, m p_o, m p_u on
 //                   G[i+1][j..j+2]; node price S u^{j-i})
 //   BSM put         Sec. 5, explicit scheme bsmG (weights b, c, a on k-1, k, k+1)
+//   binomial and trinomial puts: priced as the call of the mirrored lattice
+//                   (make_params below), so every kernel sees a call
 #pragma once
 
 #include <cstdint>
@@ -26,7 +28,7 @@ struct Params {
     int32_t D;           // columns added per row: 1 (binomial) or 2
     int32_t nw;          // stencil width (2 or 3)
     int32_t o_min;       // offset of w[0]: 0 (calls) or -1 (BSM)
-    int32_t pad0;
+    int32_t mirror;      // 1: a binomial/trinomial put priced as the mirrored call
     int64_t T;
     double w[3];         // weights on offsets o_min .. o_min+nw-1
     double wsum;         // sum of the weights = symbol at theta = 0
@@ -34,6 +36,7 @@ struct Params {
     double S, K;
     double xbase;        // calls: ln S - T logu;  BSM: ln(S/K) - T ds
     double out_scale;    // 1 for the calls, K for the put (price = K v)
+    double dt;           // calendar time per row, expiry / T (years)
     // Exponential tilt of the call stencil: a call value never exceeds its
     // node price S u^k, which grows like e^{kappa x} along a row, so tilted
     // convolutions carry v(x) e^{-kappa x} (kept near the local scale of the
@@ -96,24 +99,41 @@ __device__ inline void build_exp_tables(const Params &P, ExpTables &E) {
 
 // Lattice parameter setup (hot-path step a1).  Formulas as in the paper; the
 // trinomial Boyle form solves the two-moment system in closed form.
+//
+// Binomial and trinomial puts.  Dividing a put value by its node price
+// S u^x turns the put recursion into a call recursion on the same lattice,
+// mirrored in j: with j' = D i - j the cell holds C = G S / (S u^x) and
+//   C[i][j'] = max(sum_t w'_t C[i+1][j'+t], K u^{x'} - S),  x' = -x,
+// where w'_t is the put's weight on the child at mirrored offset t times that
+// child's price ratio (u^{+1} for the up child, u^{-1} for the down child).
+// That is the call with spot K, strike S, discount per step e^{-q dt} and
+// yield r (put-call symmetry of the lattice; McDonald and Schroder 1998), so
+// the recursion, its red/green divider (Cor. 2.7 applied to the mirrored call)
+// and every kernel below are the call's; only the boundary is mirrored back
+// (last green put column = D i - 1 - last red mirrored column).  The weights
+// are built from the put's own probabilities, so the identity is exact for
+// both trinomial forms.
 __device__ inline Params make_params(const aop_request &q) {
     Params P;
-    P.model = q.model;
+    const bool mirror = (q.model == AOP_BINOMIAL_PUT || q.model == AOP_TRINOMIAL_PUT);
+    P.model = mirror ? q.model - AOP_BINOMIAL_PUT : q.model;
     P.status = AOP_OK;
     P.T = q.T;
-    P.S = q.S0;
-    P.K = q.K;
+    P.S = mirror ? q.K : q.S0;
+    P.K = mirror ? q.S0 : q.K;
     P.w[0] = P.w[1] = P.w[2] = 0.0;
-    P.pad0 = 0;
+    P.mirror = mirror ? 1 : 0;
     P.out_scale = 1.0;
+    P.dt = (q.T >= 1) ? q.expiry / (double)q.T : 0.0;
     if (!(q.S0 > 0) || !(q.K > 0) || !(q.sigma > 0) || !(q.expiry > 0) || q.T < 1 ||
-        q.T > AOP_MAX_T || q.model < 0 || q.model > 2) {
+        q.T > AOP_MAX_T || q.model < 0 || q.model > AOP_TRINOMIAL_PUT) {
         P.status = AOP_EINVAL;
         P.D = 1; P.nw = 2; P.o_min = 0; P.wsum = 1; P.logu = 0; P.xbase = 0;
+        P.model = AOP_BINOMIAL_CALL; P.mirror = 0;
         return P;
     }
     const double T = (double)q.T;
-    if (q.model == AOP_BINOMIAL_CALL) {
+    if (P.model == AOP_BINOMIAL_CALL) {
         double dt = q.expiry / T;
         double logu = q.sigma * sqrt(dt);
         double u = exp(logu);
@@ -122,11 +142,16 @@ __device__ inline Params make_params(const aop_request &q) {
         double m = exp(-q.r * dt);
         if (!(p >= 0.0 && p <= 1.0)) P.status = AOP_EUNSTABLE;
         P.D = 1; P.nw = 2; P.o_min = 0;
-        P.w[0] = m * (1.0 - p);
-        P.w[1] = m * p;
+        if (mirror) {                 // mirrored offset 0 = up child, 1 = down child
+            P.w[0] = m * p * u;
+            P.w[1] = m * (1.0 - p) * d;
+        } else {
+            P.w[0] = m * (1.0 - p);
+            P.w[1] = m * p;
+        }
         P.logu = logu;
-        P.xbase = log(q.S0) - T * logu;
-    } else if (q.model == AOP_TRINOMIAL_CALL) {
+        P.xbase = log(P.S) - T * logu;
+    } else if (P.model == AOP_TRINOMIAL_CALL) {
         double dt = q.expiry / T;
         double m = exp(-q.r * dt);
         double logu, u, pu, pd, po;
@@ -153,19 +178,25 @@ __device__ inline Params make_params(const aop_request &q) {
             pd = (a11 * r2 - a21 * r1) / det;
             po = 1.0 - pu - pd;
         }
-        (void)u;
         if (!(pu >= 0 && pd >= 0 && po >= 0)) P.status = AOP_EUNSTABLE;
         P.D = 2; P.nw = 3; P.o_min = 0;
-        P.w[0] = m * pd; P.w[1] = m * po; P.w[2] = m * pu;
+        if (mirror) {                 // mirrored offsets 0, 1, 2 = up, middle, down child
+            P.w[0] = m * pu * u; P.w[1] = m * po; P.w[2] = m * pd / u;
+        } else {
+            P.w[0] = m * pd; P.w[1] = m * po; P.w[2] = m * pu;
+        }
         P.logu = logu;
-        P.xbase = log(q.S0) - T * logu;
+        P.xbase = log(P.S) - T * logu;
     } else {
-        if (q.q != 0.0) P.status = AOP_EINVAL;
+        // Sec. 5's scheme; a dividend yield q enters the first-derivative
+        // term only: v_tau = v_ss + (omega_q - 1) v_s - omega v with
+        // omega_q = 2(r - q)/sigma^2 (q = 0 is the paper's scheme).
         double dtau = q.sigma * q.sigma * q.expiry / (2.0 * T);
         double omega = 2.0 * q.r / (q.sigma * q.sigma);
+        double omega_q = 2.0 * (q.r - q.q) / (q.sigma * q.sigma);
         double ds = sqrt(3.0 * dtau);
         double al = dtau / (ds * ds);
-        double be = (omega - 1.0) * dtau / (2.0 * ds);
+        double be = (omega_q - 1.0) * dtau / (2.0 * ds);
         double a = al + be, b = al - be;
         double c = 1.0 - a - b - omega * dtau;
         if (!(a >= 0 && b >= 0 && c >= 0)) P.status = (P.status ? P.status : AOP_EUNSTABLE);

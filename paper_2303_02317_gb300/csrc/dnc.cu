@@ -163,6 +163,7 @@ struct DncArgs {
     int *err;
     aop_stats *stats;
     int64_t *opt_ns;       // per-option device time (nullable)
+    double *greeks;        // per option delta, gamma, theta (nullable)
     int flags;             // AOP_FLAG_* bits
     const int32_t *order;  // batch: the i-th option taken is order[i] (nullable: i)
     // serving session (sreq == nullptr in batch mode): requests are read from
@@ -905,11 +906,12 @@ struct Walker {
     int32_t *bnd;
     Counters &cnt;
     int lane;
+    double *gk;                   // delta, gamma, theta of this option (nullable)
 
-    __device__ Walker(Cta<MODE> &c_, double *buf, int32_t *bnd_, Counters &cnt_)
+    __device__ Walker(Cta<MODE> &c_, double *buf, int32_t *bnd_, Counters &cnt_, double *gk_ = nullptr)
         : c(c_), S(c_.S), P(c_.S.P), E(c_.S.E), exw(buf),
           bnd(bnd_), cnt(cnt_),
-          lane(threadIdx.x & 31) {}
+          lane(threadIdx.x & 31), gk(gk_) {}
 
     __device__ void record(int64_t row, int32_t v) const {
         if (bnd && lane == 0) bnd[row] = v;
@@ -1280,11 +1282,104 @@ struct Walker {
         return ret;
     }
 
+    // ----- sensitivities from the rows next to the root
+    // With gk set, the chain stops at row 2 of a call lattice (row T-2 of
+    // the put grid) and the last two rows are evaluated here in FP64 from
+    // that row's cells (red cells from the row buffer, green ones from the
+    // exercise value), which keeps rows 1 and 2 for delta, gamma and theta.
+    // The formulas are the standard lattice ones (centred differences on the
+    // nodes of rows 1-2, the time step between row 0 and the middle node of
+    // row 2 / row 1), in the option's own spot coordinates; a lattice put
+    // priced as a mirrored call is mapped back cell by cell first
+    // (put value = mirrored value times u^x, x the put node's exponent).
+    __device__ double finish_call_greeks(int64_t b, const Buf &row) {
+        const int D = P.D;
+        double g2[5], g1[3], g0 = 0.0;
+        int32_t b1 = -1, b0 = -1;
+        if (lane == 0) {
+            for (int j = 0; j <= 2 * D; j++)
+                g2[j] = (j <= b) ? cell_ld<MODE>(row, j) : exercise(P, E, ex_index(P, 2, j));
+            for (int j = 0; j <= D; j++) {
+                double cv = P.w[0] * g2[j] + P.w[1] * g2[j + 1];
+                if (D == 2) cv += P.w[2] * g2[j + 2];
+                const double e = exercise(P, E, ex_index(P, 1, j));
+                if (cv >= e) b1 = j;
+                g1[j] = fmax(cv, e);
+            }
+            double cv = P.w[0] * g1[0] + P.w[1] * g1[1];
+            if (D == 2) cv += P.w[2] * g1[2];
+            const double e = exercise(P, E, ex_index(P, 0, 0));
+            if (cv >= e) b0 = 0;
+            g0 = fmax(cv, e);
+            if (bnd) { bnd[1] = b1; bnd[0] = b0; }
+            // option-side rows: o2[j], o1[j] with node price S0 u^{x(i, j)}
+            const double u = exp(P.logu);
+            const double S0 = P.mirror ? P.K : P.S;
+            double o2[5], o1[3];
+            for (int j = 0; j <= 2 * D; j++) {
+                const int x = (D == 1) ? 2 * j - 2 : j - 2;
+                o2[j] = P.mirror ? g2[2 * D - j] * exp(x * P.logu) : g2[j];
+            }
+            for (int j = 0; j <= D; j++) {
+                const int x = (D == 1) ? 2 * j - 1 : j - 1;
+                o1[j] = P.mirror ? g1[D - j] * exp(x * P.logu) : g1[j];
+            }
+            const double d = 1.0 / u;
+            double delta, gamma, theta;
+            if (D == 1) {
+                delta = (o1[1] - o1[0]) / (S0 * (u - d));
+                const double up = (o2[2] - o2[1]) / (S0 * (u * u - 1.0));
+                const double dn = (o2[1] - o2[0]) / (S0 * (1.0 - d * d));
+                gamma = (up - dn) / (0.5 * S0 * (u * u - d * d));
+                theta = (o2[1] - g0) / (2.0 * P.dt);
+            } else {
+                delta = (o1[2] - o1[0]) / (S0 * (u - d));
+                const double up = (o1[2] - o1[1]) / (S0 * (u - 1.0));
+                const double dn = (o1[1] - o1[0]) / (S0 * (1.0 - d));
+                gamma = (up - dn) / (0.5 * S0 * (u - d));
+                theta = (o1[1] - g0) / P.dt;
+            }
+            gk[0] = delta; gk[1] = gamma; gk[2] = theta;
+        }
+        return __shfl_sync(0xffffffffu, g0, 0);
+    }
+
+    __device__ double finish_put_greeks(int64_t f, const Buf &row) {
+        const int64_t T = P.T;
+        double v2[5], v1[3], v0 = 0.0;
+        int32_t f1 = AOP_BOUNDARY_NONE_PUT, f0 = AOP_BOUNDARY_NONE_PUT;
+        if (lane == 0) {
+            for (int k = -2; k <= 2; k++)
+                v2[k + 2] = (k <= f) ? exercise(P, E, ex_index(P, T - 2, k)) : cell_ld<MODE>(row, k);
+            for (int k = -1; k <= 1; k++) {
+                const double cv = P.w[0] * v2[k + 1] + P.w[1] * v2[k + 2] + P.w[2] * v2[k + 3];
+                const double e = exercise(P, E, ex_index(P, T - 1, k));
+                if (e > cv) f1 = k;
+                v1[k + 1] = fmax(cv, e);
+            }
+            const double cv = P.w[0] * v1[0] + P.w[1] * v1[1] + P.w[2] * v1[2];
+            const double e = exercise(P, E, ex_index(P, T, 0));
+            if (e > cv) f0 = 0;
+            v0 = fmax(cv, e);
+            if (bnd) { bnd[T - 1] = f1; bnd[T] = f0; }
+            const double K = P.out_scale, S0 = P.S;
+            const double up = exp(P.logu), dn = exp(-P.logu);
+            const double delta = K * (v1[2] - v1[0]) / (S0 * (up - dn));
+            const double gu = K * (v1[2] - v1[1]) / (S0 * (up - 1.0));
+            const double gd = K * (v1[1] - v1[0]) / (S0 * (1.0 - dn));
+            gk[0] = delta;
+            gk[1] = (gu - gd) / (0.5 * S0 * (up - dn));
+            gk[2] = K * (v1[1] - v0) / P.dt;
+        }
+        return P.out_scale * __shfl_sync(0xffffffffu, v0, 0);
+    }
+
     __device__ double price_call(int64_t b) {
         const int D = P.D;
         const Buf row{(double *)(c.slot + c.a.off_r0), 0};
+        const int64_t stop = gk ? 2 : 0;     // gk needs P.T >= 3
         int64_t i = P.T - 1;
-        while (i > 0) {
+        while (i > stop) {
             if (S.err) return __longlong_as_double(0x7ff8000000000000ll);
             if (b >= 0) {
                 // a red value never exceeds its node price; transforms (sums
@@ -1296,14 +1391,15 @@ struct Walker {
                     return __longlong_as_double(0x7ff8000000000000ll);
                 }
             }
-            if (b < 0) {
+            if (b < 0) {                     // rows 0 .. i are green
                 record_range(0, i - 1, -1);
+                if (gk) return finish_call_greeks(-1, row);
                 return exercise(P, E, ex_index(P, 0, 0));
             }
             const int64_t avail = i - kLeftoverCall;
             if (avail < c.a.B) {
-                b = naive_call(i, 0, b, i, row, row);
-                i = 0;
+                b = naive_call(i, 0, b, i - stop, row, row);
+                i = stop;
                 break;
             }
             const int64_t w = b + 1;
@@ -1313,6 +1409,7 @@ struct Walker {
             b = solve_call(i, b, h, row);
             i -= h;
         }
+        if (gk) return S.err ? 0.0 : finish_call_greeks(b, row);
         if (b < 0) return exercise(P, E, ex_index(P, 0, 0));
         return cell_ld<MODE>(row, 0);
     }
@@ -1388,18 +1485,20 @@ struct Walker {
     __device__ double price_put(int64_t f) {
         const int64_t T = P.T;
         const Buf row{(double *)(c.slot + c.a.off_r0), -T};
+        const int64_t stop = gk ? 2 : 0;     // gk needs T >= 3
         int64_t n = 1;
-        while (T - n > 0) {
+        while (T - n > stop) {
             if (S.err) return __longlong_as_double(0x7ff8000000000000ll);
             const int64_t R = T - n;
             if (f >= R) {                // every remaining cell is green
                 if (bnd)
                     for (int64_t r = n + 1 + lane; r <= T; r += 32) bnd[r] = (int32_t)(T - r);
+                if (gk) return finish_put_greeks(T, row);
                 return P.out_scale * exercise(P, E, ex_index(P, T, 0));
             }
             if (R < 2 * c.a.B) {
-                f = naive_put(n, -R, R, f, R, row, row);
-                n = T;
+                f = naive_put(n, -R, R, f, R - stop, row, row);
+                n = T - stop;
                 break;
             }
             int64_t h = c.a.B;
@@ -1407,6 +1506,7 @@ struct Walker {
             f = solve_put(n, -R, R, f, h, row);
             n += h;
         }
+        if (gk) return S.err ? 0.0 : finish_put_greeks(f, row);
         if (f >= 0) return P.out_scale * exercise(P, E, ex_index(P, T, 0));
         return P.out_scale * cell_ld<MODE>(row, 0);
     }
@@ -1615,8 +1715,9 @@ dnc_kernel(const __grid_constant__ DncArgs a)
             c.tilt = MODE == 1 || (a.flags & AOP_FLAG_TILT_ON) || first >= (int64_t)S.P.D * (S.P.T - 1) ||
                      sb - S.P.K > 2.0 * S.P.S;
         }
+        double *gk = (a.greeks && S.P.T >= 3) ? a.greeks + 3 * o : nullptr;
         if (role == 0) {
-            Walker<MODE> wk(c, walker_buf, bnd, cnt);
+            Walker<MODE> wk(c, walker_buf, bnd, cnt, gk);
             const uint64_t tw0 = gtime();
             const double price = put ? wk.price_put(first) : wk.price_call(first);
             if (lane == 0) {
@@ -1676,6 +1777,8 @@ dnc_kernel(const __grid_constant__ DncArgs a)
         if (threadIdx.x == 0) {
             const int err = S.err;
             a.prices[o] = err ? __longlong_as_double(0x7ff8000000000000ll) : S.price;
+            if (a.greeks && (err || S.P.T < 3))
+                for (int g = 0; g < 3; g++) a.greeks[3 * o + g] = __longlong_as_double(0x7ff8000000000000ll);
             if (err) {
                 if (a.status) a.status[o] = err;
                 if (a.err) atomicCAS(a.err, 0, err);
@@ -1860,7 +1963,7 @@ cudaError_t run_dnc(int method, int64_t n, const Params *d_params, int64_t T_max
                     void *ws, size_t ws_bytes, const void *d_tw, int tw_log2, double *d_prices,
                     int32_t *d_status, int32_t *d_bnd, const int64_t *d_bnd_off,
                     aop_stats *d_stats, int *d_err, int64_t *d_opt_ns, int flags, int cap, int device,
-                    cudaStream_t s, const ServeSession *srv, const int32_t *d_order)
+                    cudaStream_t s, const ServeSession *srv, const int32_t *d_order, double *d_greeks)
 {
     if (srv) n = srv->capacity;
     if (n == 0) return cudaSuccess;
@@ -1904,6 +2007,7 @@ cudaError_t run_dnc(int method, int64_t n, const Params *d_params, int64_t T_max
     a.err = d_err;
     a.stats = d_stats;
     a.opt_ns = d_opt_ns;
+    a.greeks = srv ? nullptr : d_greeks;
     a.flags = flags;
     a.order = d_order;
     if (srv) {

@@ -36,6 +36,10 @@ struct Arena {
 cudaError_t launch_params(int64_t n, const aop_request *d_reqs, Params *d_params,
                           int32_t *d_status, int64_t *d_tmax, cudaStream_t s);
 cudaError_t launch_twiddles(int log2n, void *d_tw32, void *d_tw64, cudaStream_t s);
+// Boundaries of options whose Params have mirror set (binomial and trinomial
+// puts priced as mirrored calls): b[i] <- D i - 1 - b[i] for rows 0..T.
+cudaError_t launch_mirror_boundaries(int64_t n, const Params *d_params, int32_t *d_bnd,
+                                     const int64_t *d_bnd_off, cudaStream_t s);
 cudaError_t launch_fill_i32(int32_t *p, int64_t n, int32_t v, cudaStream_t s);
 
 // stencil.cu -- plain Theta(T^2) lattice loop (temporally blocked)
@@ -66,7 +70,8 @@ cudaError_t run_dnc(int method, int64_t n, const Params *d_params, int64_t T_max
                     void *ws, size_t ws_bytes, const void *d_tw, int tw_log2, double *d_prices,
                     int32_t *d_status, int32_t *d_bnd, const int64_t *d_bnd_off,
                     aop_stats *d_stats, int *d_err, int64_t *d_opt_ns, int flags, int cap, int device,
-                    cudaStream_t s, const ServeSession *srv = nullptr, const int32_t *d_order = nullptr);
+                    cudaStream_t s, const ServeSession *srv = nullptr, const int32_t *d_order = nullptr,
+                    double *d_greeks = nullptr);
 cudaError_t run_linear_advance(int method, int nw, const double *w, int64_t count, int64_t W,
                                int64_t h, const double *d_in, double *d_out, const void *d_tw,
                                int tw_log2, void *ws, size_t ws_bytes, int *d_err,

@@ -54,6 +54,20 @@ __global__ void twiddle_kernel(int log2n, float4 *tw32, double2 *tw64)
     }
 }
 
+// One block per option (grid-stride over options); the rows of a mirrored
+// option are independent.
+__global__ void mirror_boundary_kernel(int64_t n, const Params *params, int32_t *bnd,
+                                       const int64_t *bnd_off)
+{
+    for (int64_t o = blockIdx.x; o < n; o += gridDim.x) {
+        const Params &P = params[o];
+        if (!P.mirror || P.status != AOP_OK) continue;
+        int32_t *b = bnd + bnd_off[o];
+        for (int64_t i = threadIdx.x; i <= P.T; i += blockDim.x)
+            b[i] = (int32_t)((int64_t)P.D * i - 1 - b[i]);
+    }
+}
+
 __global__ void fill_i32_kernel(int32_t *p, int64_t n, int32_t v)
 {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
@@ -70,6 +84,15 @@ cudaError_t launch_params(int64_t n, const aop_request *d_reqs, Params *d_params
     int blocks = (int)std::min<int64_t>((n + 255) / 256, 1024);
     params_kernel<<<blocks, 256, 0, s>>>(n, d_reqs, d_params, d_status,
                                          (unsigned long long *)d_tmax);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_mirror_boundaries(int64_t n, const Params *d_params, int32_t *d_bnd,
+                                     const int64_t *d_bnd_off, cudaStream_t s)
+{
+    if (n == 0) return cudaSuccess;
+    int blocks = (int)std::min<int64_t>(n, 1024);
+    mirror_boundary_kernel<<<blocks, 256, 0, s>>>(n, d_params, d_bnd, d_bnd_off);
     return cudaGetLastError();
 }
 

@@ -8,7 +8,8 @@ workloads below are synthetic option books with the parameter ranges of the
 benchmark configurations.
 
 Model codes: 0 = binomial (CRR) American call, 1 = trinomial American call,
-2 = Black-Scholes-Merton explicit finite-difference American put.
+2 = Black-Scholes-Merton explicit finite-difference American put, 3 = binomial
+American put, 4 = trinomial American put.
 """
 from __future__ import annotations
 
@@ -18,7 +19,7 @@ from typing import List, Tuple
 
 import numpy as np
 
-BINOMIAL_CALL, TRINOMIAL_CALL, BSM_PUT = 0, 1, 2
+BINOMIAL_CALL, TRINOMIAL_CALL, BSM_PUT, BINOMIAL_PUT, TRINOMIAL_PUT = 0, 1, 2, 3, 4
 TRI_BOYLE, TRI_PAPER = 0, 1
 SQRT3 = math.sqrt(3.0)
 
@@ -53,6 +54,13 @@ def fixed_call(model: int, T: int, tri_form: int = TRI_BOYLE) -> Request:
     1 year (trinomial: Boyle form with lambda=sqrt(3) unless the paper form
     is asked for)."""
     lam = SQRT3 if (model == TRINOMIAL_CALL and tri_form == TRI_BOYLE) else 0.0
+    return Request(model, 100.0, 100.0, 0.05, 0.03, 0.25, 1.0, int(T), lam, tri_form)
+
+
+def fixed_put(model: int, T: int, tri_form: int = TRI_BOYLE) -> Request:
+    """Binomial or trinomial put at S0=K=100, r=0.05, q=0.03, sigma=0.25,
+    1 year (the fixed call's parameters)."""
+    lam = SQRT3 if (model == TRINOMIAL_PUT and tri_form == TRI_BOYLE) else 0.0
     return Request(model, 100.0, 100.0, 0.05, 0.03, 0.25, 1.0, int(T), lam, tri_form)
 
 
@@ -118,16 +126,19 @@ def request_stream(n: int = 65536, rate: float = 20000.0, seed: int = 2317,
     return reqs, arrivals
 
 
-def random_small(n: int, seed: int, T_range=(8, 600), models=(0, 1, 2)) -> List[Request]:
+def random_small(n: int, seed: int, T_range=(8, 600), models=(0, 1, 2),
+                 bsm_yield: bool = False) -> List[Request]:
     """Small mixed cases for parity tests: T uniform in T_range, parameters as
-    in the precision sweep, trinomial cases alternate Boyle and paper forms."""
+    in the precision sweep, trinomial cases alternate Boyle and paper forms.
+    BSM puts have q = 0 unless bsm_yield, which draws q like the lattices."""
     rng = np.random.default_rng(seed)
     out: List[Request] = []
     for i in range(n):
         m = int(models[i % len(models)])
-        S0, K, sigma, r, q, E = (float(x[0]) for x in _draw_params(rng, 1, put=(m == BSM_PUT)))
+        S0, K, sigma, r, q, E = (float(x[0]) for x in
+                                 _draw_params(rng, 1, put=(m == BSM_PUT and not bsm_yield)))
         T = int(rng.integers(T_range[0], T_range[1] + 1))
-        if m == TRINOMIAL_CALL:
+        if m in (TRINOMIAL_CALL, TRINOMIAL_PUT):
             form = TRI_PAPER if (i // len(models)) % 2 else TRI_BOYLE
             out.append(Request(m, S0, K, r, q, sigma, E, T, SQRT3 if form == TRI_BOYLE else 0.0, form))
         else:

@@ -177,7 +177,7 @@ def test_invalid_and_unstable_requests(ctx):
     bad = [
         wl.Request(0, 0.0, 100, 0.05, 0.03, 0.2, 1.0, 64),      # S0 <= 0
         wl.Request(0, 100, 100, 0.05, 0.03, 0.0, 1.0, 64),      # sigma <= 0
-        wl.Request(2, 100, 100, 0.05, 0.01, 0.2, 1.0, 64),      # BSM with a yield
+        wl.Request(5, 100, 100, 0.05, 0.01, 0.2, 1.0, 64),      # unknown model
         wl.Request(0, 100, 100, 0.5, 0.0, 0.001, 1.0, 4),       # p > 1
     ]
     for method in METHODS:
