@@ -14,7 +14,7 @@ measured error (fp32_split), the same book through the host-buffer C-ABI call
 the per-option error against the FP64 FFT pricer and the CPU oracle, the
 roofline of the pricing kernel and the CPU oracle timed on the host cores.
 The D&C schedule (base-case height, options in flight per SM) is picked by the
-library's autotuner on half of the book before the warm-up steps.
+library's autotuner on the book before the warm-up steps.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 Multi-GPU (torchrun): every rank prices its own copy of the book (weak
@@ -427,9 +427,9 @@ def main():
 
     tuned = {}
     if not args.no_tune:
-        tuned = {"method": ctx.autotune(arr[::2], method)}
+        tuned = {"method": ctx.autotune(arr, method)}
         if method != aop.FFT_FP32SPLIT and not args.no_fp32:
-            tuned["fp32_split"] = ctx.autotune(arr[::2], aop.FFT_FP32SPLIT)
+            tuned["fp32_split"] = ctx.autotune(arr, aop.FFT_FP32SPLIT)
 
     def step(m=method):
         ctx.price_batch_device(n, d_reqs.data_ptr(), d_prices.data_ptr(), d_status.data_ptr(),

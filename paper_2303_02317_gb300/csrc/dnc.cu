@@ -293,7 +293,7 @@ __device__ int band_mc(const Params &P, int64_t g, int64_t N, bool tilt) {
 
 // s(theta_m)^g in FP64: magnitude through log1p of the exactly formed
 // 1 - |s/s(0)|^2, phase g * arg s reduced in units of pi.
-__device__ double2 bin_value(const Params &P, int64_t g, int lgN, int64_t m, bool tilt) {
+__device__ __noinline__ double2 bin_value(const Params &P, int64_t g, int lgN, int64_t m, bool tilt) {
     const double N = (double)((int64_t)1 << lgN);
     const double *w = tilt ? P.wt : P.w;
     const double wsum = tilt ? P.wtsum : P.wsum;
@@ -545,59 +545,63 @@ struct Cta {
     // e = idx(s) (zero past the window W), converted by the storage policy ST
     // (8-byte stored values).  The values are staged with cp.async (all in
     // flight at once; padding is zero-filled, not read) and converted in shared
-    // memory: in place for 8-byte transform values; for 16-byte values they are
-    // staged in the upper half of the tile and read into registers before any
-    // value is written.
+    // memory: in place for 8-byte transform values; 16-byte values are staged
+    // in the upper half of the tile and converted in rounds of 16 values a
+    // thread, each round read into registers before any of it is written (a
+    // round's writes only cover staged values of that round or earlier ones).
     template <class G, class ST, class IDX>
-    __device__ void stage_input(V *tile, int64_t count, IDX idx, const Buf &in, int64_t x_lo, int64_t W) {
+    __device__ void stage_input(V *tile, int count, IDX idx, const Buf &in, int64_t x_lo, int64_t W) {
         using T = typename ST::T;
         static_assert(sizeof(T) == 8, "stored values are 8 bytes");
-        constexpr int kPer = 16;     // values per thread: count <= 16 * group size
         const T *src = (const T *)in.p - in.base;
         if constexpr (sizeof(V) == 8) {
-            for (int64_t s = G::rank(); s < count; s += G::size()) {
-                const int64_t e = idx(s);
+            for (int s = G::rank(); s < count; s += G::size()) {
+                const int e = idx(s);
                 const bool ok = e < W;
                 fft::cp_async<8>(&tile[s], ok ? (const void *)&src[x_lo + e] : (const void *)in.p, ok ? 8 : 0);
             }
             fft::cp_async_wait();
             if constexpr (!ST::kIdentity) {
-                for (int64_t s = G::rank(); s < count; s += G::size()) {
+                for (int s = G::rank(); s < count; s += G::size()) {
                     const T d = *(const T *)&tile[s];
                     tile[s] = ST::to_v(d);
                 }
             }
             if (tilt) {
-                for (int64_t s = G::rank(); s < count; s += G::size()) {
-                    const int64_t e = idx(s);
+                for (int s = G::rank(); s < count; s += G::size()) {
+                    const int e = idx(s);
                     if (e < W) tile[s] = tilt_in(tile[s], W - 1 - e);
                 }
             }
         } else {
+            constexpr int kPer = 16;
             T *st = (T *)tile + count;
-            for (int64_t s = G::rank(); s < count; s += G::size()) {
-                const int64_t e = idx(s);
+            for (int s = G::rank(); s < count; s += G::size()) {
+                const int e = idx(s);
                 const bool ok = e < W;
                 fft::cp_async<8>(&st[s], ok ? (const void *)&src[x_lo + e] : (const void *)in.p, ok ? 8 : 0);
             }
             fft::cp_async_wait();
-            T r[kPer];
+            for (int base = 0; base < count; base += kPer * G::size()) {
+                T r[kPer];
 #pragma unroll
-            for (int k = 0; k < kPer; k++) {
-                const int64_t s = G::rank() + (int64_t)k * G::size();
-                if (s < count) r[k] = st[s];
-            }
-            G::sync();
+                for (int k = 0; k < kPer; k++) {
+                    const int s = base + G::rank() + k * G::size();
+                    if (s < count) r[k] = st[s];
+                }
+                G::sync();
 #pragma unroll
-            for (int k = 0; k < kPer; k++) {
-                const int64_t s = G::rank() + (int64_t)k * G::size();
-                if (s < count) {
-                    tile[s] = ST::to_v(r[k]);
-                    if (tilt) {
-                        const int64_t e = idx(s);
-                        if (e < W) tile[s] = tilt_in(tile[s], W - 1 - e);
+                for (int k = 0; k < kPer; k++) {
+                    const int s = base + G::rank() + k * G::size();
+                    if (s < count) {
+                        tile[s] = ST::to_v(r[k]);
+                        if (tilt) {
+                            const int e = idx(s);
+                            if (e < W) tile[s] = tilt_in(tile[s], W - 1 - e);
+                        }
                     }
                 }
+                G::sync();
             }
         }
         G::sync();
@@ -610,8 +614,8 @@ struct Cta {
 
     // tile[s] = scr[idx(s)] for s < count, through cp.async
     template <class G, class IDX>
-    __device__ void stage_scratch(V *tile, int64_t count, IDX idx, const V *scr) {
-        for (int64_t s = G::rank(); s < count; s += G::size())
+    __device__ void stage_scratch(V *tile, int count, IDX idx, const V *scr) {
+        for (int s = G::rank(); s < count; s += G::size())
             fft::cp_async<(int)sizeof(V)>(&tile[s], &scr[idx(s)], (int)sizeof(V));
         fft::cp_async_wait();
         G::sync();
@@ -627,55 +631,32 @@ struct Cta {
 
     // One pass over global memory: the stages with half-sizes 2^s_lo .. 2^s_hi
     // of an N-point transform, on tiles of (2^(s_hi-s_lo+1) elements x Q
-    // consecutive columns) staged in shared memory.  DIF = forward (stages top
-    // down); otherwise inverse.  The first forward pass reads (and splits) the
-    // FP64 input; the last inverse pass extracts the FP64 output.
+    // consecutive columns) staged in shared memory, radix-4 inside the tile.
+    // DIF = forward (stages top down); otherwise inverse.  The first forward
+    // pass reads (and splits) the FP64 input; the last inverse pass extracts
+    // the FP64 output.
     template <class G, class ST, bool DIF>
     __device__ void tile_pass(V *tile, int lg_tile, V *scr, int lgN, int s_lo, int s_hi, bool first, bool last,
                               const Buf &in, int64_t x_lo, int64_t W, const Buf &out, int64_t y_lo, int64_t off,
                               int64_t nout, const ConvScale &cs) {
         const int L = s_hi - s_lo + 1;
-        const int64_t Gn = (int64_t)1 << L;
-        const int64_t lo_count = (int64_t)1 << s_lo;
-        const int64_t hi_count = ((int64_t)1 << lgN) >> (s_hi + 1);
-        const int64_t Q = min(lo_count, ((int64_t)1 << lg_tile) >> L);
+        const int lgQ = min(s_lo, lg_tile - L);
+        const int qm = (1 << lgQ) - 1;
+        const int count = 1 << (L + lgQ);
+        const int lo_count = 1 << s_lo;
+        const int hi_count = 1 << (lgN - s_hi - 1);
         const Tw *T = tw();
-        const int twl = a.tw_log2;
-        for (int64_t hb = 0; hb < hi_count; hb++) {
-            const int64_t hbase = hb << (s_hi + 1);
-            for (int64_t q0 = 0; q0 < lo_count; q0 += Q) {
-                auto idx = [=](int64_t s) {
-                    const int64_t t = s / Q, q = s - t * Q;
-                    return hbase + (t << s_lo) + q0 + q;
-                };
-                if (first) stage_input<G, ST>(tile, Gn * Q, idx, in, x_lo, W);
-                else stage_scratch<G>(tile, Gn * Q, idx, scr);
-                for (int step = 0; step < L; step++) {
-                    const int lm = DIF ? (L - 1 - step) : step;
-                    const int64_t m = (int64_t)1 << lm;
-                    const int lgM2 = lm + s_lo + 1;
-                    for (int64_t s = G::rank(); s < (Gn / 2) * Q; s += G::size()) {
-                        const int64_t pr = s / Q, q = s - pr * Q;
-                        const int64_t tm = pr & (m - 1);
-                        const int64_t t = ((pr - tm) << 1) + tm;
-                        const int64_t k = (tm << s_lo) + q0 + q;
-                        const Tw w = fft::tw_get<MODE>(T, twl, k, lgM2);
-                        V *pa = &tile[t * Q + q], *pb = &tile[(t + m) * Q + q];
-                        if (DIF) {
-                            V u = *pa, v = *pb;
-                            *pa = fft::cadd(u, v);
-                            *pb = fft::twmul<false>(fft::csub(u, v), w);
-                        } else {
-                            V u = *pa, v = fft::twmul<true>(*pb, w);
-                            *pa = fft::cadd(u, v);
-                            *pb = fft::csub(u, v);
-                        }
-                    }
-                    G::sync();
-                }
-                for (int64_t s = G::rank(); s < Gn * Q; s += G::size()) {
-                    const int64_t t = s / Q, q = s - t * Q;
-                    const int64_t e = hbase + (t << s_lo) + q0 + q;
+        for (int hb = 0; hb < hi_count; hb++) {
+            const int hbase = hb << (s_hi + 1);
+            for (int q0 = 0; q0 < lo_count; q0 += qm + 1) {
+                auto idx = [=](int s) { return hbase + ((s >> lgQ) << s_lo) + q0 + (s & qm); };
+                if (first) stage_input<G, ST>(tile, count, idx, in, x_lo, W);
+                else stage_scratch<G>(tile, count, idx, scr);
+                const fft::Cols cl{lgQ, s_lo, q0};
+                if (DIF) fft::dif_cols<MODE, G>(tile, L, L - 1, 0, cl, T);
+                else fft::dit_cols<MODE, G>(tile, L, 0, L - 1, cl, T);
+                for (int s = G::rank(); s < count; s += G::size()) {
+                    const int e = idx(s);
                     if (last) {
                         const int64_t k = e - off;
                         if (k >= 0 && k < nout) store<ST>(out, y_lo + k, untilt<ST>(ST::from_v(tile[s], cs), W - 1 - k, cs));
@@ -720,17 +701,16 @@ struct Cta {
             cnt.conv_out += nout;
         }
         const Tw *T = tw();
-        const int twl = a.tw_log2;
         if (lgN <= lg_tile) {
             const long long q1 = clock64();
-            stage_input<G, ST>(tile, N, [](int64_t s) { return s; }, in, x_lo, W);
+            stage_input<G, ST>(tile, (int)N, [](int s) { return s; }, in, x_lo, W);
             const long long q2 = clock64();
-            fft::dif_range<MODE, G>(tile, N, lgN - 1, 0, T, twl);
-            for (int64_t p = G::rank(); p < N; p += G::size())
+            fft::dif_all<MODE, G>(tile, lgN, T);
+            for (int p = G::rank(); p < (int)N; p += G::size())
                 tile[p] = mul_bin(tile[p], sp, mc, fft::brev_n((uint32_t)p, lgN), (uint32_t)N, g, lgN);
             G::sync();
             const long long q3 = clock64();
-            fft::dit_range<MODE, G>(tile, N, 0, lgN - 1, T, twl);
+            fft::dit_all<MODE, G>(tile, lgN, T);
             const long long q4 = clock64();
             for (int64_t t = G::rank(); t < nout; t += G::size())
                 store<ST>(out, y_lo + t, untilt<ST>(ST::from_v(tile[off + t], cs), W - 1 - t, cs));
@@ -746,37 +726,38 @@ struct Cta {
             return lgN;
         }
         if (leader<G>()) cnt.gbytes += (int64_t)sizeof(V) * N * 4 + 8 * (W + nout);
-        // outer stages lg_tile .. lgN-1 in chunks of at most lg_tile - 2 stages
-        // (so that a tile row spans >= 4 consecutive elements)
-        const int chunk = max(1, lg_tile - 2);
-        int nch = 0;
+        // outer stages lg_tile .. lgN-1 in as few passes as the tile allows,
+        // balanced: a pass of L stages moves rows of Q = 2^(lg_tile - L)
+        // consecutive values, at least 32 bytes (one DRAM sector)
+        const int chunk = max(1, lg_tile - (sizeof(V) >= 16 ? 1 : 2));
+        const int outer = lgN - lg_tile;
+        const int nch = min(16, (outer + chunk - 1) / chunk);
         int ch_lo[16], ch_hi[16];
-        for (int s_hi = lgN - 1; s_hi >= lg_tile && nch < 16; ) {
-            int s_lo = max(lg_tile, s_hi - chunk + 1);
-            ch_lo[nch] = s_lo;
-            ch_hi[nch] = s_hi;
-            nch++;
-            s_hi = s_lo - 1;
+        for (int c = 0, s_hi = lgN - 1; c < nch; c++) {
+            const int len = outer / nch + (c < outer % nch ? 1 : 0);
+            ch_hi[c] = s_hi;
+            ch_lo[c] = s_hi - len + 1;
+            s_hi -= len;
         }
         for (int c = 0; c < nch; c++)
             tile_pass<G, ST, true>(tile, lg_tile, scr, lgN, ch_lo[c], ch_hi[c], c == 0, false, in, x_lo, W, out, y_lo,
-                               off, nout, cs);
+                                   off, nout, cs);
         // inner stages on contiguous blocks, with the kernel-power product
-        const int64_t N2 = (int64_t)1 << lg_tile;
-        for (int64_t b = 0; b < N / N2; b++) {
-            V *blk = scr + b * N2;
-            stage_scratch<G>(tile, N2, [](int64_t s) { return s; }, blk);
-            fft::dif_range<MODE, G>(tile, N2, lg_tile - 1, 0, T, twl);
-            for (int64_t s = G::rank(); s < N2; s += G::size())
+        const int N2 = 1 << lg_tile;
+        for (int b = 0; b < (int)(N / N2); b++) {
+            V *blk = scr + (int64_t)b * N2;
+            stage_scratch<G>(tile, N2, [](int s) { return s; }, blk);
+            fft::dif_all<MODE, G>(tile, lg_tile, T);
+            for (int s = G::rank(); s < N2; s += G::size())
                 tile[s] = mul_bin(tile[s], sp, mc, fft::brev_n((uint32_t)(b * N2 + s), lgN), (uint32_t)N, g, lgN);
             G::sync();
-            fft::dit_range<MODE, G>(tile, N2, 0, lg_tile - 1, T, twl);
-            for (int64_t s = G::rank(); s < N2; s += G::size()) blk[s] = tile[s];
+            fft::dit_all<MODE, G>(tile, lg_tile, T);
+            for (int s = G::rank(); s < N2; s += G::size()) blk[s] = tile[s];
             G::sync();
         }
         for (int c = nch - 1; c >= 0; c--)
             tile_pass<G, ST, false>(tile, lg_tile, scr, lgN, ch_lo[c], ch_hi[c], false, c == 0, in, x_lo, W, out, y_lo,
-                                off, nout, cs);
+                                    off, nout, cs);
         return lgN;
     }
 };
@@ -1843,7 +1824,7 @@ Layout make_layout(int method, int64_t T_max, int B, int scratch_units) {
     L.vsz = value_bytes(method);
     L.W_max = 2 * T_max + 1;
     L.N_max = (int64_t)1 << ilog2_ceil(L.W_max);
-    L.lg_tile = (L.vsz == 8) ? 10 : 9;       // 8 KiB per worker tile
+    L.lg_tile = 10;                           // 8 KiB (FP32 split) or 16 KiB per worker tile
     L.lg_block = (L.vsz == 8) ? 12 : 11;     // 32 KiB block tile (linear advance entry points)
     L.tw_log2 = std::max(ilog2_ceil(L.N_max), L.lg_block + 1);
     L.spec_cap = std::max<int64_t>(1 << 17, L.N_max / 2 + 2);

@@ -194,106 +194,157 @@ __device__ __forceinline__ void cp_async(void *smem_dst, const void *gmem_src, i
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
 // --------------------------------------------------- in-place stage kernels
-// The group G cooperates on the N values of x (shared or global memory); the
-// caller synchronises the group between calls.
+// A tile holds rows x 2^lgQ columns (row t, column q at x[(t << lgQ) + q]).
+// Each column is a sub-transform of a longer transform whose consecutive rows
+// lie 2^s_lo elements apart, column q at offset q0 + q; a stage of half-size
+// M = 2^lgM rows then takes its twiddles from level lgM + s_lo + 1 at index
+// (tm << s_lo) + q0 + q, tm the row offset inside the half.  A plain tile is
+// one column (lgQ = s_lo = q0 = 0).  The group G cooperates on the tile; every
+// range function ends with a group barrier.  Indices are 32-bit (transforms
+// of at most 2^30 points).  One butterfly per thread at a time: two in flight
+// (loaded together) measured slower, the larger butterfly code missing in the
+// instruction cache.
+struct Cols {
+    int lgQ, s_lo, q0;
+};
 
+// radix-2 DIF step (half-size 2^lgM rows) over nb = rows * Q / 2 butterflies
 template <int MODE, class G, class V>
-__device__ __forceinline__ void dif2(V *x, int64_t N, int64_t M, const typename Cx<MODE>::Tw *tw,
-                                     int tw_log2, int lgM2) {
-    for (int64_t t = G::rank(); t < N / 2; t += G::size()) {
-        int64_t k = t & (M - 1);
-        int64_t j = ((t - k) << 1) + k;
-        V u = x[j], v = x[j + M];
-        x[j] = cadd(u, v);
-        x[j + M] = twmul<false>(csub(u, v), tw_get<MODE>(tw, tw_log2, k, lgM2));
+__device__ __forceinline__ void dif2c(V *x, int nb, int lgM, Cols c, const typename Cx<MODE>::Tw *tw) {
+    using Tw = typename Cx<MODE>::Tw;
+    const int qm = (1 << c.lgQ) - 1, mm = (1 << lgM) - 1;
+    const Tw *tl = tw + (1 << (lgM + c.s_lo)) + c.q0;
+    const int st = 1 << (lgM + c.lgQ);
+    for (int s = G::rank(); s < nb; s += G::size()) {
+        const int pr = s >> c.lgQ, q = s & qm, tm = pr & mm;
+        V *p = x + ((((pr - tm) << 1) + tm) << c.lgQ) + q;
+        const Tw w = __ldg(tl + (tm << c.s_lo) + q);
+        const V u = p[0], v = p[st];
+        p[0] = cadd(u, v);
+        p[st] = twmul<false>(csub(u, v), w);
     }
 }
+// radix-2 DIT step (half-size 2^lgM rows)
 template <int MODE, class G, class V>
-__device__ __forceinline__ void dit2(V *x, int64_t N, int64_t M, const typename Cx<MODE>::Tw *tw,
-                                     int tw_log2, int lgM2) {
-    for (int64_t t = G::rank(); t < N / 2; t += G::size()) {
-        int64_t k = t & (M - 1);
-        int64_t j = ((t - k) << 1) + k;
-        V u = x[j];
-        V v = twmul<true>(x[j + M], tw_get<MODE>(tw, tw_log2, k, lgM2));
-        x[j] = cadd(u, v);
-        x[j + M] = csub(u, v);
-    }
-}
-// two DIF stages (half-sizes M and M/2) as one radix-4 pass, M >= 2
-template <int MODE, class G, class V>
-__device__ __forceinline__ void dif4(V *x, int64_t N, int64_t M, const typename Cx<MODE>::Tw *tw,
-                                     int tw_log2, int lgM2) {
-    const int64_t h = M >> 1;
-    for (int64_t t = G::rank(); t < N / 4; t += G::size()) {
-        int64_t k = t & (h - 1);
-        int64_t j = ((t - k) << 2) + k;
-        V a0 = x[j], a1 = x[j + h], a2 = x[j + M], a3 = x[j + M + h];
-        auto w1 = tw_get<MODE>(tw, tw_log2, k, lgM2);       // e^{-2 pi i k/(2M)}
-        auto w2 = tw_get<MODE>(tw, tw_log2, k, lgM2 - 1);   // e^{-2 pi i k/M}
-        V b0 = cadd(a0, a2), b2 = twmul<false>(csub(a0, a2), w1);
-        V b1 = cadd(a1, a3), b3 = cmul_mi(twmul<false>(csub(a1, a3), w1));
-        x[j] = cadd(b0, b1);
-        x[j + h] = twmul<false>(csub(b0, b1), w2);
-        x[j + M] = cadd(b2, b3);
-        x[j + M + h] = twmul<false>(csub(b2, b3), w2);
-    }
-}
-// inverse of dif4 (up to the factor 4)
-template <int MODE, class G, class V>
-__device__ __forceinline__ void dit4(V *x, int64_t N, int64_t M, const typename Cx<MODE>::Tw *tw,
-                                     int tw_log2, int lgM2) {
-    const int64_t h = M >> 1;
-    for (int64_t t = G::rank(); t < N / 4; t += G::size()) {
-        int64_t k = t & (h - 1);
-        int64_t j = ((t - k) << 2) + k;
-        V c0 = x[j], c1 = x[j + h], c2 = x[j + M], c3 = x[j + M + h];
-        auto w1 = tw_get<MODE>(tw, tw_log2, k, lgM2);
-        auto w2 = tw_get<MODE>(tw, tw_log2, k, lgM2 - 1);
-        V t1 = twmul<true>(c1, w2);
-        V b0 = cadd(c0, t1), b1 = csub(c0, t1);
-        V t3 = twmul<true>(c3, w2);
-        V b2 = cadd(c2, t3), b3 = csub(c2, t3);
-        V t2 = twmul<true>(b2, w1);
-        x[j] = cadd(b0, t2);
-        x[j + M] = csub(b0, t2);
-        V t4 = cmul_pi(twmul<true>(b3, w1));
-        x[j + h] = cadd(b1, t4);
-        x[j + M + h] = csub(b1, t4);
+__device__ __forceinline__ void dit2c(V *x, int nb, int lgM, Cols c, const typename Cx<MODE>::Tw *tw) {
+    using Tw = typename Cx<MODE>::Tw;
+    const int qm = (1 << c.lgQ) - 1, mm = (1 << lgM) - 1;
+    const Tw *tl = tw + (1 << (lgM + c.s_lo)) + c.q0;
+    const int st = 1 << (lgM + c.lgQ);
+    for (int s = G::rank(); s < nb; s += G::size()) {
+        const int pr = s >> c.lgQ, q = s & qm, tm = pr & mm;
+        V *p = x + ((((pr - tm) << 1) + tm) << c.lgQ) + q;
+        const Tw w = __ldg(tl + (tm << c.s_lo) + q);
+        const V u = p[0], v = twmul<true>(p[st], w);
+        p[0] = cadd(u, v);
+        p[st] = csub(u, v);
     }
 }
 
-// Forward DIF stages with half-sizes from 2^lgMhi down to 2^lgMlo, with a group
-// barrier after each pass.
+// one radix-4 butterfly: its four values (rows t, t + h, t + M, t + M + h)
+// and its two twiddles (levels lgM + s_lo + 1 and lgM + s_lo)
+template <int MODE, class V>
+struct Bf4 {
+    V *p;
+    V a0, a1, a2, a3;
+    typename Cx<MODE>::Tw w1, w2;
+};
+template <int MODE, class V>
+__device__ __forceinline__ Bf4<MODE, V> bf4_load(V *x, int s, int lgM, Cols c, int hs,
+                                                const typename Cx<MODE>::Tw *t1,
+                                                const typename Cx<MODE>::Tw *t2) {
+    Bf4<MODE, V> b;
+    const int qm = (1 << c.lgQ) - 1, hm = (1 << (lgM - 1)) - 1;
+    const int pr = s >> c.lgQ, q = s & qm, tm = pr & hm;
+    b.p = x + ((((pr - tm) << 2) + tm) << c.lgQ) + q;
+    const int k = (tm << c.s_lo) + q;
+    b.w1 = __ldg(t1 + k);
+    b.w2 = __ldg(t2 + k);
+    b.a0 = b.p[0];
+    b.a1 = b.p[hs];
+    b.a2 = b.p[2 * hs];
+    b.a3 = b.p[3 * hs];
+    return b;
+}
+// two DIF stages (half-sizes M and M/2) as one radix-4 butterfly
+template <int MODE, class V>
+__device__ __forceinline__ void bf4_dif(const Bf4<MODE, V> &b, int hs) {
+    const V b0 = cadd(b.a0, b.a2), b2 = twmul<false>(csub(b.a0, b.a2), b.w1);
+    const V b1 = cadd(b.a1, b.a3), b3 = cmul_mi(twmul<false>(csub(b.a1, b.a3), b.w1));
+    b.p[0] = cadd(b0, b1);
+    b.p[hs] = twmul<false>(csub(b0, b1), b.w2);
+    b.p[2 * hs] = cadd(b2, b3);
+    b.p[3 * hs] = twmul<false>(csub(b2, b3), b.w2);
+}
+// its inverse (DIT, half-sizes M/2 then M; up to the factor 4)
+template <int MODE, class V>
+__device__ __forceinline__ void bf4_dit(const Bf4<MODE, V> &b, int hs) {
+    const V t1 = twmul<true>(b.a1, b.w2);
+    const V b0 = cadd(b.a0, t1), b1 = csub(b.a0, t1);
+    const V t3 = twmul<true>(b.a3, b.w2);
+    const V b2 = cadd(b.a2, t3), b3 = csub(b.a2, t3);
+    const V t2 = twmul<true>(b2, b.w1);
+    b.p[0] = cadd(b0, t2);
+    b.p[2 * hs] = csub(b0, t2);
+    const V t4 = cmul_pi(twmul<true>(b3, b.w1));
+    b.p[hs] = cadd(b1, t4);
+    b.p[3 * hs] = csub(b1, t4);
+}
+// radix-4 step over nb = rows * Q / 4 butterflies, M = 2^lgM >= 2 rows
+template <int MODE, class G, bool DIF, class V>
+__device__ __forceinline__ void step4c(V *x, int nb, int lgM, Cols c, const typename Cx<MODE>::Tw *tw) {
+    using Tw = typename Cx<MODE>::Tw;
+    const Tw *t1 = tw + (1 << (lgM + c.s_lo)) + c.q0;
+    const Tw *t2 = tw + (1 << (lgM - 1 + c.s_lo)) + c.q0;
+    const int hs = 1 << (lgM - 1 + c.lgQ);
+    for (int s = G::rank(); s < nb; s += G::size()) {
+        const Bf4<MODE, V> A = bf4_load<MODE>(x, s, lgM, c, hs, t1, t2);
+        if (DIF) bf4_dif(A, hs);
+        else bf4_dit(A, hs);
+    }
+}
+
+// Forward DIF stages with half-sizes from 2^lgMhi down to 2^lgMlo rows on a
+// tile of 2^lgR rows, a group barrier after each pass.  The range functions
+// are kept out of line: every transform of a mode then runs one copy of the
+// butterfly code, which with the walker's base cases must stay inside the
+// SM's instruction cache (inlined at each call site, instruction fetch became
+// the largest stall of the pricing kernel).
 template <int MODE, class G, class V>
-__device__ void dif_range(V *x, int64_t N, int lgMhi, int lgMlo, const typename Cx<MODE>::Tw *tw,
-                          int tw_log2) {
+__device__ __noinline__ void dif_cols(V *x, int lgR, int lgMhi, int lgMlo, Cols c, const typename Cx<MODE>::Tw *tw) {
     int lg = lgMhi;
     if (((lgMhi - lgMlo + 1) & 1) != 0) {   // odd number of stages: one radix-2 first
-        dif2<MODE, G>(x, N, (int64_t)1 << lg, tw, tw_log2, lg + 1);
+        dif2c<MODE, G>(x, 1 << (lgR + c.lgQ - 1), lg, c, tw);
         G::sync();
         lg--;
     }
     for (; lg > lgMlo; lg -= 2) {
-        dif4<MODE, G>(x, N, (int64_t)1 << lg, tw, tw_log2, lg + 1);
+        step4c<MODE, G, true>(x, 1 << (lgR + c.lgQ - 2), lg, c, tw);
         G::sync();
     }
 }
-// Inverse DIT stages with half-sizes from 2^lgMlo up to 2^lgMhi.
+// Inverse DIT stages with half-sizes from 2^lgMlo up to 2^lgMhi rows.
 template <int MODE, class G, class V>
-__device__ void dit_range(V *x, int64_t N, int lgMlo, int lgMhi, const typename Cx<MODE>::Tw *tw,
-                          int tw_log2) {
+__device__ __noinline__ void dit_cols(V *x, int lgR, int lgMlo, int lgMhi, Cols c, const typename Cx<MODE>::Tw *tw) {
     int lg = lgMlo;
     const int nst = lgMhi - lgMlo + 1;
-    const int pairs = nst / 2;
-    for (int p = 0; p < pairs; p++, lg += 2) {
-        dit4<MODE, G>(x, N, (int64_t)1 << (lg + 1), tw, tw_log2, lg + 2);
+    for (int p = 0; p < nst / 2; p++, lg += 2) {
+        step4c<MODE, G, false>(x, 1 << (lgR + c.lgQ - 2), lg + 1, c, tw);
         G::sync();
     }
     if (nst & 1) {
-        dit2<MODE, G>(x, N, (int64_t)1 << lg, tw, tw_log2, lg + 1);
+        dit2c<MODE, G>(x, 1 << (lgR + c.lgQ - 1), lg, c, tw);
         G::sync();
     }
+}
+// Whole transforms of a plain tile of 2^lgN points.
+template <int MODE, class G, class V>
+__device__ void dif_all(V *x, int lgN, const typename Cx<MODE>::Tw *tw) {
+    dif_cols<MODE, G>(x, lgN, lgN - 1, 0, Cols{0, 0, 0}, tw);
+}
+template <int MODE, class G, class V>
+__device__ void dit_all(V *x, int lgN, const typename Cx<MODE>::Tw *tw) {
+    dit_cols<MODE, G>(x, lgN, 0, lgN - 1, Cols{0, 0, 0}, tw);
 }
 
 // ------------------------------------------------- value conversions by mode
