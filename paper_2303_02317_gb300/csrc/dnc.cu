@@ -1001,8 +1001,13 @@ struct Walker {
             const int t1 = pt;
             pt = cand(bp);               // and of row k + 1 for the next row
             pre = (pt >= 0) ? ext[slot(k + 1, pt)] : A::zero();
+            // registers wholly right of the previous divider hold no cell that
+            // can be red in this row (the divider does not move right); they
+            // keep their values, which the stencil of the last active
+            // register may read (exercise values refreshed below)
 #pragma unroll
             for (int r = 0; r < R; r++) {
+                if (r > (bp >> 5)) continue;
                 const T nx = (r + 1 < R) ? val[(r + 1) % R] : A::zero();
                 const T n1 = A::shfl(lane == 0 ? nx : val[r], (lane + 1) & 31);
                 if (D == 2) {
@@ -1131,8 +1136,16 @@ struct Walker {
             p1 = ld(fp - 1);
             p2 = ld(nr);
             T prev = A::zero();
+            // only registers that hold the test cell fp or red cells (fp .. nr)
+            // are stepped: cells left of fp are green and keep their exercise
+            // values, cells right of nr are outside the row
+            const int r_lo = (int)((fp - lo) >> 5), r_hi = (int)((nr - lo) >> 5);
 #pragma unroll
             for (int r = 0; r < R; r++) {
+                if (r < r_lo || r > r_hi) {
+                    prev = val[r];
+                    continue;
+                }
                 const int64_t x = lo + lane + 32 * r;
                 const T nx = (r + 1 < R) ? val[(r + 1) % R] : A::zero();
                 const T vl = A::shfl(lane == 31 ? prev : val[r], (lane + 31) & 31);
