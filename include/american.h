@@ -125,7 +125,7 @@ typedef struct aop_request {
 
 typedef struct aop_options {
     int32_t method;     /* aop_method */
-    int32_t base_case;  /* D&C base-case height in rows; 0 = tuned default */
+    int32_t base_case;  /* D&C base-case height in rows (2 .. 64, clamped); 0 = tuned default */
     int32_t flags;      /* AOP_FLAG_* bits, 0 for none */
     int32_t ctas_per_sm; /* D&C: options in flight per SM; 0 = as many as fit */
 } aop_options;
@@ -315,13 +315,15 @@ aop_status aop_server_info(const aop_server *srv, int64_t *slots, int64_t *publi
 aop_status aop_server_destroy(aop_server *srv);
 
 /* Autotuner for the divide-and-conquer methods (no counterpart in the paper,
- * which fixes its base case by hand): prices the n host requests once per
- * schedule -- base-case height in {16, 32, 64} x options in flight per SM in
- * {1, 2, 3, 4} -- timing each second run with CUDA events, and keeps the
- * fastest schedule as this context's default for `method` (used where
- * aop_options.base_case or ctas_per_sm is 0).  best_out (nullable) receives
- * it.  Costs 24 batch calls: pass a sample of the workload.  AOP_EINVAL for
- * the plain stencil or a bad method. */
+ * which fixes its base case by hand): prices the n host requests twice per
+ * schedule -- base-case height in {16, 31, 32, 47, 63, 64} x options in
+ * flight per SM in {1, 2, 3, 4}, skipping counts the kernel's registers and
+ * shared memory cannot hold -- timing each second run with CUDA events, and
+ * keeps the fastest schedule as this context's default for `method` (used
+ * where aop_options.base_case or ctas_per_sm is 0).  best_out (nullable)
+ * receives it.  Costs up to 48 batch calls: pass a sample of the workload, or
+ * the workload itself when it is priced repeatedly.  AOP_EINVAL for the plain
+ * stencil or a bad method. */
 aop_status aop_ctx_autotune(aop_ctx *ctx, int64_t n, const aop_request *reqs, int32_t method,
                             aop_options *best_out);
 

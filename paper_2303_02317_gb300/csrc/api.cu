@@ -118,11 +118,9 @@ int resolve_base_case(const aop_ctx *c, const aop_options *opt) {
     int b = kDefaultBaseCase;
     if (opt && opt->base_case > 0) b = opt->base_case;
     else if (c && m >= 0 && m < 4 && c->tuned_B[m] > 0) b = c->tuned_B[m];
-    int p = 1;
-    while (p < b) p <<= 1;   // power of two
-    if (p < 2) p = 2;
-    if (p > 64) p = 64;
-    return p;
+    if (b < 2) b = 2;
+    if (b > 64) b = 64;
+    return b;
 }
 
 // Core of every batch: d_reqs etc. on the device, T_max known.
@@ -528,14 +526,19 @@ aop_status aop_ctx_get_option_times(aop_ctx *c, int64_t n, int64_t *ns_out) {
 aop_status aop_ctx_autotune(aop_ctx *c, int64_t n, const aop_request *reqs, int32_t method,
                             aop_options *best_out) {
     if (!c || n <= 0 || !reqs || method < 0 || method > 3 || method == AOP_STENCIL_FP64) return AOP_EINVAL;
-    static const int kB[] = {16, 32, 64};
+    // heights 2^k - 1 fit a binomial strip (B + 1 cells) or a trinomial one
+    // (2B + 2 cells) into whole registers of 32 cells
+    static const int kB[] = {16, 31, 32, 47, 63, 64};
     static const int kCap[] = {1, 2, 3, 4};
+    int64_t T_max = 1;
+    for (int64_t i = 0; i < n; i++) T_max = std::max<int64_t>(T_max, reqs[i].T);
     std::vector<double> prices((size_t)n);
     std::vector<aop_status> status((size_t)n);
     float best = -1.f;
     int bB = 0, bCap = 0;
     for (int B : kB) {
         for (int cap : kCap) {
+            if (cap > 1 && cap > dnc_max_per_sm(method, T_max, B)) continue;   // same as fewer
             aop_options o{method, B, 0, cap};
             float ms = 0.f;
             for (int rep = 0; rep < 2; rep++) {   // the first run sizes the workspace

@@ -48,7 +48,8 @@ namespace aop {
 namespace {
 
 // CTA shape: one walker warp plus three worker warps.  Workers below `big`
-// may take multi-pass transforms (each owns a global scratch area).  Seven
+// may take multi-pass transforms (each owns a global scratch area; all three
+// do: a long advance never waits for one of two scratch owners).  Seven
 // workers per option (two options per SM) lost to this shape in the
 // doubled-FP32 mode: shorter waits, but slower base cases.  min_ctas sets the
 // register budget: 128 a thread for four options per SM (FP32-split), 255 for
@@ -58,7 +59,7 @@ template <int MODE> struct Shape {
     static constexpr int warps = 4;
     static constexpr int threads = 32 * warps;
     static constexpr int workers = warps - 1;
-    static constexpr int big = 2;
+    static constexpr int big = 3;
     static constexpr int min_ctas = (MODE == 1) ? 4 : 2;
 };
 inline int shape_workers(int) { return Shape<0>::workers; }
@@ -142,7 +143,7 @@ struct Task {
 struct DncArgs {
     const Params *params;
     int64_t n;
-    int B;                 // base-case height (power of two)
+    int B;                 // base-case height (2 .. 64 rows)
     int lg_tile;           // log2 of a worker's shared-memory transform tile
     int lg_block;          // log2 of the block-level tile (linear advance entry points)
     int64_t W_max;         // widest row (doubles)
@@ -220,7 +221,7 @@ struct Shared {
     SpecEntry spec[kSpecSlots];
     int spec_n;
     int spec_lock;
-    // direct index of the entries with g a power of two: entry + 1 (0 = none)
+    // direct index of the entries with g = Bodd * 2^k: entry + 1 (0 = none)
     volatile int16_t spec_map[kSpecLg][kSpecLg];
     long long arena_used;
     int opt;
@@ -452,10 +453,13 @@ struct Cta {
     // (arena exhausted).  Called by every thread of the group G.
     template <class G>
     __device__ const Sp *spectrum(int64_t g, int lgN, int &mc_out, ConvScale &cs) {
-        // fast path: a ready entry found through the direct index, no lock
-        const bool pow2 = g > 0 && (g & (g - 1)) == 0 && lgN < kSpecLg;
-        const int lgg = pow2 ? 63 - __clzll((unsigned long long)g) : 0;
-        if (pow2 && lgg < kSpecLg) {
+        // fast path: a ready entry found through the direct index, no lock.
+        // The recursion's heights are the base-case height times powers of
+        // two, so g = Bodd * 2^lgg with Bodd the odd part of B.
+        const int lgg = g > 0 ? __ffsll((long long)g) - 1 : 0;
+        const bool direct = g > 0 && a.B > 0 && (g >> lgg) == (a.B >> (__ffs(a.B) - 1)) && lgN < kSpecLg &&
+                            lgg < kSpecLg;
+        if (direct) {
             const int v = S.spec_map[lgg][lgN];
             if (v > 0) {
                 SpecEntry &e = S.spec[v - 1];
@@ -494,7 +498,7 @@ struct Cta {
                     S.arena_used += mc + 1;
                     __threadfence_block();
                     S.spec_n = idx + 1;
-                    if (pow2 && lgg < kSpecLg) S.spec_map[lgg][lgN] = (int16_t)(idx + 1);
+                    if (direct) S.spec_map[lgg][lgN] = (int16_t)(idx + 1);
                     build = 1;
                 } else {
                     idx = -1 - mc;   // no room: evaluate on the fly
@@ -1937,6 +1941,13 @@ int dnc_per_sm(int method, int64_t n, size_t smem, int cap, int device) {
     const int64_t share = (n + sms - 1) / sms;
     if (share >= 1 && share < per_sm) per_sm = (int)share;
     return std::max(1, per_sm);
+}
+
+// Options in flight per SM that the pricing kernel's registers and shared
+// memory allow (the autotuner tries no more).
+int dnc_max_per_sm(int method, int64_t T_max, int base_case) {
+    Layout L = make_layout(method, T_max, base_case, shape_big(method));
+    return ctas_per_sm(method, L.smem);
 }
 
 // One CTA per option in flight, at most n.

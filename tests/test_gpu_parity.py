@@ -76,15 +76,17 @@ def test_random_small(ctx, method):
 
 
 @pytest.mark.parametrize("method", [aop.FFT_FP64, aop.FFT_FP32SPLIT, aop.FFT_DF32], ids=["fft64", "fft32", "df32"])
-@pytest.mark.parametrize("B", [2, 8, 32, 64])
+@pytest.mark.parametrize("B", [2, 8, 31, 32, 47, 63, 64])
 def test_base_case_heights(ctx, method, B):
-    """The trapezoid cut does not change the result (any base-case height)."""
+    """The trapezoid cut does not change the result (any base-case height,
+    powers of two or not: the recursion's heights are B times powers of two)."""
     for r in wl.random_small(9, seed=100 + B, T_range=(200, 1500)):
         _check(r, method, base_case=B)
 
 
 @pytest.mark.parametrize("method", [aop.FFT_FP64, aop.FFT_FP32SPLIT, aop.FFT_DF32], ids=["fft64", "fft32", "df32"])
-def test_wide_rows_at_the_largest_base_case(ctx, method):
+@pytest.mark.parametrize("B", [63, 64])
+def test_wide_rows_at_the_largest_base_case(ctx, method, B):
     """Whole rows red (no yield) with the largest base case: the chain's last
     trapezoids are as wide as the lattice rows (up to 2 x 175 cells), wider
     than one base case holds, and must be cut further."""
@@ -93,7 +95,7 @@ def test_wide_rows_at_the_largest_base_case(ctx, method):
                   wl.Request(1, 120.0, 100.0, 0.08, 1e-4, 0.2, 2.0, T, 0.0, 1),
                   wl.Request(0, 100.0, 100.0, 0.05, 0.0, 0.3, 1.0, T),
                   wl.Request(2, 100.0, 100.0, 0.05, 0.0, 0.3, 1.0, T)):
-            _check(r, method, base_case=64)
+            _check(r, method, base_case=B)
 
 
 @pytest.mark.parametrize("method", METHODS, ids=[MNAME[m] for m in METHODS])

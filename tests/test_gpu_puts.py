@@ -87,7 +87,7 @@ def test_bsm_put_with_yield_random(ctx, method):
 
 
 @pytest.mark.parametrize("method", [aop.FFT_FP64, aop.FFT_FP32SPLIT, aop.FFT_DF32], ids=["fft64", "fft32", "df32"])
-@pytest.mark.parametrize("B", [2, 16, 64])
+@pytest.mark.parametrize("B", [2, 16, 31, 63, 64])
 def test_put_base_case_heights(ctx, method, B):
     for r in wl.random_small(9, seed=41 + B, T_range=(100, 1500), models=(BP, TP, 2), bsm_yield=True):
         _check(r, method, base_case=B)
