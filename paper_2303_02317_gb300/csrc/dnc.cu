@@ -960,11 +960,10 @@ struct Walker {
     // lane, so each lane loads its one value a row ahead and the per-row chain
     // is shuffle -> stencil -> test.  A is the arithmetic (FP64, or doubled
     // FP32 on the FP32 pipe).
-    template <int R, class A>
+    template <int R, int D, class A>
     __device__ int64_t call_rows(int64_t i0, int64_t c0, int64_t b, int64_t h, const Buf &in, const Buf &out,
                                  int64_t klo, int64_t khi) {
         using T = typename A::T;
-        const int D = P.D;
         const typename A::Wts w = A::weights(S);
         const T *ext = (const T *)exw;
         // 32-bit arithmetic relative to (i0, c0) inside the base case: column
@@ -1005,13 +1004,10 @@ struct Walker {
             const int t1 = pt;
             pt = cand(bp);               // and of row k + 1 for the next row
             pre = (pt >= 0) ? ext[slot(k + 1, pt)] : A::zero();
-            // registers wholly right of the previous divider hold no cell that
-            // can be red in this row (the divider does not move right); they
-            // keep their values, which the stencil of the last active
-            // register may read (exercise values refreshed below)
+            // straight-line over the registers (R fits the window), so that
+            // their shuffles and sums overlap
 #pragma unroll
             for (int r = 0; r < R; r++) {
-                if (r > (bp >> 5)) continue;
                 const T nx = (r + 1 < R) ? val[(r + 1) % R] : A::zero();
                 const T n1 = A::shfl(lane == 0 ? nx : val[r], (lane + 1) & 31);
                 if (D == 2) {
@@ -1063,11 +1059,18 @@ struct Walker {
         A::fill(S, (typename A::T *)exw, klo, khi, lane);
         __syncwarp();
         if (lane == 0) cnt.fill_cyc += clock64() - fc0;
-        if (need <= 32) return call_rows<1, A>(i0, c0, b, h, in, out, klo, khi);
-        if (need <= 64) return call_rows<2, A>(i0, c0, b, h, in, out, klo, khi);
-        if (need <= 128) return call_rows<4, A>(i0, c0, b, h, in, out, klo, khi);
-        if (need <= 256) return call_rows<8, A>(i0, c0, b, h, in, out, klo, khi);
-        return call_rows<9, A>(i0, c0, b, h, in, out, klo, khi);
+        if (P.D == 1) {
+            if (need <= 32) return call_rows<1, 1, A>(i0, c0, b, h, in, out, klo, khi);
+            if (need <= 64) return call_rows<2, 1, A>(i0, c0, b, h, in, out, klo, khi);
+            if (need <= 128) return call_rows<4, 1, A>(i0, c0, b, h, in, out, klo, khi);
+            if (need <= 256) return call_rows<8, 1, A>(i0, c0, b, h, in, out, klo, khi);
+            return call_rows<9, 1, A>(i0, c0, b, h, in, out, klo, khi);
+        }
+        if (need <= 32) return call_rows<1, 2, A>(i0, c0, b, h, in, out, klo, khi);
+        if (need <= 64) return call_rows<2, 2, A>(i0, c0, b, h, in, out, klo, khi);
+        if (need <= 128) return call_rows<4, 2, A>(i0, c0, b, h, in, out, klo, khi);
+        if (need <= 256) return call_rows<8, 2, A>(i0, c0, b, h, in, out, klo, khi);
+        return call_rows<9, 2, A>(i0, c0, b, h, in, out, klo, khi);
     }
 
     __device__ int64_t naive_call_body(int64_t i0, int64_t c0, int64_t b, int64_t h, const Buf &in, const Buf &out) {
