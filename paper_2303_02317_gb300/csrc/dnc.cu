@@ -625,6 +625,44 @@ struct Cta {
         G::sync();
     }
 
+    // tile[s] times the kernel power of bin brev(base + s), s < count, for the
+    // group G.  Each thread loads the spectrum entries of four of its bins
+    // before it multiplies any, so that their global-memory latencies overlap
+    // (one at a time, they serialised the product).  Out of line: one copy for
+    // the single-tile and the multi-pass transforms.
+    template <class G>
+    __device__ __noinline__ void product(V *tile, int count, uint32_t base, int lgN, const Sp *sp, int mc,
+                                         int64_t g) {
+        const uint32_t N = 1u << lgN;
+        if (!sp) {
+            for (int s = G::rank(); s < count; s += G::size())
+                tile[s] = mul_bin(tile[s], sp, mc, fft::brev_n(base + (uint32_t)s, lgN), N, g, lgN);
+            G::sync();
+            return;
+        }
+        constexpr int kB = 4;
+        for (int s0 = G::rank(); s0 < count; s0 += kB * G::size()) {
+            Sp w[kB];
+            uint32_t m[kB];
+#pragma unroll
+            for (int j = 0; j < kB; j++) {
+                const int s = s0 + j * G::size();
+                m[j] = fft::brev_n(base + (uint32_t)s, lgN);
+                const uint32_t mm = (m[j] <= N / 2) ? m[j] : N - m[j];
+                if (s < count && (int)mm <= mc) w[j] = sp[mm];   // written by this CTA: plain (coherent) load
+                else m[j] = 0xffffffffu;            // outside the band: zero
+            }
+#pragma unroll
+            for (int j = 0; j < kB; j++) {
+                const int s = s0 + j * G::size();
+                if (s >= count) break;
+                if (m[j] == 0xffffffffu) tile[s] = fft::czero<V>();
+                else tile[s] = (m[j] <= N / 2) ? fft::twmul<false>(tile[s], w[j]) : fft::twmul<true>(tile[s], w[j]);
+            }
+        }
+        G::sync();
+    }
+
     __device__ V mul_bin(V z, const Sp *sp, int mc, uint32_t m, uint32_t N, int64_t g, int lgN) const {
         if (sp) return fft::spec_mul<MODE>(z, sp, mc, m, N);
         uint32_t mm = (m <= N / 2) ? m : N - m;
@@ -710,9 +748,7 @@ struct Cta {
             stage_input<G, ST>(tile, (int)N, [](int s) { return s; }, in, x_lo, W);
             const long long q2 = clock64();
             fft::dif_all<MODE, G>(tile, lgN, T);
-            for (int p = G::rank(); p < (int)N; p += G::size())
-                tile[p] = mul_bin(tile[p], sp, mc, fft::brev_n((uint32_t)p, lgN), (uint32_t)N, g, lgN);
-            G::sync();
+            product<G>(tile, (int)N, 0u, lgN, sp, mc, g);
             const long long q3 = clock64();
             fft::dit_all<MODE, G>(tile, lgN, T);
             const long long q4 = clock64();
@@ -752,9 +788,7 @@ struct Cta {
             V *blk = scr + (int64_t)b * N2;
             stage_scratch<G>(tile, N2, [](int s) { return s; }, blk);
             fft::dif_all<MODE, G>(tile, lg_tile, T);
-            for (int s = G::rank(); s < N2; s += G::size())
-                tile[s] = mul_bin(tile[s], sp, mc, fft::brev_n((uint32_t)(b * N2 + s), lgN), (uint32_t)N, g, lgN);
-            G::sync();
+            product<G>(tile, N2, (uint32_t)(b * N2), lgN, sp, mc, g);
             fft::dit_all<MODE, G>(tile, lg_tile, T);
             for (int s = G::rank(); s < N2; s += G::size()) blk[s] = tile[s];
             G::sync();
