@@ -383,7 +383,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--stencil-sample", type=int, default=4)
     ap.add_argument("--small", action="store_true",
-                    help="reduced book (T=2^15, 152 options) for profiler captures")
+                    help="reduced book (T=2^15, 304 options: two per SM) for profiler captures")
     ap.add_argument("--configs", action="store_true",
                     help="single-option latency tables of the fixed configurations (C1-C3) instead of the book")
     ap.add_argument("--config-runs", type=int, default=10)
@@ -411,8 +411,8 @@ def main():
     global T_BENCH, N_BINOMIAL, N_TRINOMIAL, WORKLOAD
     if args.small:
         # reduced book of the same kernel for profiler captures
-        T_BENCH, N_BINOMIAL, N_TRINOMIAL = 1 << 15, 76, 76
-        WORKLOAD = "precision_sweep_T32768_76binomial_76trinomial"
+        T_BENCH, N_BINOMIAL, N_TRINOMIAL = 1 << 15, 152, 152
+        WORKLOAD = "precision_sweep_T32768_152binomial_152trinomial"
     reqs = wl.precision_sweep(T=T_BENCH, n_binomial=N_BINOMIAL, n_trinomial=N_TRINOMIAL)
     n = len(reqs)
     arr = aop.requests_array(reqs)

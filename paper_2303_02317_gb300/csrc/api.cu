@@ -64,7 +64,7 @@ struct aop_server {
 
 namespace {
 
-constexpr int kDefaultBaseCase = 32;
+constexpr int kDefaultBaseCase = 63;    // the tuner's usual pick: strips fill whole registers
 
 aop_status cuda_fail(cudaError_t e) {
     return e == cudaSuccess ? AOP_OK : (e == cudaErrorMemoryAllocation ? AOP_ENOMEM : AOP_ECUDA);

@@ -221,6 +221,7 @@ struct Shared {
     SpecEntry spec[kSpecSlots];
     int spec_n;
     int spec_lock;
+    volatile unsigned posted;   // bit d: task slot d holds a posted task (idle workers scan this word)
     // direct index of the entries with g = Bodd * 2^k: entry + 1 (0 = none)
     volatile int16_t spec_map[kSpecLg][kSpecLg];
     long long arena_used;
@@ -241,6 +242,8 @@ struct Shared {
     float2 wdf[3];
     float2 kdf;
 };
+
+static_assert(kMaxDepth <= 32, "task slots are bits of Shared::posted");
 
 // Tilt tables of the current option (all threads of the block).
 template <int MODE>
@@ -953,6 +956,7 @@ struct Walker {
             t.lgN = lgN < 2 ? 2 : lgN;
             __threadfence_block();
             t.state = TASK_POSTED;
+            atomicOr((unsigned *)&S.posted, 1u << d);
         }
         __syncwarp();
     }
@@ -961,8 +965,10 @@ struct Walker {
         if (lane == 0) {
             Task &t = S.tasks[d];
             const uint64_t t0 = gtime();
+            unsigned ns = 16;            // backoff: a long wait polls less often
             while (t.state == TASK_POSTED || t.state == TASK_CLAIMED) {
-                __nanosleep(20);
+                __nanosleep(ns);
+                if (ns < 128) ns <<= 1;
                 if (gtime() - t0 > kWaitNs) { atomicCAS((int *)&S.err, 0, AOP_ETIMEOUT); break; }
             }
             cnt.wait_ns += (long long)(gtime() - t0);
@@ -1711,6 +1717,7 @@ dnc_kernel(const __grid_constant__ DncArgs a)
             S.done = 0;
             S.err = 0;
             for (int d = 0; d < kMaxDepth; d++) S.tasks[d].state = TASK_FREE;
+            S.posted = 0;
         }
         __syncthreads();
         if (S.P.status != AOP_OK) {
@@ -1766,15 +1773,21 @@ dnc_kernel(const __grid_constant__ DncArgs a)
             const int wid = role - 1;
             V *tile = tiles + ((int64_t)wid << a.lg_tile);
             uint64_t idle0 = gtime();
+            unsigned nap = 32;           // idle backoff (ns), reset by each task
             for (;;) {
                 int pick = -1;
                 if (lane == 0) {
                     if (S.done) pick = -2;
                     else {
-                        for (int d = kMaxDepth - 1; d >= 0; d--) {
+                        // posted slots from the mask word, deepest first
+                        unsigned m = S.posted;
+                        while (m) {
+                            const int d = 31 - __clz(m);
+                            m &= ~(1u << d);
                             if (S.tasks[d].state != TASK_POSTED) continue;
                             if (wid >= Shape<MODE>::big && S.tasks[d].lgN > a.lg_tile) continue;
                             if (atomicCAS((int *)&S.tasks[d].state, TASK_POSTED, TASK_CLAIMED) == TASK_POSTED) {
+                                atomicAnd((unsigned *)&S.posted, ~(1u << d));
                                 pick = d;
                                 break;
                             }
@@ -1784,7 +1797,8 @@ dnc_kernel(const __grid_constant__ DncArgs a)
                 pick = __shfl_sync(0xffffffffu, pick, 0);
                 if (pick == -2) break;
                 if (pick < 0) {
-                    __nanosleep(64);
+                    __nanosleep(nap);
+                    if (nap < 256) nap <<= 1;
                     if (gtime() - idle0 > kWaitNs) {
                         if (lane == 0) atomicCAS((int *)&S.err, 0, AOP_ETIMEOUT);
                         break;
@@ -1801,6 +1815,7 @@ dnc_kernel(const __grid_constant__ DncArgs a)
                 __syncwarp();
                 if (lane == 0) S.tasks[pick].state = TASK_DONE;
                 idle0 = gtime();
+                nap = 32;
                 if (lane == 0) {
                     cnt.busy_ns += (long long)(idle0 - tb);
                     cnt.hist_n[min(lgN, 23)]++;
