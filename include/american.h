@@ -80,12 +80,16 @@ typedef enum {
     AOP_STENCIL_FP64 = 2,   /* plain Theta(T^2) backward induction (Fig. 1 loop
                                and its trinomial / finite-difference analogues),
                                temporally blocked, FP64 */
-    AOP_FFT_DF32 = 3        /* trapezoidal D&C, FFT convolutions in double-float
+    AOP_FFT_DF32 = 3,       /* trapezoidal D&C, FFT convolutions in double-float
                                arithmetic (pairs of FP32 numbers, ~48-bit
                                significands, on the FP32 pipe); base cases and
                                boundary tests likewise (in FP64 where a
                                window's prices span more than e^80); root in
                                FP64 */
+    AOP_STENCIL_DF32 = 4    /* the plain loop of AOP_STENCIL_FP64 in double-float
+                               arithmetic (~2^-48 relative rounding per row;
+                               exercise values clamped to +-1e30, far outside
+                               the walk's reach from the root) */
 } aop_method;
 
 typedef enum {
@@ -210,7 +214,7 @@ aop_status price_american_batch(aop_ctx *ctx, int64_t n, const aop_request *reqs
                                 aop_status *status, void *stream);
 
 /* Price and sensitivities of n options (host arrays, as price_american_batch)
- * with a divide-and-conquer method (AOP_FFT_*; AOP_STENCIL_FP64 gives
+ * with a divide-and-conquer method (AOP_FFT_*; the AOP_STENCIL_* methods give
  * AOP_EINVAL).  greeks (host, double[3n]) receives per option delta (dV/dS0),
  * gamma (d2V/dS0^2) and theta (dV/dt, per year, t calendar time) from the
  * lattice rows next to the root, the standard lattice estimates:

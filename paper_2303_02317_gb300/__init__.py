@@ -10,7 +10,7 @@ convolutions and FP64 base cases), FFT_FP32SPLIT (the same with FP32
 hi/lo-split convolutions), FFT_DF32 (doubled-FP32 convolutions; both FP32
 methods evaluate base cases in doubled FP32, in FP64 where the exercise
 values span too wide a range), STENCIL_FP64 (plain Theta(T^2) backward
-induction).
+induction) and STENCIL_DF32 (the same loop in doubled FP32).
 """
 from __future__ import annotations
 
@@ -29,7 +29,7 @@ LIB_PATH = os.path.join(HERE, "libamerican.so")
 HEADER = os.path.join(os.path.dirname(HERE), "include", "american.h")
 
 BINOMIAL_CALL, TRINOMIAL_CALL, BSM_PUT, BINOMIAL_PUT, TRINOMIAL_PUT = 0, 1, 2, 3, 4
-FFT_FP64, FFT_FP32SPLIT, STENCIL_FP64, FFT_DF32 = 0, 1, 2, 3
+FFT_FP64, FFT_FP32SPLIT, STENCIL_FP64, FFT_DF32, STENCIL_DF32 = 0, 1, 2, 3, 4
 TRI_BOYLE, TRI_PAPER = 0, 1
 BOUNDARY_NONE_PUT = -(2 ** 31)
 MAX_T = 1 << 20

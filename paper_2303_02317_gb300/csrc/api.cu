@@ -145,19 +145,21 @@ aop_status run_batch(aop_ctx *c, int64_t n, const aop_request *d_reqs, const aop
                      double *d_greeks = nullptr)
 {
     const int method = opt ? opt->method : AOP_FFT_FP64;
-    if (method < 0 || method > 3) return AOP_EINVAL;
-    if (d_greeks && method == AOP_STENCIL_FP64) return AOP_EINVAL;
+    if (method < 0 || method > 4) return AOP_EINVAL;
+    const bool stencil = (method == AOP_STENCIL_FP64 || method == AOP_STENCIL_DF32);
+    if (d_greeks && stencil) return AOP_EINVAL;
     if (c->serving) return AOP_EBUSY;
     if (n == 0 || T_max < 1) return AOP_OK;
     const int B = resolve_base_case(c, opt);
     CK(cudaMemsetAsync(c->d_stats, 0, sizeof(aop_stats), s));
     CK(cudaMemsetAsync(c->d_err, 0, sizeof(int), s));
-    if (method == AOP_STENCIL_FP64) {
+    if (stencil) {
         size_t need = stencil_workspace_bytes(n, T_max);
         aop_status st = ensure(&c->ws, &c->ws_size, need, c->cap);
         if (st) return st;
         CK(cudaEventRecord(c->ev0, s));
-        CK(run_stencil(n, d_params, T_max, c->ws, d_prices, d_status, d_bnd, d_bnd_off, c->d_stats, s));
+        CK(run_stencil(n, d_params, T_max, c->ws, d_prices, d_status, d_bnd, d_bnd_off, c->d_stats, s,
+                       method == AOP_STENCIL_DF32));
         CK(cudaEventRecord(c->ev1, s));
     } else {
         int64_t W = 2 * T_max + 1;
@@ -525,7 +527,7 @@ aop_status aop_ctx_get_option_times(aop_ctx *c, int64_t n, int64_t *ns_out) {
 
 aop_status aop_ctx_autotune(aop_ctx *c, int64_t n, const aop_request *reqs, int32_t method,
                             aop_options *best_out) {
-    if (!c || n <= 0 || !reqs || method < 0 || method > 3 || method == AOP_STENCIL_FP64) return AOP_EINVAL;
+    if (!c || n <= 0 || !reqs || method < 0 || method > 3 || method == AOP_STENCIL_FP64) return AOP_EINVAL;   // D&C only
     // heights 2^k - 1 fit a binomial strip (B + 1 cells) or a trinomial one
     // (2B + 2 cells) into whole registers of 32 cells
     static const int kB[] = {16, 31, 32, 47, 63, 64};
@@ -598,7 +600,7 @@ aop_status aop_server_create(aop_ctx *c, int64_t capacity, int64_t T_max, const 
                              aop_server **out) {
     if (!c || !out || capacity < 1 || T_max < 1 || T_max > AOP_MAX_T) return AOP_EINVAL;
     const int method = opt ? opt->method : AOP_FFT_FP64;
-    if (method < 0 || method > 3 || method == AOP_STENCIL_FP64) return AOP_EINVAL;
+    if (method < 0 || method > 3 || method == AOP_STENCIL_FP64) return AOP_EINVAL;   // D&C only
     if (c->serving) return AOP_EBUSY;
     CK(cudaSetDevice(c->device));
     aop_server *s = new aop_server;

@@ -856,34 +856,10 @@ struct ArithDF {
     __device__ static T shfl(T v, int src) {
         return make_float2(__shfl_sync(0xffffffffu, v.x, src), __shfl_sync(0xffffffffu, v.y, src));
     }
-    // high products exact through FMA, the low parts and rounding errors of
-    // the non-negative terms summed once, one renormalisation (__fmul_rn
-    // keeps the compiler from fusing a product into the two-sum that follows)
-    __device__ static T dot2(const Wts &w, T a, T b) {
-        const float p0 = __fmul_rn(w.w0.x, a.x), p1 = __fmul_rn(w.w1.x, b.x);
-        float e = fmaf(w.w0.x, a.x, -p0) + fmaf(w.w1.x, b.x, -p1);
-        e = fmaf(w.w0.x, a.y, fmaf(w.w0.y, a.x, e));
-        e = fmaf(w.w1.x, b.y, fmaf(w.w1.y, b.x, e));
-        float s, t;
-        fft::two_sum(p0, p1, s, t);
-        float h, l;
-        fft::fast_two_sum(s, t + e, h, l);
-        return make_float2(h, l);
-    }
-    __device__ static T dot3(const Wts &w, T a, T b, T c) {
-        const float p0 = __fmul_rn(w.w0.x, a.x), p1 = __fmul_rn(w.w1.x, b.x), p2 = __fmul_rn(w.w2.x, c.x);
-        float e = fmaf(w.w0.x, a.x, -p0) + fmaf(w.w1.x, b.x, -p1) + fmaf(w.w2.x, c.x, -p2);
-        e = fmaf(w.w0.x, a.y, fmaf(w.w0.y, a.x, e));
-        e = fmaf(w.w1.x, b.y, fmaf(w.w1.y, b.x, e));
-        e = fmaf(w.w2.x, c.y, fmaf(w.w2.y, c.x, e));
-        float s, t, s2, t2;
-        fft::two_sum(p0, p1, s, t);
-        fft::two_sum(s, p2, s2, t2);
-        float h, l;
-        fft::fast_two_sum(s2, (t + t2) + e, h, l);
-        return make_float2(h, l);
-    }
-    __device__ static bool ge(T a, T b) { return a.x > b.x || (a.x == b.x && a.y >= b.y); }
+    // fused dot products of the stencil (fft.cuh)
+    __device__ static T dot2(const Wts &w, T a, T b) { return fft::df_dot2(w.w0, w.w1, a, b); }
+    __device__ static T dot3(const Wts &w, T a, T b, T c) { return fft::df_dot3(w.w0, w.w1, w.w2, a, b, c); }
+    __device__ static bool ge(T a, T b) { return fft::df_ge(a, b); }
     __device__ static bool pos(T a) { return a.x > 0.f || (a.x == 0.f && a.y > 0.f); }
     __device__ static bool cont_ge(T cont, T ex) { return !pos(ex) || ge(cont, ex); }
     __device__ static bool ex_gt(T ex, T cont) { return pos(ex) && !ge(cont, ex); }

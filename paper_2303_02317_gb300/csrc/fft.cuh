@@ -85,6 +85,42 @@ __device__ __forceinline__ void df_mul(float ah, float al, float bh, float bl, f
     fast_two_sum(p, e, rh, rl);
 }
 
+// w0 a + w1 (+ w2 c) for non-negative doubled-FP32 weights and values (the
+// stencils of the lattices): high products exact through FMA, the low parts and
+// the products' rounding errors summed once, one renormalisation (__fmul_rn keeps
+// the compiler from fusing a product into the two-sum that follows).
+__device__ __forceinline__ float2 df_dot2(float2 w0, float2 w1, float2 a, float2 b) {
+    const float p0 = __fmul_rn(w0.x, a.x), p1 = __fmul_rn(w1.x, b.x);
+    float e = fmaf(w0.x, a.x, -p0) + fmaf(w1.x, b.x, -p1);
+    e = fmaf(w0.x, a.y, fmaf(w0.y, a.x, e));
+    e = fmaf(w1.x, b.y, fmaf(w1.y, b.x, e));
+    float s, t;
+    two_sum(p0, p1, s, t);
+    float h, l;
+    fast_two_sum(s, t + e, h, l);
+    return make_float2(h, l);
+}
+__device__ __forceinline__ float2 df_dot3(float2 w0, float2 w1, float2 w2, float2 a, float2 b, float2 c) {
+    const float p0 = __fmul_rn(w0.x, a.x), p1 = __fmul_rn(w1.x, b.x), p2 = __fmul_rn(w2.x, c.x);
+    float e = fmaf(w0.x, a.x, -p0) + fmaf(w1.x, b.x, -p1) + fmaf(w2.x, c.x, -p2);
+    e = fmaf(w0.x, a.y, fmaf(w0.y, a.x, e));
+    e = fmaf(w1.x, b.y, fmaf(w1.y, b.x, e));
+    e = fmaf(w2.x, c.y, fmaf(w2.y, c.x, e));
+    float s, t, s2, t2;
+    two_sum(p0, p1, s, t);
+    two_sum(s, p2, s2, t2);
+    float h, l;
+    fast_two_sum(s2, (t + t2) + e, h, l);
+    return make_float2(h, l);
+}
+// a >= b for normalised doubled-FP32 values
+__device__ __forceinline__ bool df_ge(float2 a, float2 b) { return a.x > b.x || (a.x == b.x && a.y >= b.y); }
+// the nearest doubled-FP32 value of an FP64 number
+__device__ __forceinline__ float2 df_from(double v) {
+    const float h = (float)v;
+    return make_float2(h, (float)(v - (double)h));
+}
+
 // ------------------------------------------------------------- complex ops
 __device__ __forceinline__ double2 cadd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
 __device__ __forceinline__ double2 csub(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }

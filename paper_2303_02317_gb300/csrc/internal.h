@@ -46,7 +46,7 @@ cudaError_t launch_fill_i32(int32_t *p, int64_t n, int32_t v, cudaStream_t s);
 size_t stencil_workspace_bytes(int64_t n, int64_t T_max);
 cudaError_t run_stencil(int64_t n, const Params *d_params, int64_t T_max, void *ws,
                         double *d_prices, int32_t *d_status, int32_t *d_bnd,
-                        const int64_t *d_bnd_off, aop_stats *d_stats, cudaStream_t s);
+                        const int64_t *d_bnd_off, aop_stats *d_stats, cudaStream_t s, bool df);
 
 // dnc.cu -- trapezoidal divide-and-conquer pricer
 int dnc_max_per_sm(int method, int64_t T_max, int base_case);

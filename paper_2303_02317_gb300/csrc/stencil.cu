@@ -11,10 +11,27 @@
 // kRows on each side for the put) into shared memory, and steps kRows rows
 // there (overlapped tiling: the halo is recomputed by the neighbour tile).
 // The per-row divider is reduced per tile and merged with atomicMax.
+//
+// Two arithmetics (template flag DF): FP64, and doubled FP32 (a cell is an
+// unevaluated pair hi + lo of FP32 numbers in the same 8-byte slot, ~48-bit
+// significands, summed on the FP32 pipe).  On this GPU an FP64 warp
+// instruction occupies a sub-partition's FP64 unit for ~64 cycles, so the
+// doubled-FP32 loop is the faster plain form; its values carry ~2^-48 relative
+// rounding per row.  Doubled-FP32 exercise values are clamped to +-1e30 (FP32
+// range).  The clamp lies at least ln(1e28) = 64 log-price units from any node
+// within e^2 of the spot or strike, many standard deviations of the walk
+// (sigma sqrt(expiry) < 2 for every supported request), so its effect on the
+// root value is below the rounding: the clamped cells only meet the root
+// through transition weights far under 1e-300.  Call cells at the clamp are
+// taken as green (as the D&C does for node prices past its range): they lie far
+// above every early-exercise boundary with a yield, and without one (whole rows
+// red) the reported divider stops below the clamp.
 #include <algorithm>
 #include <cstdio>
+#include <type_traits>
 
 #include "common.cuh"
+#include "fft.cuh"
 #include "internal.h"
 
 namespace aop {
@@ -43,8 +60,18 @@ __device__ inline int64_t remaining_after(int64_t T, int64_t launch) {
     return r < 0 ? 0 : r;
 }
 
+constexpr double kDfClamp = 1e30;
+
+// a cell value as stored by the arithmetic DF (FP64, or the pair hi, lo)
+template <bool DF>
+__device__ __forceinline__ void put_cell(double *p, double v) {
+    if (DF) *(float2 *)p = fft::df_from(fmin(fmax(v, -kDfClamp), kDfClamp));
+    else *p = v;
+}
+
 // Exercise table and the first row (calls: row T; put: row 0), and the divider
 // of that row.  grid: (chunks, n).
+template <bool DF>
 __global__ void stencil_init_kernel(const Params *params, int64_t n, int64_t T_max, double *ws,
                                     int32_t *bnd, const int64_t *bnd_off)
 {
@@ -63,10 +90,10 @@ __global__ void stencil_init_kernel(const Params *params, int64_t n, int64_t T_m
     for (int64_t kp = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; kp <= 2 * T;
          kp += (int64_t)gridDim.x * blockDim.x) {
         double e = exercise(P, E, kp);
-        ex[kp] = e;
+        put_cell<DF>(&ex[kp], e);
         if (P.model == AOP_BSM_PUT) {
             // row 0 holds k in [-T, T] at index k + T = kp; continuation 0
-            row[kp] = e > 0.0 ? e : 0.0;
+            put_cell<DF>(&row[kp], e > 0.0 ? e : 0.0);
             if (e > 0.0) best = max(best, (int)(kp - T));
         } else {
             // row T: column j has k' = 2j (binomial) or j (trinomial)
@@ -75,7 +102,7 @@ __global__ void stencil_init_kernel(const Params *params, int64_t n, int64_t T_m
             if (P.model == AOP_BINOMIAL_CALL) { hit = (kp % 2 == 0); j = kp / 2; }
             else { hit = true; j = kp; }
             if (hit) {
-                row[j] = e > 0.0 ? e : 0.0;
+                put_cell<DF>(&row[j], e > 0.0 ? e : 0.0);
                 if (0.0 >= e) best = max(best, (int)j);
             }
         }
@@ -98,11 +125,15 @@ __global__ void stencil_init_kernel(const Params *params, int64_t n, int64_t T_m
 // One temporal block of up to kRows rows for every option.  grid-stride over
 // tiles; tile -> (option, segment) through per-option tile counts computed in
 // shared memory.
+template <bool DF>
 __global__ void __launch_bounds__(kThreads)
 stencil_block_kernel(const Params *params, int64_t n, int64_t T_max, int64_t launch,
                      double *ws, int32_t *bnd, const int64_t *bnd_off, long long *cells)
 {
-    __shared__ double buf[2][kBuf];
+    using C = typename std::conditional<DF, float2, double>::type;   // one 8-byte cell
+    static_assert(sizeof(C) == sizeof(double), "cells share the FP64 layout");
+    __shared__ double buf_raw[2][kBuf];
+    C (*buf)[kBuf] = (C (*)[kBuf])buf_raw;
     __shared__ int s_bnd[kRows + 1];
     __shared__ int64_t s_tiles_total;
     const StencilOpt L = stencil_layout(T_max);
@@ -144,13 +175,14 @@ stencil_block_kernel(const Params *params, int64_t n, int64_t T_max, int64_t lau
         const int64_t R = remaining_after(T, launch);
         const int Kp = (int)min((int64_t)kRows, R);
         const int64_t Rout = R - Kp;
-        double *ex = ws + o * L.stride;
-        double *rowA = ex + L.W;
-        double *rowB = rowA + L.W;
-        const double *src = (launch % 2 == 0) ? rowA : rowB;
-        double *dst = (launch % 2 == 0) ? rowB : rowA;
+        const C *ex = (const C *)(ws + o * L.stride);
+        C *rowA = (C *)(ws + o * L.stride + L.W);
+        C *rowB = rowA + L.W;
+        const C *src = (launch % 2 == 0) ? rowA : rowB;
+        C *dst = (launch % 2 == 0) ? rowB : rowA;
         const bool put = (P.model == AOP_BSM_PUT);
         const double w0 = P.w[0], w1 = P.w[1], w2 = P.w[2];
+        const float2 v0 = fft::df_from(w0), v1 = fft::df_from(w1), v2 = fft::df_from(w2);
         const int nw = P.nw;
         const int64_t nseg = ((put ? 2 * Rout + 1 : (int64_t)P.D * Rout + 1) + kSeg - 1) / kSeg;
 
@@ -184,26 +216,36 @@ stencil_block_kernel(const Params *params, int64_t n, int64_t T_max, int64_t lau
             int64_t nlo, nhi;
             if (!put) { nlo = lo; nhi = min(hi - P.D, (int64_t)P.D * r); }
             else { nlo = max(lo + 1, -(T - r)); nhi = min(hi - 1, T - r); }
-            const double *pv = buf[cur];
-            double *nv = buf[cur ^ 1];
+            const C *pv = buf[cur];
+            C *nv = buf[cur ^ 1];
             int best = INT32_MIN;
             for (int64_t x = nlo + threadIdx.x; x <= nhi; x += blockDim.x) {
                 const int64_t ix = x - base;
-                double cont;
-                if (!put) {
-                    cont = w0 * pv[ix] + w1 * pv[ix + 1];
-                    if (nw == 3) cont += w2 * pv[ix + 2];
+                C cont;
+                if constexpr (DF) {
+                    if (!put) cont = (nw == 3) ? fft::df_dot3(v0, v1, v2, pv[ix], pv[ix + 1], pv[ix + 2])
+                                               : fft::df_dot2(v0, v1, pv[ix], pv[ix + 1]);
+                    else cont = fft::df_dot3(v0, v1, v2, pv[ix - 1], pv[ix], pv[ix + 1]);
                 } else {
-                    cont = w0 * pv[ix - 1] + w1 * pv[ix] + w2 * pv[ix + 1];
+                    if (!put) {
+                        cont = w0 * pv[ix] + w1 * pv[ix + 1];
+                        if (nw == 3) cont += w2 * pv[ix + 2];
+                    } else {
+                        cont = w0 * pv[ix - 1] + w1 * pv[ix] + w2 * pv[ix + 1];
+                    }
                 }
-                const double e = ex[ex_index(P, r, x)];
+                const C e = ex[ex_index(P, r, x)];
+                bool ge;
+                if constexpr (DF) ge = fft::df_ge(cont, e);
+                else ge = cont >= e;
                 bool take_ex;
                 if (!put) {
-                    const bool red = cont >= e;
+                    bool red = ge;
+                    if constexpr (DF) red = red && e.x < (float)kDfClamp;
                     take_ex = !red;
                     if (red && x >= own_lo && x <= own_hi) best = max(best, (int)x);
                 } else {
-                    take_ex = e > cont;
+                    take_ex = !ge;
                     if (take_ex && x >= own_lo && x <= own_hi) best = max(best, (int)x);
                 }
                 nv[ix] = take_ex ? e : cont;
@@ -234,6 +276,7 @@ stencil_block_kernel(const Params *params, int64_t n, int64_t T_max, int64_t lau
     }
 }
 
+template <bool DF>
 __global__ void stencil_finish_kernel(const Params *params, int64_t n, int64_t T_max, const double *ws,
                                       double *prices)
 {
@@ -245,7 +288,14 @@ __global__ void stencil_finish_kernel(const Params *params, int64_t n, int64_t T
         const int64_t launches = (P.T + kRows - 1) / kRows;
         const double *rowA = ws + o * L.stride + L.W;
         const double *row = (launches % 2 == 0) ? rowA : rowA + L.W;
-        const double v = (P.model == AOP_BSM_PUT) ? row[P.T] : row[0];
+        const int64_t at = (P.model == AOP_BSM_PUT) ? P.T : 0;
+        double v;
+        if (DF) {
+            const float2 c = ((const float2 *)row)[at];
+            v = (double)c.x + (double)c.y;
+        } else {
+            v = row[at];
+        }
         prices[o] = v * P.out_scale;
     }
 }
@@ -267,11 +317,12 @@ size_t stencil_workspace_bytes(int64_t n, int64_t T_max) {
     return (size_t)n * (size_t)stencil_layout(T_max).stride * sizeof(double) + 256;
 }
 
-cudaError_t run_stencil(int64_t n, const Params *d_params, int64_t T_max, void *ws,
-                        double *d_prices, int32_t *d_status, int32_t *d_bnd,
-                        const int64_t *d_bnd_off, aop_stats *d_stats, cudaStream_t s)
+template <bool DF>
+static cudaError_t run_stencil_t(int64_t n, const Params *d_params, int64_t T_max, void *ws,
+                                 double *d_prices, int32_t *d_status, int32_t *d_bnd,
+                                 const int64_t *d_bnd_off, aop_stats *d_stats, cudaStream_t s)
 {
-    (void)d_status;
+    (void)d_status;          // statuses come from the parameter kernel
     if (n == 0) return cudaSuccess;
     double *w = (double *)ws;
     if (d_bnd) {
@@ -280,7 +331,7 @@ cudaError_t run_stencil(int64_t n, const Params *d_params, int64_t T_max, void *
     {
         int chunks = (int)std::min<int64_t>((2 * T_max + 1 + 255) / 256, 1024);
         dim3 grid(chunks, (unsigned)std::min<int64_t>(n, 65535));
-        stencil_init_kernel<<<grid, 256, 0, s>>>(d_params, n, T_max, w, d_bnd, d_bnd_off);
+        stencil_init_kernel<DF><<<grid, 256, 0, s>>>(d_params, n, T_max, w, d_bnd, d_bnd_off);
     }
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
@@ -288,10 +339,18 @@ cudaError_t run_stencil(int64_t n, const Params *d_params, int64_t T_max, void *
     const int64_t launches = (T_max + kRows - 1) / kRows;
     long long *cells = d_stats ? (long long *)&d_stats->stencil_cells : nullptr;
     for (int64_t l = 0; l < launches; l++) {
-        stencil_block_kernel<<<sms * 4, kThreads, 0, s>>>(d_params, n, T_max, l, w, d_bnd, d_bnd_off, cells);
+        stencil_block_kernel<DF><<<sms * 4, kThreads, 0, s>>>(d_params, n, T_max, l, w, d_bnd, d_bnd_off, cells);
     }
-    stencil_finish_kernel<<<(unsigned)((n + 127) / 128), 128, 0, s>>>(d_params, n, T_max, w, d_prices);
+    stencil_finish_kernel<DF><<<(unsigned)((n + 127) / 128), 128, 0, s>>>(d_params, n, T_max, w, d_prices);
     return cudaGetLastError();
+}
+
+cudaError_t run_stencil(int64_t n, const Params *d_params, int64_t T_max, void *ws,
+                        double *d_prices, int32_t *d_status, int32_t *d_bnd,
+                        const int64_t *d_bnd_off, aop_stats *d_stats, cudaStream_t s, bool df)
+{
+    return df ? run_stencil_t<true>(n, d_params, T_max, ws, d_prices, d_status, d_bnd, d_bnd_off, d_stats, s)
+              : run_stencil_t<false>(n, d_params, T_max, ws, d_prices, d_status, d_bnd, d_bnd_off, d_stats, s);
 }
 
 }  // namespace aop

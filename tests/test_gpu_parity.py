@@ -12,8 +12,8 @@ from tests import parity
 
 pytestmark = pytest.mark.gpu
 
-METHODS = [aop.FFT_FP64, aop.FFT_FP32SPLIT, aop.STENCIL_FP64, aop.FFT_DF32]
-MNAME = {0: "fft64", 1: "fft32", 2: "stencil", 3: "df32"}
+METHODS = [aop.FFT_FP64, aop.FFT_FP32SPLIT, aop.STENCIL_FP64, aop.FFT_DF32, aop.STENCIL_DF32]
+MNAME = {0: "fft64", 1: "fft32", 2: "stencil", 3: "df32", 4: "stencil_df32"}
 
 
 @pytest.fixture(scope="module")
@@ -130,11 +130,16 @@ def test_extreme_parameters(ctx, method):
 
 def test_fp32_range_status(ctx):
     """No yield, three years at sigma 0.6 and T = 8192: every row is red and the
-    deep in-the-money values reach e^94 S0.  The FP32 methods answer
-    AOP_ERANGE (8) for that option only; FP64 prices it."""
+    deep in-the-money values reach e^94 S0.  The FP32 D&C methods answer
+    AOP_ERANGE (8) for that option only; FP64 prices it, and so does the
+    doubled-FP32 stencil, whose clamp of the exercise values at 1e30 lies 64
+    log-units from the money, out of the walk's reach."""
     wide = wl.Request(0, 100.0, 100.0, 0.05, 0.0, 0.6, 3.0, 8192)
     fine = wl.fixed_call(0, 8192)
     ref = oracle.price_american(wide.as_dict())
+    prices, status = ctx.price_batch([wide, fine], method=aop.STENCIL_DF32)
+    assert (status == 0).all()
+    assert abs(prices[0] - ref) <= parity.price_tol(aop.STENCIL_DF32, ref, wide.K), (prices[0], ref)
     for m in (aop.FFT_FP32SPLIT, aop.FFT_DF32):
         prices, status = ctx.price_batch([wide, fine], method=m)
         assert status[0] == 8 and np.isnan(prices[0]), (m, status, prices)

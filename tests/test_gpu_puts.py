@@ -15,8 +15,8 @@ from tests import parity
 
 pytestmark = pytest.mark.gpu
 
-METHODS = [aop.FFT_FP64, aop.FFT_FP32SPLIT, aop.STENCIL_FP64, aop.FFT_DF32]
-MNAME = {0: "fft64", 1: "fft32", 2: "stencil", 3: "df32"}
+METHODS = [aop.FFT_FP64, aop.FFT_FP32SPLIT, aop.STENCIL_FP64, aop.FFT_DF32, aop.STENCIL_DF32]
+MNAME = {0: "fft64", 1: "fft32", 2: "stencil", 3: "df32", 4: "stencil_df32"}
 BP, TP = aop.BINOMIAL_PUT, aop.TRINOMIAL_PUT
 
 
