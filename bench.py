@@ -44,6 +44,34 @@ FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12     # SMs x FP32 lanes x FMA x 
 FP64_PEAK_TFLOPS = 1.25                              # GB300 dense FP64 (vendor figure)
 WORKLOAD = "precision_sweep_T131072_256binomial_256trinomial"
 
+# DRAM traffic of one launch of the pricing kernel on this book, from one
+# ncu capture (dram__bytes_read.sum + dram__bytes_write.sum, one-pass launch
+# list of `bench.py --steps 2 --warmup 3 --no-tune --no-cpu-baseline
+# --stencil-sample 0 --serve-n 0`, summarised in
+# profiles/bench_launches_precision_sweep_T131072.md).  It holds for the kernel
+# sources whose SHA-256 is recorded with it; any other source reports null.
+KERNEL_SOURCES = ("paper_2303_02317_gb300/csrc/dnc.cu", "paper_2303_02317_gb300/csrc/fft.cuh",
+                  "paper_2303_02317_gb300/csrc/common.cuh")
+TRAFFIC_CAPTURE = {"sources_sha256": "02be6678a52544c992bb27fd8efc8bff1485af9bf79adc7f899977c7a0e96fd1",
+                   "bytes_per_launch": {"df32": 65217e6, "fft32": 37582e6, "fft64": 68945e6}}
+
+
+def kernel_sources_sha256() -> str:
+    import hashlib
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
+def captured_traffic(method_name: str):
+    """Bytes per launch of the captured kernel, or None when the sources
+    changed since the capture (or the method was not captured)."""
+    if TRAFFIC_CAPTURE["sources_sha256"] != kernel_sources_sha256():
+        return None
+    return TRAFFIC_CAPTURE["bytes_per_launch"].get(method_name)
+
 
 def _peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
@@ -588,7 +616,7 @@ def main():
         note = "FP64 peak: vendor dense FP64 figure"
     achieved = flops / kern_s / 1e12
     roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-            "frac": achieved / peak, "traffic": None, "kernel": "dnc_kernel",
+            "frac": achieved / peak, "traffic": captured_traffic(args.method), "kernel": "dnc_kernel",
             "per_launch_flops": flops, "kernel_ms": kms, "peak_source": note,
             "hbm_gbs_measured": peaks.get("hbm_gbs")}
 

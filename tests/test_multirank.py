@@ -51,3 +51,15 @@ def test_single_rank_is_identity():
     import bench
     assert bench.reduce_max(42.0, 1) == 42.0
     assert bench.whole_job_rate(512, 1, 500.0) == 1024.0
+
+
+def test_captured_traffic_only_for_the_captured_sources(monkeypatch):
+    """The roofline's DRAM traffic is reported only while the pricing kernel's
+    sources hash to the value recorded with the ncu capture."""
+    import bench
+    sha = bench.kernel_sources_sha256()
+    monkeypatch.setattr(bench, "TRAFFIC_CAPTURE", {"sources_sha256": sha, "bytes_per_launch": {"df32": 123}})
+    assert bench.captured_traffic("df32") == 123
+    assert bench.captured_traffic("fft64") is None
+    monkeypatch.setattr(bench, "TRAFFIC_CAPTURE", {"sources_sha256": "0" * 64, "bytes_per_launch": {"df32": 123}})
+    assert bench.captured_traffic("df32") is None
