@@ -69,7 +69,7 @@ constexpr int kSpecSlots = 128;
 constexpr int kSpecLg = 22;                // log2 g and log2 N of directly indexed spectra
 constexpr int kLeftoverCall = 48;          // rows solved naively at the root
 constexpr double kDfLogRange = 80.0;       // largest log price ratio of a doubled-FP32 base case
-constexpr int kRegCells = 288;             // widest base-case window: 9 registers per lane
+constexpr int kRegCells = 256;             // widest base-case window: 8 registers per lane
 constexpr int kNaiveCap = 512;             // widest base-case window (cells) and exercise table
 constexpr uint64_t kWaitNs = 30ull * 1000000000ull;   // bound of every spin-wait (30 s)
 
@@ -1079,14 +1079,12 @@ struct Walker {
             if (need <= 32) return call_rows<1, 1, A>(i0, c0, b, h, in, out, klo, khi);
             if (need <= 64) return call_rows<2, 1, A>(i0, c0, b, h, in, out, klo, khi);
             if (need <= 128) return call_rows<4, 1, A>(i0, c0, b, h, in, out, klo, khi);
-            if (need <= 256) return call_rows<8, 1, A>(i0, c0, b, h, in, out, klo, khi);
-            return call_rows<9, 1, A>(i0, c0, b, h, in, out, klo, khi);
+            return call_rows<8, 1, A>(i0, c0, b, h, in, out, klo, khi);
         }
         if (need <= 32) return call_rows<1, 2, A>(i0, c0, b, h, in, out, klo, khi);
         if (need <= 64) return call_rows<2, 2, A>(i0, c0, b, h, in, out, klo, khi);
         if (need <= 128) return call_rows<4, 2, A>(i0, c0, b, h, in, out, klo, khi);
-        if (need <= 256) return call_rows<8, 2, A>(i0, c0, b, h, in, out, klo, khi);
-        return call_rows<9, 2, A>(i0, c0, b, h, in, out, klo, khi);
+        return call_rows<8, 2, A>(i0, c0, b, h, in, out, klo, khi);
     }
 
     __device__ int64_t naive_call_body(int64_t i0, int64_t c0, int64_t b, int64_t h, const Buf &in, const Buf &out) {
@@ -1219,8 +1217,7 @@ struct Walker {
         if (w <= 32) return put_rows<1, A>(n, lo, hi, f, h, in, out);
         if (w <= 64) return put_rows<2, A>(n, lo, hi, f, h, in, out);
         if (w <= 128) return put_rows<4, A>(n, lo, hi, f, h, in, out);
-        if (w <= 256) return put_rows<8, A>(n, lo, hi, f, h, in, out);
-        return put_rows<9, A>(n, lo, hi, f, h, in, out);
+        return put_rows<8, A>(n, lo, hi, f, h, in, out);
     }
 
     __device__ int64_t naive_put_body(int64_t n, int64_t lo, int64_t hi, int64_t f, int64_t h, const Buf &in,
