@@ -126,6 +126,11 @@ typedef struct aop_request {
  * same SM sub-partition, apart from the convolution warps; this bit spreads
  * them one per sub-partition instead (the FP64 mode always spreads). */
 #define AOP_FLAG_SPREAD_WALKERS 8
+/* Test of the failure path (D&C methods): no convolution warp takes a task and
+ * every device-side wait gives up after 20 ms, so each option ends with
+ * AOP_ETIMEOUT and a NaN price; the call returns and the context stays usable.
+ * Nothing is faulted or hung.  Not for pricing. */
+#define AOP_FLAG_TEST_STALL 16
 
 typedef struct aop_options {
     int32_t method;     /* aop_method */

@@ -152,6 +152,7 @@ FLAG_OPTION_TIMES = 1
 FLAG_TILT_OFF = 2
 FLAG_TILT_ON = 4
 FLAG_SPREAD_WALKERS = 8
+FLAG_TEST_STALL = 16
 
 
 

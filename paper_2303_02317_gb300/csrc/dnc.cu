@@ -72,6 +72,7 @@ constexpr double kDfLogRange = 80.0;       // largest log price ratio of a doubl
 constexpr int kRegCells = 256;             // widest base-case window: 8 registers per lane
 constexpr int kNaiveCap = 512;             // widest base-case window (cells) and exercise table
 constexpr uint64_t kWaitNs = 30ull * 1000000000ull;   // bound of every spin-wait (30 s)
+constexpr uint64_t kStallNs = 20000000ull;             // the bound under AOP_FLAG_TEST_STALL (20 ms)
 
 __device__ __forceinline__ uint64_t gtime() {
     uint64_t t;
@@ -177,6 +178,13 @@ struct DncArgs {
     volatile int32_t *sdone;           // 1 once request o's result is written
     int64_t sT_max;                    // longest T the session's workspace holds
 };
+
+// Bound of the walker's and the workers' waits: AOP_FLAG_TEST_STALL (a test of
+// the failure path: no worker takes a task) shortens it so that the first wait
+// gives up quickly with AOP_ETIMEOUT.
+__device__ __forceinline__ uint64_t wait_limit(const DncArgs &a) {
+    return (a.flags & AOP_FLAG_TEST_STALL) ? kStallNs : kWaitNs;
+}
 
 // Serving: claim the next published request, or -1 when the host asks the
 // kernel to stop or nothing is published for kIdleNs (the host relaunches the
@@ -942,10 +950,11 @@ struct Walker {
             Task &t = S.tasks[d];
             const uint64_t t0 = gtime();
             unsigned ns = 16;            // backoff: a long wait polls less often
+            const uint64_t lim = wait_limit(c.a);
             while (t.state == TASK_POSTED || t.state == TASK_CLAIMED) {
                 __nanosleep(ns);
                 if (ns < 128) ns <<= 1;
-                if (gtime() - t0 > kWaitNs) { atomicCAS((int *)&S.err, 0, AOP_ETIMEOUT); break; }
+                if (gtime() - t0 > lim) { atomicCAS((int *)&S.err, 0, AOP_ETIMEOUT); break; }
             }
             cnt.wait_ns += (long long)(gtime() - t0);
             t.state = TASK_FREE;
@@ -1751,7 +1760,7 @@ dnc_kernel(const __grid_constant__ DncArgs a)
                 int pick = -1;
                 if (lane == 0) {
                     if (S.done) pick = -2;
-                    else {
+                    else if (!(a.flags & AOP_FLAG_TEST_STALL)) {
                         // posted slots from the mask word, deepest first
                         unsigned m = S.posted;
                         while (m) {
@@ -1772,7 +1781,7 @@ dnc_kernel(const __grid_constant__ DncArgs a)
                 if (pick < 0) {
                     __nanosleep(nap);
                     if (nap < 256) nap <<= 1;
-                    if (gtime() - idle0 > kWaitNs) {
+                    if (gtime() - idle0 > wait_limit(a)) {
                         if (lane == 0) atomicCAS((int *)&S.err, 0, AOP_ETIMEOUT);
                         break;
                     }
