@@ -25,11 +25,12 @@
 //
 // Execution inside the CTA follows the paper's observation that each FFT
 // advance can run in parallel with the recursion beside it (proof of Thm 2.8):
-// warp 0 (the walker) runs the recursion and the base cases and posts
-// every linear advance as a task in a per-depth slot; warps 1..3 (workers)
-// execute the tasks (warp-level FFT convolutions) while the walker continues
-// down the sub-trapezoid, and the walker waits for a task only when its
-// output is needed.  The kernel power s(theta)^h of every (height, transform
+// one warp (the walker: in the FP32 modes the one on SM sub-partition 0, so that
+// the walkers of an SM share it) runs the recursion and the base cases and posts
+// every linear advance as a task in a per-depth slot; the other three warps
+// (workers) execute the tasks (warp-level FFT convolutions) while the walker
+// continues down the sub-trapezoid, and the walker waits for a task only when
+// its output is needed.  The kernel power s(theta)^h of every (height, transform
 // length) pair is evaluated once per option in FP64 on the band where |s|^h
 // exceeds 2^-60 of its peak and cached.
 #include <algorithm>
