@@ -30,6 +30,7 @@ import os
 import statistics
 import subprocess
 import sys
+import tempfile
 import time
 
 import numpy as np
@@ -47,8 +48,8 @@ WORKLOAD = "precision_sweep_T131072_256binomial_256trinomial"
 # DRAM traffic of one launch of the pricing kernel on this book, from one
 # ncu capture (dram__bytes_read.sum + dram__bytes_write.sum, one-pass launch
 # list of `bench.py --steps 2 --warmup 3 --no-tune --no-cpu-baseline
-# --stencil-sample 0 --serve-n 0`, summarised in
-# profiles/bench_launches_precision_sweep_T131072.md).  It holds for the kernel
+# --stencil-sample 0 --serve-n 0`, summarised with the launch list under
+# profiles/).  It holds for the kernel
 # sources whose SHA-256 is recorded with it; any other source reports null.
 KERNEL_SOURCES = ("paper_2303_02317_gb300/csrc/dnc.cu", "paper_2303_02317_gb300/csrc/fft.cuh",
                   "paper_2303_02317_gb300/csrc/common.cuh")
@@ -180,7 +181,9 @@ class ClockSampler:
     def __init__(self, index: int):
         self.index = index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", "clocks_bench.csv")
+        # the raw samples (the JSON line carries their summary); BENCH_CLOCKS_CSV
+        # overrides the place
+        self.path = os.environ.get("BENCH_CLOCKS_CSV") or os.path.join(tempfile.gettempdir(), "bench_clocks.csv")
 
     def start(self):
         os.makedirs(os.path.dirname(self.path), exist_ok=True)

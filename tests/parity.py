@@ -1,6 +1,7 @@
 """Shared parity rules for the GPU tests (no library code here).
 
-Tolerances (derived in DESIGN.md, "Parity tolerances"):
+Tolerances (the FFT rounding is relative to the largest value of the
+convolved window, O(K) near the divider, hence the absolute floor in K):
   FP64 methods (FFT_FP64, STENCIL_FP64) and the doubled-FP32 ones (FFT_DF32,
   STENCIL_DF32):
       |gpu - oracle| <= 1e-10 |oracle| + 1e-12 K
