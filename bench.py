@@ -103,7 +103,7 @@ def whole_job_rate(options_per_rank: int, world: int, ms: float) -> float:
 
 class EnergyMeter:
     """GPU energy over a region, read through NVML (read-only queries):
-    the driver's total-energy counter when the device exposes it, else the
+    the GPU's total-energy counter (NVML) when the device exposes it, else the
     integral of power readings taken every 5 ms by a background thread
     (trapezoid rule).  measure() returns (joules, how) or (None, reason)."""
 
@@ -121,7 +121,7 @@ class EnergyMeter:
             if lib.nvmlDeviceGetHandleByIndex_v2(ctypes.c_uint(index), ctypes.byref(h)) != 0:
                 raise RuntimeError("no NVML handle for device %d" % index)
             self.lib, self.handle = lib, h
-        except Exception as e:                      # no driver library here
+        except Exception as e:                      # no NVML library here
             self.why = str(e)
 
     def _counter_mj(self):
