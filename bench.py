@@ -43,6 +43,9 @@ T_BENCH = 1 << 17
 N_BINOMIAL = N_TRINOMIAL = 256
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12     # SMs x FP32 lanes x FMA x max clock
 FP64_PEAK_TFLOPS = 1.25                              # GB300 dense FP64 (vendor figure)
+# FP64 FMA rate measured on this GPU: one warp instruction per 64 cycles per SM
+# sub-partition whatever the active lanes -> 152 x 4 x 32 / 64 x 2 flop x 2.07 GHz
+FP64_MEASURED_TFLOPS = 152 * 4 * 32 / 64 * 2 * 2.07e9 / 1e12
 WORKLOAD = "precision_sweep_T131072_256binomial_256trinomial"
 
 # DRAM traffic of one launch of the pricing kernel on this book, from one
@@ -251,10 +254,24 @@ def cpu_oracle_sample(reqs, n_sample, budget_s=25.0):
     return len(done) / dt, dt, threads, desc, done, prices
 
 
-def stencil_sample(ctx, aop, sarr, m, p_ref, local):
+def stencil_flops(reqs) -> float:
+    """Algorithmic flops of the plain backward induction over the requests:
+    (D+1) products and D sums per cell, T(T+1)/2 cells for the binomial
+    lattice, T^2 for the trinomial one and the BSM grid."""
+    tot = 0.0
+    for r in reqs:
+        T = float(r.T)
+        if r.model in (0, 3):
+            tot += 3.0 * T * (T + 1) / 2
+        else:
+            tot += 5.0 * T * T
+    return tot
+
+
+def stencil_sample(ctx, aop, sarr, m, p_ref, local, reqs=None):
     """Price a sample of the book with the plain stencil method m: ms/option,
-    cells/s, energy and the largest relative distance to the FP64 D&C prices
-    p_ref of the same options."""
+    cells/s, its ALU roofline, energy and the largest relative distance to the
+    FP64 D&C prices p_ref of the same options."""
     meter = EnergyMeter(local)
     meter.start()
     ps, ss = ctx.price_batch(sarr, method=m)
@@ -269,6 +286,16 @@ def stencil_sample(ctx, aop, sarr, m, p_ref, local):
            "energy_how": how}
     if joules is not None:
         out["joules_per_option"] = joules / len(sarr)
+    if reqs is not None:
+        fl = stencil_flops(reqs)
+        ach = fl / (ms / 1e3) / 1e12
+        if m == aop.STENCIL_FP64:
+            peak, src = FP64_MEASURED_TFLOPS, "FP64 peak measured: one warp FMA per 64 cycles per SM sub-partition"
+        else:
+            peak, src = FP32_PEAK_TFLOPS, ("FP32 peak derived from unit counts; a doubled-FP32 cell costs "
+                                           "about 25 FP32 instructions for its 3-5 algorithmic flops")
+        out["roofline"] = {"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
+                           "flops": fl, "peak_source": src}
     return out
 
 
@@ -597,8 +624,8 @@ def main():
               [N_BINOMIAL + i for i in range(args.stencil_sample - args.stencil_sample // 2)]
         desc = "%d options of the book (%d binomial, %d trinomial)" % (
             len(samp), sum(1 for r in samp if r.model == 0), sum(1 for r in samp if r.model == 1))
-        stencil = stencil_sample(ctx, aop, sarr, aop.STENCIL_FP64, p64[idx], local)
-        stencil32 = stencil_sample(ctx, aop, sarr, aop.STENCIL_DF32, p64[idx], local)
+        stencil = stencil_sample(ctx, aop, sarr, aop.STENCIL_FP64, p64[idx], local, samp)
+        stencil32 = stencil_sample(ctx, aop, sarr, aop.STENCIL_DF32, p64[idx], local, samp)
         stencil["sample"] = stencil32["sample"] = desc
         cands = [(s_["ms_per_option"], name, s_) for name, s_ in (("stencil_fp64", stencil), ("stencil_df32", stencil32))
                  if s_["failed"] == 0 and s_["max_rel_fft64_vs_stencil"] is not None

@@ -63,3 +63,14 @@ def test_captured_traffic_only_for_the_captured_sources(monkeypatch):
     assert bench.captured_traffic("fft64") is None
     monkeypatch.setattr(bench, "TRAFFIC_CAPTURE", {"sources_sha256": "0" * 64, "bytes_per_launch": {"df32": 123}})
     assert bench.captured_traffic("df32") is None
+
+
+def test_stencil_flops_counts_the_lattice_cells():
+    """(D+1) products and D sums per cell: T(T+1)/2 binomial cells, T^2
+    trinomial or BSM cells."""
+    import bench
+    from paper_2303_02317_gb300 import workloads as wl
+    T = 100
+    assert bench.stencil_flops([wl.fixed_call(0, T)]) == 3.0 * T * (T + 1) / 2
+    assert bench.stencil_flops([wl.fixed_call(1, T)]) == 5.0 * T * T
+    assert bench.stencil_flops([wl.fixed_bsm_put(T)]) == 5.0 * T * T
