@@ -347,6 +347,21 @@ def serve_stream(ctx, aop, wl, method, args, stencil_method=None):
                                              "p99": float(np.percentile(lat[:m], 99) * 1e3)},
             "max_rel_fft_vs_stencil": float(rel[ok & (ps > 1e-3 * arr["K"][:m])].max()),
             "what": "the first %d requests of the stream as one plain-stencil batch" % m}
+    # the same mix offered below capacity (80 % of the rate just sustained):
+    # the latency the session adds when requests do not queue behind a backlog
+    n2 = min(8192, len(reqs))
+    rate2 = 0.8 * out["options_per_s"]
+    reqs2, arr2 = wl.request_stream(n=n2, rate=rate2, seed=2318)
+    with aop.Server(ctx, capacity=n2, T_max=T_MAX, method=method) as srv:
+        p2, st2, lat2 = srv.serve_stream(aop.requests_array(reqs2), arr2, timeout_s=600.0)
+    if (st2 != 0).any():
+        raise SystemExit("serving below capacity: status %s" % np.unique(st2))
+    span2 = float((arr2 + lat2).max() - arr2.min())
+    out["below_capacity"] = {
+        "requests": n2, "offered_rate_per_s": rate2, "options_per_s": n2 / span2,
+        "latency_ms": {"p50": float(np.percentile(lat2, 50) * 1e3), "p99": float(np.percentile(lat2, 99) * 1e3),
+                       "max": float(lat2.max() * 1e3), "mean": float(lat2.mean() * 1e3)},
+        "stream": "same mix and T range, Poisson at 80 % of the sustained rate, seed 2318"}
     return out
 
 
