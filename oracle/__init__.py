@@ -225,12 +225,31 @@ def max_threads() -> int:
     return int(_load().or_max_threads())
 
 
+def linear_advance(x, w, h: int):
+    """The linear stencil of the continuation region applied h times (the
+    step each FFT convolution of Sec. 3.3 "Solving a Trapezoid" performs over
+    the red cells): y_{k+1}[j] = sum_o w[o] y_k[j + o] for o = 0 .. len(w)-1,
+    keeping the cells whose dependency cone lies inside the segment, so that a
+    row of W cells yields W - (len(w) - 1) h cells.  Plain FP64 numpy, one
+    step at a time.  x: (count, W) or (W,) array."""
+    y = np.array(x, dtype=np.float64, copy=True)
+    w = [float(v) for v in w]
+    span = len(w) - 1
+    for _ in range(int(h)):
+        n = y.shape[-1] - span
+        z = w[0] * y[..., 0:n]
+        for o in range(1, span + 1):
+            z = z + w[o] * y[..., o:o + n]
+        y = z
+    return y
+
+
 def tie_band(req) -> float:
     """Rows whose oracle margin is at most this may legitimately disagree on
     the boundary index by one (a tie between continuation and exercise)."""
     return 1e-12 * (1.0 if int(_field(req, "model")) == BSM else float(_field(req, "K")))
 
 
-__all__ = ["build", "params", "status_of", "price_american", "price_european", "grid", "greeks",
+__all__ = ["build", "params", "status_of", "price_american", "price_european", "grid", "greeks", "linear_advance",
            "price_many", "max_threads", "columns", "tie_band", "BOPM", "TOPM", "BSM",
            "BOPM_PUT", "TOPM_PUT", "INT32_MIN"]

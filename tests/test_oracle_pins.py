@@ -533,3 +533,46 @@ def test_american_greeks_satisfy_the_pde_at_the_root(oracle_lib):
         S = req["S0"]
         res = t + 0.5 * req["sigma"] ** 2 * S * S * g + (req["r"] - req["q"]) * S * d - req["r"] * v
         assert abs(res) < 3e-3 * req["r"] * v, (model, res, v)
+
+
+# ------------------------------------------------ the linear advance (Sec. 3.3)
+
+def _unit_response(oracle, w, h, W):
+    """Row of the h-step advance's kernel: the advance of unit rows e_j."""
+    eye = np.eye(W)
+    return oracle.linear_advance(eye, w, h)[:, 0]      # output cell 0 sees input j with weight k_j
+
+
+def test_linear_advance_binomial_coefficients(oracle_lib):
+    """Two-point stencil: output cell y sees input y + j with weight
+    C(h, j) w0^(h-j) w1^j (the binomial distribution of h up-moves)."""
+    from math import comb
+    w, h = (0.37, 0.61), 23
+    k = _unit_response(oracle_lib, w, h, h + 1)
+    want = np.array([comb(h, j) * w[0] ** (h - j) * w[1] ** j for j in range(h + 1)])
+    assert np.allclose(k, want, rtol=1e-13, atol=0.0)
+
+
+def test_linear_advance_trinomial_coefficients(oracle_lib):
+    """Three-point stencil: the weight of offset j is the multinomial sum
+    over a + b + c = h, b + 2c = j of h!/(a! b! c!) w0^a w1^b w2^c."""
+    from math import factorial
+    w, h = (0.21, 0.5, 0.28), 9
+    k = _unit_response(oracle_lib, w, h, 2 * h + 1)
+    want = np.zeros(2 * h + 1)
+    for c in range(h + 1):
+        for b in range(h - c + 1):
+            a = h - b - c
+            want[b + 2 * c] += factorial(h) // (factorial(a) * factorial(b) * factorial(c)) * \
+                w[0] ** a * w[1] ** b * w[2] ** c
+    assert np.allclose(k, want, rtol=1e-13, atol=0.0)
+
+
+def test_linear_advance_constant_row_and_shape(oracle_lib):
+    """A constant row stays constant times (sum w)^h; W cells give
+    W - (len(w) - 1) h cells."""
+    for w, h in (((0.4, 0.55), 17), ((0.2, 0.3, 0.45), 11)):
+        x = np.full((2, 200), 3.5)
+        y = oracle_lib.linear_advance(x, w, h)
+        assert y.shape == (2, 200 - (len(w) - 1) * h)
+        assert np.allclose(y, 3.5 * sum(w) ** h, rtol=1e-14, atol=0.0)
