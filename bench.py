@@ -458,7 +458,7 @@ def run_reference(args):
     value = len(sample) / per_step
     line = {
         "impl": "reference", "metric": "options_per_second", "value": value, "unit": "options/s",
-        "n_gpus": 0, "steps": args.steps, "warmup": args.warmup, "ms_per_step": per_step * 1e3,
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": per_step * 1e3,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
         "config": {"workload": WORKLOAD, "T": T_BENCH, "step_sample": "1 binomial + 1 trinomial option"},
