@@ -675,6 +675,67 @@ struct Cta {
         G::sync();
     }
 
+    // Real-input form of a single-tile advance (16-byte transform values, whose
+    // imaginary half would otherwise carry zeros): the N real cells are staged
+    // as M = N/2 complex values z[s] = x[2s] + i x[2s+1]; after the M-point
+    // forward transform Z, each pair of bins (k, M-k) gives the N-point
+    // spectrum of the row, X[k] = E + W^k O and X[k+M] = E - W^k O with
+    // E = (Z[k] + conj Z[M-k])/2, O = (Z[k] - conj Z[M-k])/(2i), W = e^{-2 pi i/N};
+    // times the kernel power Y = X S, it is folded back into
+    // Z''[k] = (Y[k] + Y[k+M]) + i W^{-k} (Y[k] - Y[k+M]), whose M-point inverse
+    // is N (y[2s] + i y[2s+1]) (Y is Hermitian, so the pair's second bin is
+    // Z''[M-k] = conj(A) + i W^k conj(B) with A, B the sum and difference).
+    template <class G, class ST>
+    __device__ void stage_real(V *tile, int N, const Buf &in, int64_t x_lo, int64_t W) {
+        using C = typename ST::T;                      // an 8-byte stored cell
+        static_assert(sizeof(C) == 8, "stored values are 8 bytes");
+        const C *src = (const C *)in.p - in.base;
+        for (int c = G::rank(); c < N; c += G::size()) {
+            const bool ok = c < W;
+            fft::cp_async<8>((C *)tile + c, ok ? (const void *)&src[x_lo + c] : (const void *)in.p, ok ? 8 : 0);
+        }
+        fft::cp_async_wait();
+        G::sync();
+        for (int s = G::rank(); s < N / 2; s += G::size()) {
+            // cells 2s and 2s + 1 occupy the bytes of tile[s]: read both first
+            const C c0 = ((const C *)tile)[2 * s], c1 = ((const C *)tile)[2 * s + 1];
+            V v0 = ST::to_v(c0), v1 = ST::to_v(c1);
+            if (tilt) {
+                if (2 * s < W) v0 = tilt_in(v0, W - 1 - 2 * s);
+                if (2 * s + 1 < W) v1 = tilt_in(v1, W - 2 - 2 * s);
+            }
+            if constexpr (MODE == 0) {
+                tile[s] = make_double2(v0.x, v1.x);
+            } else {
+                fft::df2 r;
+                r.v = make_float4(v0.v.x, v1.v.x, v0.v.z, v1.v.z);
+                tile[s] = r;
+            }
+        }
+        G::sync();
+    }
+    template <class G>
+    __device__ void real_pairs(V *tile, int lgN, const Sp *sp, int mc, int64_t g) {
+        const int lgM = lgN - 1;
+        const uint32_t M = 1u << lgM, N = 2u * M;
+        const Tw *T = tw();
+        for (int k = G::rank(); k <= (int)(M / 2); k += G::size()) {
+            const int j = (int)((M - (uint32_t)k) & (M - 1));
+            const int pk = (int)fft::brev_n((uint32_t)k, lgM), pj = (int)fft::brev_n((uint32_t)j, lgM);
+            const V zk = tile[pk], cj = fft::cconj(tile[pj]);
+            const V E = fft::chalf(fft::cadd(zk, cj));
+            const V O = fft::chalf(fft::cmul_mi(fft::csub(zk, cj)));
+            const Tw w = fft::tw_get<MODE>(T, a.tw_log2, k, lgN);     // W^k, k < M
+            const V wo = fft::twmul<false>(O, w);
+            const V yk = mul_bin(fft::cadd(E, wo), sp, mc, (uint32_t)k, N, g, lgN);
+            const V ym = mul_bin(fft::csub(E, wo), sp, mc, (uint32_t)k + M, N, g, lgN);
+            const V A = fft::cadd(yk, ym), B = fft::csub(yk, ym);
+            tile[pk] = fft::cadd(A, fft::cmul_pi(fft::twmul<true>(B, w)));
+            if (pj != pk) tile[pj] = fft::cadd(fft::cconj(A), fft::cmul_pi(fft::twmul<false>(fft::cconj(B), w)));
+        }
+        G::sync();
+    }
+
     __device__ V mul_bin(V z, const Sp *sp, int mc, uint32_t m, uint32_t N, int64_t g, int lgN) const {
         if (sp) return fft::spec_mul<MODE>(z, sp, mc, m, N);
         uint32_t mm = (m <= N / 2) ? m : N - m;
@@ -755,6 +816,37 @@ struct Cta {
             cnt.conv_out += nout;
         }
         const Tw *T = tw();
+        if constexpr (sizeof(V) == 16) {
+            if (lgN <= lg_tile) {
+                const long long q1 = clock64();
+                stage_real<G, ST>(tile, (int)N, in, x_lo, W);
+                const long long q2 = clock64();
+                fft::dif_all<MODE, G>(tile, lgN - 1, T);
+                real_pairs<G>(tile, lgN, sp, mc, g);
+                const long long q3 = clock64();
+                fft::dit_all<MODE, G>(tile, lgN - 1, T);
+                const long long q4 = clock64();
+                for (int64_t t = G::rank(); t < nout; t += G::size()) {
+                    const int64_t p = off + t;
+                    V v = tile[p >> 1];
+                    if (p & 1) {                          // odd cells in the imaginary part
+                        if constexpr (MODE == 0) v = make_double2(v.y, 0.0);
+                        else v.v = make_float4(v.v.y, 0.f, v.v.w, 0.f);
+                    }
+                    store<ST>(out, y_lo + t, untilt<ST>(ST::from_v(v, cs), W - 1 - t, cs));
+                }
+                G::sync();
+                if (leader<G>()) {
+                    const long long q5 = clock64();
+                    cnt.cv_cyc[0] += q1 - q0;
+                    cnt.cv_cyc[1] += q2 - q1;
+                    cnt.cv_cyc[2] += q3 - q2;
+                    cnt.cv_cyc[3] += q4 - q3;
+                    cnt.cv_cyc[4] += q5 - q4;
+                }
+                return lgN;
+            }
+        }
         if (lgN <= lg_tile) {
             const long long q1 = clock64();
             stage_input<G, ST>(tile, (int)N, [](int s) { return s; }, in, x_lo, W);

@@ -154,6 +154,16 @@ __device__ __forceinline__ float2 cmul_pi(float2 a) { return make_float2(-a.y, a
 __device__ __forceinline__ df2 cmul_mi(df2 a) { df2 r; r.v = make_float4(a.v.y, -a.v.x, a.v.w, -a.v.z); return r; }
 __device__ __forceinline__ df2 cmul_pi(df2 a) { df2 r; r.v = make_float4(-a.v.y, a.v.x, -a.v.w, a.v.z); return r; }
 
+// complex conjugate and halving (exact)
+__device__ __forceinline__ double2 cconj(double2 a) { return make_double2(a.x, -a.y); }
+__device__ __forceinline__ df2 cconj(df2 a) { df2 r; r.v = make_float4(a.v.x, -a.v.y, a.v.z, -a.v.w); return r; }
+__device__ __forceinline__ double2 chalf(double2 a) { return make_double2(0.5 * a.x, 0.5 * a.y); }
+__device__ __forceinline__ df2 chalf(df2 a) {
+    df2 r;
+    r.v = make_float4(0.5f * a.v.x, 0.5f * a.v.y, 0.5f * a.v.z, 0.5f * a.v.w);
+    return r;
+}
+
 // v * w (CONJ: v * conj(w))
 template <bool CONJ>
 __device__ __forceinline__ double2 twmul(double2 v, double2 w) {
