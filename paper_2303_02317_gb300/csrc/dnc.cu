@@ -685,24 +685,29 @@ struct Cta {
     // Z''[k] = (Y[k] + Y[k+M]) + i W^{-k} (Y[k] - Y[k+M]), whose M-point inverse
     // is N (y[2s] + i y[2s+1]) (Y is Hermitian, so the pair's second bin is
     // Z''[M-k] = conj(A) + i W^k conj(B) with A, B the sum and difference).
-    template <class G, class ST>
-    __device__ void stage_real(V *tile, int N, const Buf &in, int64_t x_lo, int64_t W) {
+    // Stage the cells 2e and 2e + 1 (e = idx(s)) of the window as tile[s] =
+    // x[2e] + i x[2e+1] (zero past W).  The two 8-byte cells land in the bytes
+    // of tile[s] and are converted in place by the thread that loaded them.
+    template <class G, class ST, class IDX>
+    __device__ void stage_packed(V *tile, int count, IDX idx, const Buf &in, int64_t x_lo, int64_t W) {
         using C = typename ST::T;                      // an 8-byte stored cell
         static_assert(sizeof(C) == 8, "stored values are 8 bytes");
         const C *src = (const C *)in.p - in.base;
-        for (int c = G::rank(); c < N; c += G::size()) {
-            const bool ok = c < W;
-            fft::cp_async<8>((C *)tile + c, ok ? (const void *)&src[x_lo + c] : (const void *)in.p, ok ? 8 : 0);
+        for (int s = G::rank(); s < count; s += G::size()) {
+            const int64_t c = 2 * (int64_t)idx(s);
+            const bool ok0 = c < W, ok1 = c + 1 < W;
+            fft::cp_async<8>((C *)tile + 2 * s, ok0 ? (const void *)&src[x_lo + c] : (const void *)in.p, ok0 ? 8 : 0);
+            fft::cp_async<8>((C *)tile + 2 * s + 1, ok1 ? (const void *)&src[x_lo + c + 1] : (const void *)in.p,
+                             ok1 ? 8 : 0);
         }
         fft::cp_async_wait();
-        G::sync();
-        for (int s = G::rank(); s < N / 2; s += G::size()) {
-            // cells 2s and 2s + 1 occupy the bytes of tile[s]: read both first
+        for (int s = G::rank(); s < count; s += G::size()) {
+            const int64_t c = 2 * (int64_t)idx(s);
             const C c0 = ((const C *)tile)[2 * s], c1 = ((const C *)tile)[2 * s + 1];
             V v0 = ST::to_v(c0), v1 = ST::to_v(c1);
             if (tilt) {
-                if (2 * s < W) v0 = tilt_in(v0, W - 1 - 2 * s);
-                if (2 * s + 1 < W) v1 = tilt_in(v1, W - 2 - 2 * s);
+                if (c < W) v0 = tilt_in(v0, W - 1 - c);
+                if (c + 1 < W) v1 = tilt_in(v1, W - 2 - c);
             }
             if constexpr (MODE == 0) {
                 tile[s] = make_double2(v0.x, v1.x);
@@ -714,24 +719,47 @@ struct Cta {
         }
         G::sync();
     }
+    // Output cell c (= 2e or 2e + 1) of element value v of a real transform
+    __device__ static V packed_part(V v, int64_t c) {
+        if (c & 1) {
+            if constexpr (MODE == 0) v = make_double2(v.y, 0.0);
+            else v.v = make_float4(v.v.y, 0.f, v.v.w, 0.f);
+        }
+        return v;
+    }
+    // The split-product-merge step on blocks of 2^lti bins of an M-point
+    // transform (M = 2^lgM) stored in bit-reversed order: the block of residue
+    // rb holds bins k = rb + (brev(s) << (lgM - lti)); bin M - k lies in the
+    // mirror block at slot s ^ (2^lti - 1) (held at tile + 2^lti when `two`),
+    // or, for the blocks of residue 0 and 2^(lgM-lti-1), in the same block.
     template <class G>
-    __device__ void real_pairs(V *tile, int lgN, const Sp *sp, int mc, int64_t g) {
-        const int lgM = lgN - 1;
+    __device__ void real_pairs(V *tile, bool two, int rb, int lgM, int lti, const Sp *sp, int mc, int64_t g) {
         const uint32_t M = 1u << lgM, N = 2u * M;
+        const int lgN = lgM + 1;
+        const int Bs = 1 << lti, mask = Bs - 1, nbl = lgM - lti;
         const Tw *T = tw();
-        for (int k = G::rank(); k <= (int)(M / 2); k += G::size()) {
-            const int j = (int)((M - (uint32_t)k) & (M - 1));
-            const int pk = (int)fft::brev_n((uint32_t)k, lgM), pj = (int)fft::brev_n((uint32_t)j, lgM);
+        auto pair = [&](int pk, int pj, uint32_t k) {
             const V zk = tile[pk], cj = fft::cconj(tile[pj]);
             const V E = fft::chalf(fft::cadd(zk, cj));
             const V O = fft::chalf(fft::cmul_mi(fft::csub(zk, cj)));
             const Tw w = fft::tw_get<MODE>(T, a.tw_log2, k, lgN);     // W^k, k < M
             const V wo = fft::twmul<false>(O, w);
-            const V yk = mul_bin(fft::cadd(E, wo), sp, mc, (uint32_t)k, N, g, lgN);
-            const V ym = mul_bin(fft::csub(E, wo), sp, mc, (uint32_t)k + M, N, g, lgN);
+            const V yk = mul_bin(fft::cadd(E, wo), sp, mc, k, N, g, lgN);
+            const V ym = mul_bin(fft::csub(E, wo), sp, mc, k + M, N, g, lgN);
             const V A = fft::cadd(yk, ym), B = fft::csub(yk, ym);
             tile[pk] = fft::cadd(A, fft::cmul_pi(fft::twmul<true>(B, w)));
             if (pj != pk) tile[pj] = fft::cadd(fft::cconj(A), fft::cmul_pi(fft::twmul<false>(fft::cconj(B), w)));
+        };
+        if (two) {
+            for (int s = G::rank(); s < Bs; s += G::size())
+                pair(s, Bs + (s ^ mask), (uint32_t)rb + (fft::brev_n((uint32_t)s, lti) << nbl));
+        } else if (rb == 0) {
+            for (int kp = G::rank(); kp <= Bs / 2; kp += G::size())
+                pair((int)fft::brev_n((uint32_t)kp, lti), (int)fft::brev_n((uint32_t)((Bs - kp) & mask), lti),
+                     (uint32_t)kp << nbl);
+        } else {
+            for (int s = G::rank(); s < Bs / 2; s += G::size())
+                pair(s, s ^ mask, (uint32_t)rb + (fft::brev_n((uint32_t)s, lti) << nbl));
         }
         G::sync();
     }
@@ -750,7 +778,7 @@ struct Cta {
     // DIF = forward (stages top down); otherwise inverse.  The first forward
     // pass reads (and splits) the FP64 input; the last inverse pass extracts
     // the FP64 output.
-    template <class G, class ST, bool DIF>
+    template <class G, class ST, bool DIF, bool REAL = false>
     __device__ void tile_pass(V *tile, int lg_tile, V *scr, int lgN, int s_lo, int s_hi, bool first, bool last,
                               const Buf &in, int64_t x_lo, int64_t W, const Buf &out, int64_t y_lo, int64_t off,
                               int64_t nout, const ConvScale &cs) {
@@ -765,16 +793,30 @@ struct Cta {
             const int hbase = hb << (s_hi + 1);
             for (int q0 = 0; q0 < lo_count; q0 += qm + 1) {
                 auto idx = [=](int s) { return hbase + ((s >> lgQ) << s_lo) + q0 + (s & qm); };
-                if (first) stage_input<G, ST>(tile, count, idx, in, x_lo, W);
-                else stage_scratch<G>(tile, count, idx, scr);
+                if (first) {
+                    if constexpr (REAL) stage_packed<G, ST>(tile, count, idx, in, x_lo, W);
+                    else stage_input<G, ST>(tile, count, idx, in, x_lo, W);
+                } else {
+                    stage_scratch<G>(tile, count, idx, scr);
+                }
                 const fft::Cols cl{lgQ, s_lo, q0};
                 if (DIF) fft::dif_cols<MODE, G>(tile, L, L - 1, 0, cl, T);
                 else fft::dit_cols<MODE, G>(tile, L, 0, L - 1, cl, T);
                 for (int s = G::rank(); s < count; s += G::size()) {
                     const int e = idx(s);
                     if (last) {
-                        const int64_t k = e - off;
-                        if (k >= 0 && k < nout) store<ST>(out, y_lo + k, untilt<ST>(ST::from_v(tile[s], cs), W - 1 - k, cs));
+                        if constexpr (REAL) {
+                            for (int h = 0; h < 2; h++) {      // cells 2e and 2e + 1
+                                const int64_t k = 2 * (int64_t)e + h - off;
+                                if (k >= 0 && k < nout)
+                                    store<ST>(out, y_lo + k,
+                                              untilt<ST>(ST::from_v(packed_part(tile[s], h), cs), W - 1 - k, cs));
+                            }
+                        } else {
+                            const int64_t k = e - off;
+                            if (k >= 0 && k < nout)
+                                store<ST>(out, y_lo + k, untilt<ST>(ST::from_v(tile[s], cs), W - 1 - k, cs));
+                        }
                     } else {
                         scr[e] = tile[s];
                     }
@@ -817,23 +859,18 @@ struct Cta {
         }
         const Tw *T = tw();
         if constexpr (sizeof(V) == 16) {
-            if (lgN <= lg_tile) {
+            if (lgN <= lg_tile + 1) {                     // N/2 complex points fit the tile
                 const long long q1 = clock64();
-                stage_real<G, ST>(tile, (int)N, in, x_lo, W);
+                stage_packed<G, ST>(tile, (int)N / 2, [](int s) { return s; }, in, x_lo, W);
                 const long long q2 = clock64();
                 fft::dif_all<MODE, G>(tile, lgN - 1, T);
-                real_pairs<G>(tile, lgN, sp, mc, g);
+                real_pairs<G>(tile, false, 0, lgN - 1, lgN - 1, sp, mc, g);
                 const long long q3 = clock64();
                 fft::dit_all<MODE, G>(tile, lgN - 1, T);
                 const long long q4 = clock64();
                 for (int64_t t = G::rank(); t < nout; t += G::size()) {
-                    const int64_t p = off + t;
-                    V v = tile[p >> 1];
-                    if (p & 1) {                          // odd cells in the imaginary part
-                        if constexpr (MODE == 0) v = make_double2(v.y, 0.0);
-                        else v.v = make_float4(v.v.y, 0.f, v.v.w, 0.f);
-                    }
-                    store<ST>(out, y_lo + t, untilt<ST>(ST::from_v(v, cs), W - 1 - t, cs));
+                    const int64_t p = off + t;            // odd cells in the imaginary part
+                    store<ST>(out, y_lo + t, untilt<ST>(ST::from_v(packed_part(tile[p >> 1], p), cs), W - 1 - t, cs));
                 }
                 G::sync();
                 if (leader<G>()) {
@@ -867,6 +904,54 @@ struct Cta {
                 cnt.cv_cyc[3] += q4 - q3;
                 cnt.cv_cyc[4] += q5 - q4;
             }
+            return lgN;
+        }
+        if constexpr (sizeof(V) == 16) {
+            // the real row as an M = N/2-point complex transform: outer stages
+            // lti .. lgM-1 over global memory, then the inner stages on pairs of
+            // mirror blocks of 2^lti bins (half a tile each) around the
+            // split-product-merge step
+            const int lgM = lgN - 1, lti = lg_tile - 1;
+            if (leader<G>()) cnt.gbytes += (int64_t)sizeof(V) * (N / 2) * 4 + 8 * (W + nout);
+            const int chunk = max(1, lg_tile - 1);
+            const int outer = lgM - lti;
+            const int nch = min(16, (outer + chunk - 1) / chunk);
+            int ch_lo[16], ch_hi[16];
+            for (int c = 0, s_hi = lgM - 1; c < nch; c++) {
+                const int len = outer / nch + (c < outer % nch ? 1 : 0);
+                ch_hi[c] = s_hi;
+                ch_lo[c] = s_hi - len + 1;
+                s_hi -= len;
+            }
+            for (int c = 0; c < nch; c++)
+                tile_pass<G, ST, true, true>(tile, lg_tile, scr, lgM, ch_lo[c], ch_hi[c], c == 0, false, in, x_lo, W,
+                                             out, y_lo, off, nout, cs);
+            const int Bs = 1 << lti, lgb = lgM - lti, nb = 1 << lgb;
+            for (int b = 0; b < nb; b++) {
+                const int rb = (int)fft::brev_n((uint32_t)b, lgb);
+                const int b2 = (int)fft::brev_n((uint32_t)((nb - rb) & (nb - 1)), lgb);
+                if (b2 < b) continue;                      // each mirror pair once
+                const bool two = b2 != b;
+                V *blk1 = scr + (int64_t)b * Bs, *blk2 = scr + (int64_t)b2 * Bs;
+                const int cnt2 = two ? 2 * Bs : Bs;
+                for (int s = G::rank(); s < cnt2; s += G::size())
+                    fft::cp_async<(int)sizeof(V)>(&tile[s], s < Bs ? &blk1[s] : &blk2[s - Bs], (int)sizeof(V));
+                fft::cp_async_wait();
+                G::sync();
+                fft::dif_all<MODE, G>(tile, lti, T);
+                if (two) fft::dif_all<MODE, G>(tile + Bs, lti, T);
+                real_pairs<G>(tile, two, rb, lgM, lti, sp, mc, g);
+                fft::dit_all<MODE, G>(tile, lti, T);
+                if (two) fft::dit_all<MODE, G>(tile + Bs, lti, T);
+                for (int s = G::rank(); s < cnt2; s += G::size()) {
+                    if (s < Bs) blk1[s] = tile[s];
+                    else blk2[s - Bs] = tile[s];
+                }
+                G::sync();
+            }
+            for (int c = nch - 1; c >= 0; c--)
+                tile_pass<G, ST, false, true>(tile, lg_tile, scr, lgM, ch_lo[c], ch_hi[c], false, c == 0, in, x_lo, W,
+                                              out, y_lo, off, nout, cs);
             return lgN;
         }
         if (leader<G>()) cnt.gbytes += (int64_t)sizeof(V) * N * 4 + 8 * (W + nout);
