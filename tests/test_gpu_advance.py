@@ -25,6 +25,9 @@ CASES = [
     # (nw, W, h, count)
     (2, 5, 1, 3), (2, 64, 31, 2), (2, 100, 37, 4), (3, 100, 10, 2), (3, 4096, 1000, 2),
     (2, 4097, 2000, 1), (3, 5000, 1200, 2), (2, 70000, 3000, 1), (3, 65537, 8000, 1),
+    # around the tile sizes of the real-input transforms (16-byte values: N/2
+    # complex points in one 2^11 tile up to N = 2^12, mirror blocks beyond)
+    (2, 2048, 3, 2), (3, 2049, 5, 1), (2, 8192, 100, 1), (3, 16385, 2000, 1),
 ]
 
 
