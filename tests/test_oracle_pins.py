@@ -165,7 +165,8 @@ def test_bsm_put_without_rate_has_no_early_exercise(oracle_lib):
 
 def test_american_bounds(oracle_lib):
     """max(European on the same lattice, intrinsic) <= American;
-    call <= S0; put <= K (the north-star 'between' reading)."""
+    call <= S0; put <= K (the price lies between the European price and
+    these no-arbitrage caps)."""
     for req in wl.random_small(30, seed=3, T_range=(5, 400)):
         d = req.as_dict()
         am = oracle_lib.price_american(d)
