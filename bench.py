@@ -15,7 +15,8 @@ the book (ms/option; ratios against the faster one within 1e-6),
 the per-option error against the FP64 FFT pricer and the CPU oracle, the
 roofline of the pricing kernel and the CPU oracle timed on the host cores.
 The D&C schedule (base-case height, options in flight per SM) is picked by the
-library's autotuner on the book before the warm-up steps.
+library's autotuner on the book before the warm-up steps (--schedule B:CAP fixes
+it instead, --no-tune leaves the library default).
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 Multi-GPU (torchrun): every rank prices its own copy of the book (weak
