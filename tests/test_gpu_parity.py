@@ -194,3 +194,18 @@ def test_invalid_and_unstable_requests(ctx):
         ref = oracle.price_american(good.as_dict())
         assert abs(prices[0] - ref) <= parity.price_tol(method, ref, good.K)
         assert prices[0] == prices[-1]
+
+
+@pytest.mark.parametrize("method", [aop.FFT_DF32, aop.FFT_FP32SPLIT])
+def test_walker_placement_bit_equal(ctx, method):
+    """Which warp of a CTA walks the recursion (all walkers of an SM on one
+    sub-partition, or spread over them) changes the schedule, not the
+    arithmetic: prices are bit-equal, and equal the oracle within tolerance."""
+    reqs = wl.random_small(24, seed=41, T_range=(200, 3000))
+    p0, s0 = ctx.price_batch(reqs, method=method)
+    p1, s1 = ctx.price_batch(reqs, method=method, flags=aop.FLAG_SPREAD_WALKERS)
+    assert (s0 == 0).all() and (s1 == 0).all()
+    assert np.array_equal(p0, p1)
+    for r, p in zip(reqs, p1):
+        ref = oracle.price_american(r.as_dict())
+        assert abs(p - ref) <= parity.price_tol(method, ref, r.K), (r, p, ref)
