@@ -27,19 +27,19 @@ extern "C" {
 #endif
 
 /* Lattice models.
- *   AOP_BINOMIAL_CALL  -- Sec. 3 (Fig. 1, Def. 2.1): (T+1)x(T+1) grid, row i
+ *   AOP_BINOMIAL_CALL  -- Sec. 2 (Fig. 1, Def. 2.1): (T+1)x(T+1) grid, row i
  *       holds columns j in [0, i] at price S0 u^{2j-i}, u = e^{sigma sqrt(dt)},
  *       dt = expiry/T; weights m(1-p) on G[i+1][j] and m p on G[i+1][j+1].
- *   AOP_TRINOMIAL_CALL -- Sec. 4 and its appendix: row i holds j in [0, 2i] at
+ *   AOP_TRINOMIAL_CALL -- Sec. 3 and its appendix: row i holds j in [0, 2i] at
  *       price S0 u^{j-i}; weights m p_d, m p_o, m p_u on G[i+1][j..j+2].
- *   AOP_BSM_PUT        -- Sec. 5: explicit finite differences for the
+ *   AOP_BSM_PUT        -- Sec. 4: explicit finite differences for the
  *       nondimensional Black-Scholes-Merton put (scheme bsmG) on the shrinking
  *       triangle k in [-(T-n), T-n], dtau = sigma^2 expiry/(2T),
  *       ds = sqrt(3 dtau), s_k = ln(S0/K) + k ds.  A dividend yield q (not in
  *       the paper) sets the first-derivative coefficient to 2(r-q)/sigma^2 - 1;
  *       the discount term keeps omega = 2r/sigma^2.
  *   AOP_BINOMIAL_PUT, AOP_TRINOMIAL_PUT -- the two lattices above with the
- *       put's exercise value K - S0 u^x (Sec. 3.1 states it; the paper's
+ *       put's exercise value K - S0 u^x (Sec. 2.1 states it; the paper's
  *       method is given for calls).  Priced exactly as the call of the
  *       mirrored lattice: spot K, strike S0, the put's weights times the
  *       child/parent price ratio, read right to left (lattice put-call
@@ -96,7 +96,7 @@ typedef enum {
     AOP_TRI_BOYLE = 0,  /* u = e^{lambda sigma sqrt(dt)}, probabilities matching
                            the first two moments (Boyle 1986); lambda <= 0
                            selects sqrt(3) */
-    AOP_TRI_PAPER = 1   /* Sec. 4: u = e^{sigma sqrt(2 dt)},
+    AOP_TRI_PAPER = 1   /* Sec. 3: u = e^{sigma sqrt(2 dt)},
                            p_u = ((e^{(r-q)dt/2} - u^{-1/2})/(u^{1/2}-u^{-1/2}))^2,
                            p_d = ((u^{1/2} - e^{(r-q)dt/2})/(u^{1/2}-u^{-1/2}))^2 */
 } aop_tri_form;
@@ -191,7 +191,7 @@ aop_status aop_ctx_create(aop_ctx **ctx, int device, size_t workspace_cap_bytes)
 /* Release every device resource of the context.  NULL is accepted. */
 aop_status aop_ctx_destroy(aop_ctx *ctx);
 
-/* Price one option (Sec. 3-5), synchronously, with the FP64 FFT method on
+/* Price one option (Sec. 2-4), synchronously, with the FP64 FFT method on
  * device 0 using an internal context.  *price_out in currency units. */
 aop_status price_american(int model, double S0, double K, double r, double q,
                           double sigma, double expiry, int64_t T, double *price_out);
@@ -209,7 +209,9 @@ aop_status price_american(int model, double S0, double K, double r, double q,
 aop_status price_american_ex(const aop_request *req, const aop_options *opt,
                              double *price_out, int32_t *boundary_out);
 
-/* Price n options given in host arrays; returns when prices[] and status[]
+/* Price n options given in host arrays (the trapezoidal divide-and-conquer of
+ * Sec. 2.3, the appendix TOPM algorithm and Sec. 4.3 per option, options
+ * independent); returns when prices[] and status[]
  * (both host, length n) are filled.  status may be NULL.  Returns AOP_OK when
  * the batch ran, even if individual options failed (see status[i]); a bad
  * option does not fail the batch.  Copies to and from the device happen inside
@@ -240,7 +242,9 @@ aop_status price_american_greeks_batch(aop_ctx *ctx, int64_t n, const aop_reques
                                        const aop_options *opt, double *prices, double *greeks,
                                        aop_status *status, void *stream);
 
-/* Device-resident batch: d_reqs (aop_request[n]), d_prices (double[n]) and
+/* Device-resident batch (the same computation as price_american_batch:
+ * Sec. 2.3, the appendix TOPM algorithm, Sec. 4.3): d_reqs (aop_request[n]),
+ * d_prices (double[n]) and
  * d_status (int32[n], nullable) are device pointers; enqueued on `stream`,
  * returns without waiting.  d_boundary (nullable) is a device int32 array and
  * d_boundary_offsets (device int64[n], required with d_boundary) gives the
@@ -252,7 +256,7 @@ aop_status price_american_batch_device(aop_ctx *ctx, int64_t n, const aop_reques
                                        const int64_t *d_boundary_offsets, void *stream);
 
 /* Linear advance of one row segment by h steps of a 2- or 3-point stencil
- * (the FFT-based linear-stencil step used inside every trapezoid, Sec. 3.3
+ * (the FFT-based linear-stencil step used inside every trapezoid, Sec. 2.3
  * "Solving a Trapezoid"): for count segments stored back to back in d_in
  * (count*W doubles, device), writes d_out (count*(W - (nw-1)h) doubles):
  *     out[x] = sum_{t=0}^{(nw-1)h} c_t in[x + t],
@@ -270,7 +274,8 @@ aop_status aop_ctx_get_stats(aop_ctx *ctx, aop_stats *out);
 /* European counterparts of the requests (no early exercise): the root value
  * as one T-step linear advance of the expiry payoff, i.e. one FFT convolution
  * with the T-fold power of the stencil evaluated at the root cell (the linear
- * part of the paper's method alone, Sec. 3 and P:1428-1437), in FP64 with the
+ * part of the paper's method alone: the appendix on European call options
+ * under the binomial model), in FP64 with the
  * node-price tilt so that the payoff row's range (up to e^{+-700}) costs no
  * accuracy.  Host arrays of n; per-request status (AOP_EINVAL also for
  * T > AOP_EUROPEAN_MAX_T).  The method of the context is not used: always

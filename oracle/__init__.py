@@ -5,10 +5,10 @@ CPU-baseline leg of ``bench.py`` may import this package.  It shares no code
 with the CUDA library and the library never imports it.
 
 The C source (``oracle.c``) is the plain definition the fast method must
-reproduce: Fig. 1's nested loop for the binomial call (Sec. 3.1, Def. 2.1), the
-trinomial call of Sec. 4 and its appendix, the same two lattices with the put's
+reproduce: Fig. 1's nested loop for the binomial call (Sec. 2.1, Def. 2.1), the
+trinomial call of Sec. 3 and its appendix, the same two lattices with the put's
 exercise value, and the explicit finite-difference scheme for the
-Black-Scholes-Merton put of Sec. 5 (with an optional dividend yield).  This
+Black-Scholes-Merton put of Sec. 4 (with an optional dividend yield).  This
 wrapper only marshals arguments through ctypes.
 
 Requests are plain mappings (or objects with attributes) with the fields
@@ -134,7 +134,7 @@ def columns(req) -> int:
 
 
 def params(req) -> dict:
-    """Lattice parameters (Sec. 3.1, Sec. 4, Sec. 5); raises on bad input."""
+    """Lattice parameters (Sec. 2.1, Sec. 3, Sec. 4); raises on bad input."""
     lib = _load()
     P = _Params()
     st = lib.or_params_compute(ctypes.byref(_to_c(req)), ctypes.byref(P))
@@ -227,7 +227,7 @@ def max_threads() -> int:
 
 def linear_advance(x, w, h: int):
     """The linear stencil of the continuation region applied h times (the
-    step each FFT convolution of Sec. 3.3 "Solving a Trapezoid" performs over
+    step each FFT convolution of Sec. 2.3 "Solving a Trapezoid" performs over
     the red cells): y_{k+1}[j] = sum_o w[o] y_k[j + o] for o = 0 .. len(w)-1,
     keeping the cells whose dependency cone lies inside the segment, so that a
     row of W cells yields W - (len(w) - 1) h cells.  Plain FP64 numpy, one

@@ -10,15 +10,15 @@
  *
  * What it computes (the plain definition the fast method must reproduce):
  *
- *   BOPM call  (Fig. 1; Sec. 3.1; Def. 2.1)
+ *   BOPM call  (Fig. 1; Sec. 2.1; Def. 2.1)
  *     dt = E/T, u = e^{V sqrt(dt)}, d = 1/u, p = (e^{(R-Y)dt} - d)/(u - d),
  *     m = e^{-R dt}; weight m(1-p) on the down child G[i+1][j] and m p on the
- *     up child G[i+1][j+1] (the reading of Sec. 3.1 under which the identity
+ *     up child G[i+1][j+1] (the reading of Sec. 2.1 under which the identity
  *     s0/u + s1 u = e^{-Y dt} in the proof of Lemma 2.2 holds);
  *     G[T][j] = max(0, S u^{2j-T} - K);
  *     G[i][j] = max(m(1-p) G[i+1][j] + m p G[i+1][j+1], S u^{2j-i} - K).
  *
- *   TOPM call  (Sec. 4; appendix, trinomial model)
+ *   TOPM call  (Sec. 3; appendix, trinomial model)
  *     weights m p_d, m p_o, m p_u on G[i+1][j], G[i+1][j+1], G[i+1][j+2],
  *     exercise S u^{j-i} - K, row i holds j in [0, 2i].
  *     form 1 (the paper's): u = e^{V sqrt(2 dt)},
@@ -31,11 +31,11 @@
  *       p_u u + p_o + p_d/u = e^{(R-Y)dt},
  *       p_u u^2 + p_o + p_d/u^2 = e^{(2(R-Y)+V^2)dt}.
  *
- *   BOPM put, TOPM put  (the exercise value of a put, Sec. 3.1)
+ *   BOPM put, TOPM put  (the exercise value of a put, Sec. 2.1)
  *     the same lattices, weights and rows as the calls, with exercise value
  *     K - S u^{2j-i} (binomial) or K - S u^{j-i} (trinomial).
  *
- *   BSM put  (Sec. 5, explicit scheme bsmG)
+ *   BSM put  (Sec. 4, explicit scheme bsmG)
  *     dtau = V^2 E/(2T), omega = 2R/V^2, ds = sqrt(3 dtau),
  *     a = dtau/ds^2 + (omega-1) dtau/(2 ds) on k+1,
  *     b = dtau/ds^2 - (omega-1) dtau/(2 ds) on k-1,
@@ -43,7 +43,7 @@
  *     s_k = ln(S/K) + k ds, v^0_k = max(1 - e^{s_k}, 0),
  *     v^{n+1}_k = max(a v^n_{k+1} + c v^n_k + b v^n_{k-1}, 1 - e^{s_k})
  *     on the shrinking triangle |k| <= T-n-1; price = K v^T_0.
- *     With a dividend yield Y (absent from the paper, whose Sec. 5 sets none):
+ *     With a dividend yield Y (absent from the paper, whose Sec. 4 sets none):
  *     the substitution that yields Sec. 5's nondimensional equation gives
  *     v_tau = v_ss + (omega_Y - 1) v_s - omega v with omega_Y = 2(R-Y)/V^2,
  *     so omega_Y replaces omega in the first-derivative term of a and b while
@@ -172,7 +172,7 @@ int or_params_compute(const or_req *q, or_params *P)
 
 /* exercise value table ex[k + T] for k in [-T, T]:
    calls: S u^k - K with u^k evaluated as e^{k log u} from the exact log u of
-   the model (Sec. 3.1: node price S u^{N_u - N_d}); lattice puts: K - S u^k;
+   the model (Sec. 2.1: node price S u^{N_u - N_d}); lattice puts: K - S u^k;
    BSM put: 1 - e^{ln(S/K) + k ds} (units of K). */
 static double *exercise_table(const or_req *q, const or_params *P)
 {

@@ -1,11 +1,11 @@
 // common.cuh -- device-side definitions shared by the pricer kernels.
 //
 // Lattice parameters follow the paper's models:
-//   binomial call   Sec. 3.1 and Fig. 1 (weights m(1-p) on G[i+1][j], m p on
+//   binomial call   Sec. 2.1 and Fig. 1 (weights m(1-p) on G[i+1][j], m p on
 //                   G[i+1][j+1]; node price S u^{2j-i})
-//   trinomial call  Sec. 4 and its appendix (weights m p_d, m p_o, m p_u on
+//   trinomial call  Sec. 3 and its appendix (weights m p_d, m p_o, m p_u on
 //                   G[i+1][j..j+2]; node price S u^{j-i})
-//   BSM put         Sec. 5, explicit scheme bsmG (weights b, c, a on k-1, k, k+1)
+//   BSM put         Sec. 4, explicit scheme bsmG (weights b, c, a on k-1, k, k+1)
 //   binomial and trinomial puts: priced as the call of the mirrored lattice
 //                   (make_params below), so every kernel sees a call
 #pragma once

@@ -3,7 +3,7 @@
 // One CTA prices one option at a time (persistent grid over a device queue of
 // options).  The recursion:
 //
-//   calls (binomial Sec. 3.3, trinomial appendix "Algorithm for American call
+//   calls (binomial Sec. 2.3, trinomial appendix "Algorithm for American call
 //   option pricing under TOPM"): a row's red cells are the columns [c0, b]
 //   (b = divider, Cor. 2.7); cells right of b are green and evaluated in
 //   closed form.  solve(i0, c0, b, h) advances rows i0 -> i0-h in two halves;
@@ -15,7 +15,7 @@
 //   red count of their first row ("Partitioning the Triangle into
 //   Trapezoids"); a leftover triangle is solved naively.
 //
-//   put (Sec. 5.3): green cells are left of the divider f, red cells right of
+//   put (Sec. 4.3): green cells are left of the divider f, red cells right of
 //   it.  region(n, lo, hi, f, h) advances the window [lo, hi] of row n to
 //   [lo+h, hi-h] of row n+h in two halves; each half recurses on the
 //   sub-trapezoid of base [f-2g, f+2g] around the divider ("trapezoid eglj"),

@@ -1,5 +1,5 @@
 // fft.cuh -- FFT convolution engine for the linear advance of a row segment
-// (the FFT-based linear-stencil step the trapezoid algorithm calls, Sec. 3.3
+// (the FFT-based linear-stencil step the trapezoid algorithm calls, Sec. 2.3
 // "Solving a Trapezoid", and the periodic-grid method it cites).
 //
 // A linear advance of h steps is a correlation of the row segment with the

@@ -1,6 +1,6 @@
 // stencil.cu -- the plain Theta(T^2) backward induction on the GPU (hot-path
 // row a8): Fig. 1's nested loop for the binomial call and its analogues for the
-// trinomial call (Sec. 4) and the BSM explicit scheme (Sec. 5, bsmG), with the
+// trinomial call (Sec. 3) and the BSM explicit scheme (Sec. 4, bsmG), with the
 // early-exercise max at every cell.
 //
 // Layout: per option an exercise table ex[k'] (k' in [0, 2T]) and two row

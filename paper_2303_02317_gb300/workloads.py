@@ -3,7 +3,7 @@
 This module holds no pricing arithmetic: it only draws option parameters (and
 arrival times) with fixed seeds so that the CUDA library, the tests and the
 CPU oracle all see identical inputs.  The paper itself uses one fixed option
-(Sec. 6, parameter values) and varies only the step count T; the other
+(Sec. 5, parameter values) and varies only the step count T; the other
 workloads below are synthetic option books with the parameter ranges of the
 benchmark configurations.
 
@@ -70,7 +70,7 @@ def fixed_bsm_put(T: int) -> Request:
 
 
 def paper_params(model: int, T: int) -> Request:
-    """The paper's experiment parameters (Sec. 6): E=252 days (252/365 yr),
+    """The paper's experiment parameters (Sec. 5): E=252 days (252/365 yr),
     K=130, S=127.62, R=0.00163, V=0.2, Y=0.0163 (BSM: Y=0)."""
     q = 0.0 if model == BSM_PUT else 0.0163
     lam = SQRT3 if model == TRINOMIAL_CALL else 0.0

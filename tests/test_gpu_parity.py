@@ -56,7 +56,7 @@ def _edge_cases():
         wl.Request(2, 100.0, 100.0, 1e-6, 0.0, 0.6, 3.0, 400),   # divider jumps at row 1
         wl.Request(2, 150.0, 50.0, 0.05, 0.0, 0.2, 1.0, 400),
         wl.Request(2, 50.0, 150.0, 0.08, 0.0, 0.2, 3.0, 400),
-        # the paper's experiment parameters (Sec. 6)
+        # the paper's experiment parameters (Sec. 5)
         wl.paper_params(0, 1000), wl.paper_params(1, 1000), wl.paper_params(2, 1000),
         wl.single_binomial_t2048(),
     ]

@@ -35,7 +35,7 @@ def _rand_req(model, T, rng, q_zero=False, tri_form=0, bsm_yield=False):
 # ---------------------------------------------------------------- brute force
 @pytest.mark.parametrize("seed", range(6))
 def test_bopm_matches_nonrecombining_tree(oracle_lib, seed):
-    """Fig. 1 lattice == every path of the binomial tree (Sec. 3.1)."""
+    """Fig. 1 lattice == every path of the binomial tree (Sec. 2.1)."""
     rng = np.random.default_rng(100 + seed)
     for T in (1, 2, 5, 11):
         req = _rand_req(0, T, rng)
@@ -50,7 +50,7 @@ def test_bopm_matches_nonrecombining_tree(oracle_lib, seed):
 
 @pytest.mark.parametrize("tri_form", [0, 1])
 def test_topm_matches_nonrecombining_tree(oracle_lib, tri_form):
-    """Trinomial lattice (Sec. 4) == every path of the trinomial tree."""
+    """Trinomial lattice (Sec. 3) == every path of the trinomial tree."""
     rng = np.random.default_rng(200 + tri_form)
     for T in (1, 3, 7):
         req = _rand_req(1, T, rng, tri_form=tri_form)
@@ -63,7 +63,7 @@ def test_topm_matches_nonrecombining_tree(oracle_lib, tri_form):
 
 
 def test_bsm_matches_nonrecombining_walk(oracle_lib):
-    """The explicit scheme (Sec. 5, bsmG) is a trinomial walk with weights
+    """The explicit scheme (Sec. 4, bsmG) is a trinomial walk with weights
     (b, c, a) on (k-1, k, k+1); enumerate every path."""
     rng = np.random.default_rng(300)
     for T in (1, 4, 7):
@@ -80,7 +80,7 @@ def test_bsm_matches_nonrecombining_walk(oracle_lib):
 
 # -------------------------------------------------------------- closed forms
 def test_weight_identities(oracle_lib):
-    """Sec. 3 (proof of Lemma 2.2): s0/u + s1 u = e^{-Y dt}; the same
+    """Sec. 2 (proof of Lemma 2.2): s0/u + s1 u = e^{-Y dt}; the same
     martingale identity m (p_d/u + p_o + p_u u) = e^{-Y dt} for both
     trinomial forms; BSM: c = 1 - a - b - omega dtau with a + b = 2/3."""
     rng = np.random.default_rng(11)
@@ -194,7 +194,7 @@ def _call_checks(oracle_lib, req):
         assert min(bnd[i + 1] - 1, D * i) <= bnd[i] <= bnd[i + 1], (i, bnd[i], bnd[i + 1])
     for i in range(T + 1):
         row = g[i, : D * i + 1]
-        # hidden lemma of Sec. 3.2 (trinomial: row monotone): non-decreasing rows
+        # hidden lemma of Sec. 2.2 (trinomial: row monotone): non-decreasing rows
         assert np.all(np.diff(row) >= -1e-12 * max(1.0, np.max(np.abs(row))))
         # red cells left of the divider, green (== exercise) right of it
         k = np.arange(D * i + 1)
@@ -536,7 +536,7 @@ def test_american_greeks_satisfy_the_pde_at_the_root(oracle_lib):
         assert abs(res) < 3e-3 * req["r"] * v, (model, res, v)
 
 
-# ------------------------------------------------ the linear advance (Sec. 3.3)
+# ------------------------------------------------ the linear advance (Sec. 2.3)
 
 def _unit_response(oracle, w, h, W):
     """Row of the h-step advance's kernel: the advance of unit rows e_j."""
