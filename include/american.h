@@ -261,8 +261,10 @@ aop_status price_american_batch_device(aop_ctx *ctx, int64_t n, const aop_reques
  * (count*W doubles, device), writes d_out (count*(W - (nw-1)h) doubles):
  *     out[x] = sum_{t=0}^{(nw-1)h} c_t in[x + t],
  * where c is the h-fold self-convolution of the weights w[0..nw-1].
- * method selects AOP_FFT_FP64 or AOP_FFT_FP32SPLIT.  Synchronous.
- * Requires 1 <= nw-1, (nw-1)h < W <= 2^20. */
+ * method selects AOP_FFT_FP64, AOP_FFT_FP32SPLIT or AOP_FFT_DF32.
+ * Synchronous.  Requires 1 <= nw-1, (nw-1)h < W <= 2^20 (else AOP_EINVAL).
+ * AOP_ETIMEOUT when a bounded device-side wait gave up; the segments it hit
+ * are then NaN. */
 aop_status aop_linear_advance_device(aop_ctx *ctx, int method, int nw, const double *w,
                                      int64_t count, int64_t W, int64_t h,
                                      const double *d_in, double *d_out, void *stream);
@@ -356,9 +358,13 @@ aop_status aop_ctx_autotune(aop_ctx *ctx, int64_t n, const aop_request *reqs, in
  * device.
  *
  * Limits: 2 <= W <= AOP_NOALLOC_MAX_W, otherwise AOP_EINVAL (use
- * aop_linear_advance_device for wider segments).  The first call on a device
- * looks up the array's device address and fills its twiddle tables, and waits
- * for that on `stream`; make that first call before any stream capture.  All
+ * aop_linear_advance_device for wider segments).  The first call in a CUDA
+ * context (per device; again after cudaDeviceReset or any other re-creation
+ * of the context, which the call detects by the context's id) looks up the
+ * array's device address and fills its twiddle tables, and waits for that on
+ * `stream`; make that first call before any stream capture.  Device-side
+ * failures are not returned: a segment whose bounded device wait gave up is
+ * written as NaN.  All
  * calls share the one array: calls whose kernels overlap on the GPU (other
  * streams, other host threads) race and must be serialised by the caller.
  * Nothing is allocated or freed by this call. */

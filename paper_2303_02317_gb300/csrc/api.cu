@@ -509,10 +509,13 @@ aop_status aop_linear_advance_device(aop_ctx *c, int method, int nw, const doubl
     st = ensure(&c->ws, &c->ws_size, need, c->cap);
     if (st) return st;
     const void *tw = (method == AOP_FFT_FP64) ? c->tw64 : c->tw32;
+    CK(cudaMemsetAsync(c->d_err, 0, sizeof(int), s));
     CK(run_linear_advance(method, nw, w, count, W, h, d_in, d_out, tw, c->tw_log2, c->ws, c->ws_size,
                           c->d_err, s));
+    int err = 0;
+    CK(cudaMemcpyAsync(&err, c->d_err, sizeof(int), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
-    return AOP_OK;
+    return err ? (aop_status)err : AOP_OK;
 }
 
 aop_status aop_ctx_get_option_times(aop_ctx *c, int64_t n, int64_t *ns_out) {

@@ -38,6 +38,8 @@
 #include <cstring>
 #include <mutex>
 
+#include <cuda.h>
+
 #include "common.cuh"
 #include "fft.cuh"
 #include "internal.h"
@@ -2280,10 +2282,22 @@ __global__ void __launch_bounds__(kThreadsA) advance_kernel(const __grid_constan
     }
     __syncthreads();
     const int64_t nout = W - (int64_t)(P0.nw - 1) * h;
-    for (int64_t s = blockIdx.x; s < count; s += gridDim.x) {
+    int64_t s = blockIdx.x;
+    for (; s < count; s += gridDim.x) {
         Buf bi{const_cast<double *>(in) + s * W, 0};
         Buf bo{out + s * nout, 0};
         c.template conv<fft::BlockGroup, StoreF64<MODE>>(bi, 0, W - 1, bo, h, tile, a.lg_block, c.scratch(0), cnt);
+        __syncthreads();
+        if (S.err) break;
+    }
+    // A bounded wait gave up (AOP_ETIMEOUT): this segment and the block's
+    // remaining ones become NaN, and the status goes to the caller's error
+    // word when there is one.
+    if (S.err) {
+        const double nan = __longlong_as_double(0x7ff8000000000000ll);
+        for (; s < count; s += gridDim.x)
+            for (int64_t j = threadIdx.x; j < nout; j += blockDim.x) out[s * nout + j] = nan;
+        if (a.err && threadIdx.x == 0) atomicCAS(a.err, 0, S.err);
     }
 }
 
@@ -2477,14 +2491,42 @@ constexpr int64_t kNoAllocBytes = kNoAllocTw64Off + kNoAllocTwEntries * 16;
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
 
-// device address of the array, looked up once per device (host code may not
-// use the array's name as a device pointer)
+// device address of the array, looked up once per CUDA context on each device
+// (host code may not use the array's name as a device pointer).  A reset
+// device comes back with a new context whose copy of the array is zeroed and
+// may sit elsewhere: the context's id, unique for the life of the process,
+// tells the set-up to run again.
 struct NoAllocDevice {
     bool ready;
+    unsigned long long ctx_id;
     char *base;
 };
 std::mutex g_noalloc_mu;
 NoAllocDevice g_noalloc_dev[64];
+
+// id of the calling thread's current context through the driver's entry
+// points (the library links the runtime only); false if unavailable
+bool current_ctx_id(unsigned long long *id) {
+    typedef CUresult (*GetCurrent)(CUcontext *);
+    typedef CUresult (*GetId)(CUcontext, unsigned long long *);
+    static GetCurrent get_current = nullptr;
+    static GetId get_id = nullptr;
+    if (!get_current || !get_id) {
+        void *f1 = nullptr, *f2 = nullptr;
+        cudaDriverEntryPointQueryResult q1, q2;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f1, 12000, cudaEnableDefault, &q1) != cudaSuccess ||
+            cudaGetDriverEntryPointByVersion("cuCtxGetId", &f2, 12000, cudaEnableDefault, &q2) != cudaSuccess ||
+            q1 != cudaDriverEntryPointSuccess || q2 != cudaDriverEntryPointSuccess || !f1 || !f2) {
+            cudaGetLastError();
+            return false;
+        }
+        get_current = (GetCurrent)f1;
+        get_id = (GetId)f2;
+    }
+    CUcontext ctx = nullptr;
+    if (get_current(&ctx) != CUDA_SUCCESS || !ctx) return false;
+    return get_id(ctx, id) == CUDA_SUCCESS;
+}
 
 }  // namespace
 
@@ -2506,19 +2548,25 @@ extern "C" aop_status aop_linear_advance_noalloc(int method, int nw, const doubl
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) { cudaGetLastError(); return AOP_ECUDA; }
     char *base = nullptr;
     {
+        // the array's address in the current context (this also binds the
+        // runtime's context to the thread), then that context's id
+        void *ptr = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+        if (e != cudaSuccess || !ptr) { cudaGetLastError(); return AOP_ECUDA; }
+        unsigned long long ctx_id = 0;
+        if (!current_ctx_id(&ctx_id)) return AOP_ECUDA;
         std::lock_guard<std::mutex> lk(g_noalloc_mu);
         NoAllocDevice &D = g_noalloc_dev[dev];
-        if (!D.ready) {
-            // one-time set-up on this device: find the array and fill the
-            // twiddle tables it holds (nothing is allocated)
-            void *ptr = nullptr;
-            cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
-            if (e != cudaSuccess || !ptr) { cudaGetLastError(); return AOP_ECUDA; }
+        if (!D.ready || D.ctx_id != ctx_id || D.base != (char *)ptr) {
+            // set-up once per context on this device: fill the twiddle tables
+            // the array holds (nothing is allocated)
+            D.ready = false;
             char *b = (char *)ptr;
             e = launch_twiddles(kNoAllocTwLog2, b + kNoAllocTw32Off, b + kNoAllocTw64Off, s);
             if (e == cudaSuccess) e = cudaStreamSynchronize(s);
             if (e != cudaSuccess) { cudaGetLastError(); return AOP_ECUDA; }
             D.base = b;
+            D.ctx_id = ctx_id;
             D.ready = true;
         }
         base = D.base;

@@ -16,14 +16,16 @@ pytestmark = pytest.mark.gpu
 
 
 @pytest.mark.parametrize("method", [aop.FFT_FP64, aop.FFT_FP32SPLIT], ids=["fft64", "fft32"])
-def test_noalloc_matches_context_entry_point(method):
+def test_noalloc_matches_context_entry_point(method, oracle_lib):
+    """Two calls in a row: the widest segment the entry point takes, in more
+    segments than it runs CTAs (40 > 16), then a short binomial one; each
+    against the context entry point and the oracle's plain stencil loop."""
     torch = pytest.importorskip("torch")
     assert torch.cuda.is_available(), "GPU tests need a CUDA device"
     torch.cuda.set_device(0)
     stream = torch.cuda.Stream()
     with aop.Context(0) as ctx:
-        # two calls in a row with different shapes and weights
-        for call, (nw, W, h, count) in enumerate([(3, 12000, 2500, 5), (2, 700, 90, 3)]):
+        for call, (nw, W, h, count) in enumerate([(3, aop.NOALLOC_MAX_W, 300, 40), (2, 700, 90, 3)]):
             rng = np.random.default_rng(1000 + 17 * call + method)
             w = rng.uniform(0.2, 1.0, nw)
             w = list(w / w.sum() * 0.999)
@@ -32,7 +34,9 @@ def test_noalloc_matches_context_entry_point(method):
             dx = torch.tensor(x, dtype=torch.float64, device="cuda")
             ref = torch.full((count, nout), float("nan"), dtype=torch.float64, device="cuda")
             got = torch.full((count, nout), float("nan"), dtype=torch.float64, device="cuda")
+            torch.cuda.synchronize()
             ctx.linear_advance_device(method, w, count, W, h, dx.data_ptr(), ref.data_ptr())
+            stream.wait_stream(torch.cuda.current_stream())
             aop.linear_advance_noalloc(method, w, count, W, h, dx.data_ptr(), got.data_ptr(),
                                        stream=stream.cuda_stream)
             stream.synchronize()
@@ -41,6 +45,8 @@ def test_noalloc_matches_context_entry_point(method):
             scale = np.abs(x).max()
             tol = 1e-12 * scale if method == aop.FFT_FP64 else 1e-6 * scale
             assert np.abs(g - r).max() <= tol
+            want = oracle_lib.linear_advance(x, w, h)
+            assert np.abs(g - want).max() <= tol
 
 
 def test_noalloc_rejects_oversize():
