@@ -42,11 +42,9 @@ if ROOT not in sys.path:
 
 T_BENCH = 1 << 17
 N_BINOMIAL = N_TRINOMIAL = 256
-FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12     # SMs x FP32 lanes x FMA x max clock
-FP64_PEAK_TFLOPS = 1.25                              # GB300 dense FP64 (vendor figure)
-# FP64 FMA rate measured on this GPU: one warp instruction per 64 cycles per SM
-# sub-partition whatever the active lanes -> 152 x 4 x 32 / 64 x 2 flop x 2.07 GHz
-FP64_MEASURED_TFLOPS = 152 * 4 * 32 / 64 * 2 * 2.07e9 / 1e12
+# FMA rates of the FP32 and FP64 pipes (TFLOP/s), measured live on the
+# bench's GPU by aop_measure_fma_peak after the timed region
+MEASURED_ALU = {}
 WORKLOAD = "precision_sweep_T131072_256binomial_256trinomial"
 
 # DRAM traffic of one launch of the pricing kernel on this book, from one
@@ -291,10 +289,11 @@ def stencil_sample(ctx, aop, sarr, m, p_ref, local, reqs=None):
         fl = stencil_flops(reqs)
         ach = fl / (ms / 1e3) / 1e12
         if m == aop.STENCIL_FP64:
-            peak, src = FP64_MEASURED_TFLOPS, "FP64 peak measured: one warp FMA per 64 cycles per SM sub-partition"
+            peak, src = MEASURED_ALU["fp64"], "FP64 FMA rate measured live by aop_measure_fma_peak (of measured)"
         else:
-            peak, src = FP32_PEAK_TFLOPS, ("FP32 peak derived from unit counts; a doubled-FP32 cell costs "
-                                           "about 25 FP32 instructions for its 3-5 algorithmic flops")
+            peak, src = MEASURED_ALU["fp32"], ("FP32 FMA rate measured live by aop_measure_fma_peak (of measured); "
+                                               "a doubled-FP32 cell costs about 25 FP32 instructions for its "
+                                               "3-5 algorithmic flops")
         out["roofline"] = {"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
                            "flops": fl, "peak_source": src}
     return out
@@ -597,6 +596,11 @@ def main():
             dist.barrier()
         return
 
+    # ---- measured FMA rates of the FP32 and FP64 pipes (roofline denominators)
+    MEASURED_ALU["fp32"] = aop.measure_fma_peak(32, local) / 1e12
+    MEASURED_ALU["fp64"] = aop.measure_fma_peak(64, local) / 1e12
+    fp32_peak_tflops, fp64_peak_tflops = MEASURED_ALU["fp32"], MEASURED_ALU["fp64"]
+
     # ---- accuracy against the FP64 FFT pricer (untimed)
     def accuracy(p, ref, ok):
         if int((~np.isfinite(p)).sum()):
@@ -656,22 +660,45 @@ def main():
         if cands:
             fair = min(cands, key=lambda c: c[0])
 
-    # ---- roofline of the pricing kernel: FFT flops (FP32 or FP64) over time
-    flops = stats["fft_flops"]
+    # ---- roofline of the pricing kernel: two terms, the binding one reported.
+    # Algorithmic work per launch (kernel counters): every convolution reads
+    # its input window and writes its output window once, 8 bytes a cell (FP64
+    # or an FP32 pair); its flops are 5 N log2 N for a real convolution of
+    # length N (the 16-byte modes transform the real row) and 10 N log2 N for
+    # the FP32-split packed complex one.  The counter fft_flops holds
+    # 5 N log2 N per transform, forward and inverse.
     peaks = _peaks()
     kern_s = kms / 1e3
-    if method in (aop.FFT_FP32SPLIT, aop.FFT_DF32):
-        peak = FP32_PEAK_TFLOPS
-        note = ("FP32 peak derived: 152 SMs x 128 lanes x 2 flop x 2.07 GHz; achieved counts the "
-                "transforms' 5 N log2 N flops (a doubled-FP32 flop costs several FP32 instructions)")
+    alg_bytes = 8.0 * (stats["conv_inputs"] + stats["conv_outputs"])
+    alg_flops = stats["fft_flops"] / (1.0 if method == aop.FFT_FP32SPLIT else 2.0)
+    hbm_peak = peaks.get("hbm_gbs")
+    hbm_src = "MEASURED_PEAKS.json hbm_gbs (of measured)"
+    if not hbm_peak:
+        hbm_peak, hbm_src = 6800.0, "profiling recipe fallback (of fallback)"
+    if method == aop.FFT_FP64:
+        alu_peak, alu_src = fp64_peak_tflops, "FP64 FMA rate measured live by aop_measure_fma_peak (of measured)"
     else:
-        peak = FP64_PEAK_TFLOPS
-        note = "FP64 peak: vendor dense FP64 figure"
-    achieved = flops / kern_s / 1e12
-    roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-            "frac": achieved / peak, "traffic": captured_traffic(args.method), "kernel": "dnc_kernel",
-            "per_launch_flops": flops, "kernel_ms": kms, "peak_source": note,
-            "hbm_gbs_measured": peaks.get("hbm_gbs")}
+        alu_peak, alu_src = fp32_peak_tflops, "FP32 FMA rate measured live by aop_measure_fma_peak (of measured)"
+    hbm_ach = alg_bytes / kern_s / 1e9
+    alu_ach = alg_flops / kern_s / 1e12
+    hbm_frac = hbm_ach / hbm_peak
+    alu_frac = alu_ach / alu_peak
+    traffic = captured_traffic(args.method)
+    if hbm_frac >= alu_frac:
+        roof = {"bound": "hbm", "achieved": hbm_ach, "peak": hbm_peak, "unit": "GB/s", "frac": hbm_frac,
+                "peak_source": hbm_src}
+    else:
+        roof = {"bound": "alu", "achieved": alu_ach, "peak": alu_peak, "unit": "TFLOP/s", "frac": alu_frac,
+                "peak_source": alu_src}
+    roof.update({"traffic": traffic, "kernel": "dnc_kernel", "kernel_ms": kms,
+                 "hbm_frac": hbm_frac, "alu_frac": alu_frac,
+                 "hbm": {"algorithmic_bytes": alg_bytes, "achieved_gbs": hbm_ach, "peak_gbs": hbm_peak,
+                         "ms_at_peak": alg_bytes / hbm_peak / 1e6, "peak_source": hbm_src},
+                 "alu": {"algorithmic_flops": alg_flops, "achieved_tflops": alu_ach, "peak_tflops": alu_peak,
+                         "ms_at_peak": alg_flops / alu_peak / 1e9, "peak_source": alu_src},
+                 "traffic_ratio": (traffic / alg_bytes) if traffic else None,
+                 "count": "bytes: 8 B x (conv_inputs + conv_outputs); flops: 5 N log2 N per real "
+                          "convolution (16-byte modes), 10 N log2 N per packed complex one (FP32 split)"})
 
     # ---- CPU oracle baseline on a bounded sample
     cpu = None

@@ -307,6 +307,18 @@ aop_status price_european_batch(aop_ctx *ctx, int64_t n, const aop_request *reqs
  * AOP_ENOMEM, AOP_ECUDA. */
 typedef struct aop_server aop_server;
 
+/* Device workspace (bytes) that a context's cap must allow for
+ * options_in_flight options of up to T_max steps priced at once with a D&C
+ * method (AOP_FFT_FP64, AOP_FFT_FP32SPLIT, AOP_FFT_DF32) and base-case height
+ * base_case (0 = the library default): the per-option scratch of the
+ * divide-and-conquer (current row, per-depth rows, transform scratch, kernel
+ * powers) times the count, plus the launch's queue words.  Admission: a
+ * serving session on a context created with this cap holds options_in_flight
+ * slots for requests up to T_max.  Host-only arithmetic; AOP_EINVAL for a
+ * plain stencil method or bad sizes. */
+aop_status aop_workspace_bytes(int method, int64_t T_max, int base_case, int64_t options_in_flight,
+                               size_t *bytes_out);
+
 /* Start a session on ctx for at most `capacity` requests of up to T_max steps,
  * priced with *opt (method, base case, flags, options per SM; NULL = FFT_FP64
  * defaults). */
@@ -378,6 +390,15 @@ aop_status aop_linear_advance_noalloc(int method, int nw, const double *w, int64
  * AOP_FLAG_OPTION_TIMES; ns_out is a host array of n <= batch size entries.
  * Synchronizes the context.  AOP_EINVAL if the last batch did not record them. */
 aop_status aop_ctx_get_option_times(aop_ctx *ctx, int64_t n, int64_t *ns_out);
+
+/* Measured FMA throughput of device `device` (flop/s, two per FMA) for
+ * bits = 32 (FP32 pipe) or 64 (FP64 pipe): eight independent FMA chains per
+ * thread over 8 CTAs of 256 threads per SM, timed with CUDA events, best of
+ * three runs after one warm-up (about 0.1 s each).  A diagnostic for the
+ * roofline of the pricer's kernels (the paper has no counterpart).  Blocks
+ * the calling thread; AOP_EINVAL for other widths, AOP_ECUDA without a
+ * device. */
+aop_status aop_measure_fma_peak(int device, int bits, double *flops_per_s);
 
 /* Library version string. */
 const char *aop_version(void);

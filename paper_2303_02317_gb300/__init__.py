@@ -116,11 +116,14 @@ def load(path: Optional[str] = None):
         lib.aop_linear_advance_noalloc.argtypes = [ctypes.c_int, ctypes.c_int, vp, i64, i64, i64,
                                                    vp, vp, vp]
         lib.aop_linear_advance_noalloc.restype = ctypes.c_int
+        lib.aop_measure_fma_peak.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.POINTER(dbl)]
+        lib.aop_workspace_bytes.argtypes = [ctypes.c_int, i64, ctypes.c_int, i64, ctypes.POINTER(ctypes.c_size_t)]
         for f in ("aop_ctx_get_option_times", "aop_ctx_create", "aop_ctx_destroy", "price_american", "price_american_ex",
                   "price_american_batch", "price_american_batch_device", "price_american_greeks_batch",
                   "aop_linear_advance_device", "aop_ctx_get_stats", "aop_ctx_autotune",
                   "aop_server_create", "aop_server_submit", "aop_server_poll", "aop_server_serve_stream",
-                  "aop_server_info", "aop_server_destroy", "price_european_batch"):
+                  "aop_server_info", "aop_server_destroy", "price_european_batch", "aop_workspace_bytes",
+                  "aop_measure_fma_peak"):
             getattr(lib, f).restype = ctypes.c_int
         _lib = lib
         return lib
@@ -194,6 +197,24 @@ def price_american_ex(req, method: int = FFT_FP64, base_case: int = 0, boundary:
 
 
 NOALLOC_MAX_W = 16384
+
+
+def measure_fma_peak(bits: int = 32, device: int = 0) -> float:
+    """C: aop_measure_fma_peak -- measured FMA rate (flop/s) of the FP32
+    (bits=32) or FP64 (bits=64) pipe of the device."""
+    out = ctypes.c_double()
+    _check(load().aop_measure_fma_peak(int(device), int(bits), ctypes.byref(out)), "aop_measure_fma_peak")
+    return float(out.value)
+
+
+def workspace_bytes(method: int, T_max: int, options_in_flight: int, base_case: int = 0) -> int:
+    """C: aop_workspace_bytes -- the workspace cap that holds options_in_flight
+    options of up to T_max steps at once (host arithmetic, no device needed)."""
+    out = ctypes.c_size_t()
+    _check(load().aop_workspace_bytes(int(method), ctypes.c_int64(int(T_max)), int(base_case),
+                                      ctypes.c_int64(int(options_in_flight)), ctypes.byref(out)),
+           "aop_workspace_bytes")
+    return int(out.value)
 
 
 def linear_advance_noalloc(method: int, w: Sequence[float], count: int, W: int, h: int,

@@ -626,7 +626,10 @@ aop_status aop_server_create(aop_ctx *c, int64_t capacity, int64_t T_max, const 
     size_t need = dnc_workspace_bytes(method, capacity, T_max, s->B, s->cap, &grid, c->device);
     if (c->cap && need > c->cap) need = c->cap;     // admission: the slots the cap holds
     if ((st = ensure(&c->ws, &c->ws_size, need, c->cap))) return fail(st);
-    s->slots = grid;
+    // the slots the workspace holds (the launch clips its grid the same way)
+    const size_t stride = dnc_slot_bytes(method, T_max, s->B);
+    if (c->ws_size < stride + 8192) return fail(AOP_ENOMEM);
+    s->slots = (int)std::min<int64_t>(grid, (int64_t)((c->ws_size - 8192) / stride));
     const size_t per = sizeof(aop_request) + sizeof(double) + 2 * sizeof(int32_t);
     char *h = nullptr;
     if (cudaHostAlloc((void **)&h, (size_t)capacity * per + 256, cudaHostAllocMapped | cudaHostAllocPortable) !=
@@ -729,6 +732,16 @@ aop_status aop_server_serve_stream(aop_server *s, int64_t n, const aop_request *
         if (status) status[i] = (aop_status)s->h_status[base + i];
         if (latency_ns) latency_ns[i] = t_done[(size_t)i] - (t0 + arrival_ns[i]);
     }
+    return AOP_OK;
+}
+
+aop_status aop_workspace_bytes(int method, int64_t T_max, int base_case, int64_t options_in_flight,
+                               size_t *bytes_out) {
+    if (!bytes_out || T_max < 1 || T_max > AOP_MAX_T || options_in_flight < 1 || base_case < 0) return AOP_EINVAL;
+    if (method < 0 || method > 3 || method == AOP_STENCIL_FP64) return AOP_EINVAL;   // D&C only
+    aop_options o{method, base_case, 0, 0};
+    const int B = resolve_base_case(nullptr, &o);
+    *bytes_out = dnc_slot_bytes(method, T_max, B) * (size_t)options_in_flight + 8192;
     return AOP_OK;
 }
 

@@ -2169,6 +2169,11 @@ int64_t dnc_grid(int method, int64_t n, size_t smem, int cap, int device) {
     return std::min<int64_t>(n, (int64_t)sm_count(device) * dnc_per_sm(method, n, smem, cap, device));
 }
 
+size_t dnc_slot_bytes(int method, int64_t T_max, int base_case)
+{
+    return (size_t)make_layout(method, T_max, base_case, shape_big(method)).stride;
+}
+
 size_t dnc_workspace_bytes(int method, int64_t n, int64_t T_max, int base_case, int cap, int *grid_out, int device)
 {
     Layout L = make_layout(method, T_max, base_case, shape_big(method));

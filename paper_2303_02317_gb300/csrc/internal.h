@@ -50,6 +50,9 @@ cudaError_t run_stencil(int64_t n, const Params *d_params, int64_t T_max, void *
 
 // dnc.cu -- trapezoidal divide-and-conquer pricer
 int dnc_max_per_sm(int method, int64_t T_max, int base_case);
+// per-option workspace of the pricing kernel (one slot), without the
+// launch's 8 KiB of queue words
+size_t dnc_slot_bytes(int method, int64_t T_max, int base_case);
 size_t dnc_workspace_bytes(int method, int64_t n, int64_t T_max, int base_case, int cap, int *grid_out,
                            int device);
 // A serving session's host-shared state (see aop_server_* in the header):

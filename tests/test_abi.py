@@ -52,3 +52,16 @@ def test_no_device_is_an_error_not_a_fallback(lib):
     assert ei.value.code == 4   # AOP_ECUDA
     with pytest.raises(aop.AopError):
         aop.price_american(0, 100, 100, 0.05, 0.03, 0.2, 1.0, 64)
+
+
+def test_workspace_bytes_is_host_arithmetic(lib):
+    """aop_workspace_bytes needs no device: per-slot bytes times the count
+    plus the launch's queue words; larger T needs more; stencils refused."""
+    one = aop.workspace_bytes(aop.FFT_DF32, 1 << 13, 1)
+    four = aop.workspace_bytes(aop.FFT_DF32, 1 << 13, 4)
+    assert four - 8192 == 4 * (one - 8192) and one > 8192
+    assert aop.workspace_bytes(aop.FFT_DF32, 1 << 17, 1) > one
+    with pytest.raises(aop.AopError):
+        aop.workspace_bytes(aop.STENCIL_FP64, 1 << 13, 1)
+    with pytest.raises(aop.AopError):
+        aop.workspace_bytes(aop.FFT_FP64, 0, 1)

@@ -108,6 +108,33 @@ def test_configs_mid_size(ctx, method, T):
         _check(r, method)
 
 
+_ORACLE_2_16 = {}
+
+
+def _oracle_full(req):
+    """Oracle price, dividers and margins on all host cores, once per request."""
+    key = tuple(sorted(req.items()))
+    if key not in _ORACLE_2_16:
+        _ORACLE_2_16[key] = oracle.price_american(req, nthreads=0, with_boundary=True, with_margin=True)
+    return _ORACLE_2_16[key]
+
+
+@pytest.mark.parametrize("method", METHODS, ids=[MNAME[m] for m in METHODS])
+def test_configs_at_2_16(ctx, method):
+    """The benchmark's fixed-parameter sets at T = 2^16, the largest size at
+    which the oracle is the reference: binomial, trinomial (Boyle and the
+    paper's form) and the BSM put; price and every row's divider."""
+    T = 1 << 16
+    for r in (wl.fixed_call(0, T), wl.fixed_call(1, T), wl.fixed_call(1, T, wl.TRI_PAPER), wl.fixed_bsm_put(T)):
+        d = r.as_dict()
+        ref, bref, margin = _oracle_full(d)
+        got, b = aop.price_american_ex(d, method=method, boundary=True)
+        tol = parity.price_tol(method, ref, d["K"])
+        assert abs(got - ref) <= tol, (MNAME[method], d, got, ref, abs(got - ref), tol)
+        bad, _ = parity.check_boundary(method, d, b, bref, margin)
+        assert not bad, (MNAME[method], d, "rows", bad[:8])
+
+
 @pytest.mark.parametrize("method", METHODS, ids=[MNAME[m] for m in METHODS])
 def test_extreme_parameters(ctx, method):
     """Corners of the benchmark parameter box at T = 8192: the widest lattices

@@ -51,6 +51,31 @@ def test_stream_matches_alone(ctx, method):
         assert abs(p - ref) <= parity.price_tol(method, ref, r.K), (r, p, ref)
 
 
+@pytest.mark.parametrize("method", [aop.FFT_DF32, aop.FFT_FP32SPLIT], ids=["df32", "fft32"])
+def test_freed_slots_take_new_requests(method):
+    """A workspace cap that holds four options at T = 2^13 and 96 requests
+    arriving faster than four slots price them: requests wait for a slot and
+    are admitted into slots as they free.  Every price equals the same
+    request priced alone, bit for bit."""
+    torch = pytest.importorskip("torch")
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    T_max = 1 << 13
+    cap = aop.workspace_bytes(method, T_max, 4, base_case=31)
+    reqs, arrivals = _stream(96, 41, 5e-5, (200, T_max))
+    with aop.Context(0, workspace_cap_bytes=cap) as c:
+        with aop.Server(c, capacity=96, T_max=T_max, method=method, base_case=31) as srv:
+            assert 1 <= srv.info()["slots"] <= 4
+            prices, status, lat = srv.serve_stream(reqs, arrivals, timeout_s=300.0)
+        assert (status == 0).all(), status
+        alone = np.array([c.price_batch([r], method=method, base_case=31)[0][0] for r in reqs])
+    assert np.array_equal(prices, alone), np.max(np.abs(prices - alone))
+    # at some arrival more requests were outstanding than there are slots, so
+    # some waited and were admitted into a slot freed by another
+    done = arrivals + lat
+    outstanding = max(int(np.sum((arrivals <= t) & (done > t))) for t in arrivals)
+    assert outstanding > 4, outstanding
+
+
 def test_submit_poll_and_idle_relaunch(ctx):
     """Requests submitted one at a time are priced; after more than the
     kernel's 2 s idle limit the next request relaunches it."""
