@@ -253,24 +253,39 @@ def cpu_oracle_sample(reqs, n_sample, budget_s=25.0):
     return len(done) / dt, dt, threads, desc, done, prices
 
 
-def stencil_flops(reqs) -> float:
-    """Algorithmic flops of the plain backward induction over the requests:
-    (D+1) products and D sums per cell, T(T+1)/2 cells for the binomial
-    lattice, T^2 for the trinomial one and the BSM grid."""
-    tot = 0.0
-    for r in reqs:
-        T = float(r.T)
-        if r.model in (0, 3):
-            tot += 3.0 * T * (T + 1) / 2
-        else:
-            tot += 5.0 * T * T
-    return tot
+def max_rel_floor(p_ref, p, ok, reqs, floor=1e-3):
+    """Largest relative distance over the options priced at or above
+    floor x K (the relative error of a near-zero price says nothing; those
+    options are covered by the absolute distance over K)."""
+    K = np.array([r.K for r in reqs])
+    sel = ok & (np.abs(p_ref) >= floor * K)
+    if not sel.any():
+        return None
+    return float(np.max(np.abs(p_ref[sel] - p[sel]) / np.abs(p_ref[sel])))
 
 
-def stencil_sample(ctx, aop, sarr, m, p_ref, local, reqs=None):
+def lattice_cells(r) -> float:
+    """Cells the plain backward induction updates for one request: rows
+    T-1 .. 0 of the binomial lattice hold i+1 cells (T(T+1)/2 in all), of the
+    trinomial one 2i+1 (T^2); the BSM grid's rows 1 .. T hold 2(T-n)+1 (T^2)."""
+    T = float(r.T)
+    return T * (T + 1) / 2 if r.model in (0, 3) else T * T
+
+
+# Instructions per cell of the plain stencil on the pipe that bounds it,
+# counted from its source: the doubled-FP32 stencil sum (19 FP32 operations for
+# two terms, 31 for three: exact products through FMA, two-sums, one
+# renormalisation) and the max (compare and select, about 5); the FP64 stencil
+# one FP64 multiply and one FMA per extra term, and the compare.
+STENCIL_INSTR = {"df32": {2: 24.0, 3: 36.0}, "fp64": {2: 3.0, 3: 4.0}}
+
+
+def stencil_sample(ctx, aop, sarr, m, p_ref, local, reqs):
     """Price a sample of the book with the plain stencil method m: ms/option,
-    cells/s, its ALU roofline, energy and the largest relative distance to the
-    FP64 D&C prices p_ref of the same options."""
+    lattice cells/s, its roofline on the pipe that bounds it (instruction
+    issue of the FP32 or FP64 pipe at the measured FMA rate), energy and the
+    largest relative distance to the FP64 D&C prices p_ref of the same
+    options."""
     meter = EnergyMeter(local)
     meter.start()
     ps, ss = ctx.price_batch(sarr, method=m)
@@ -278,24 +293,28 @@ def stencil_sample(ctx, aop, sarr, m, p_ref, local, reqs=None):
     st = ctx.stats()
     ms = st["kernel_ms"]
     ok = ss == 0
+    cells = sum(lattice_cells(r) for r in reqs)
     out = {"ms_per_option": ms / len(sarr), "options_per_s": len(sarr) / (ms / 1e3),
-           "cells": st["stencil_cells"], "gcells_per_s": st["stencil_cells"] / (ms / 1e3) / 1e9,
+           "cells": cells, "gcells_per_s": cells / (ms / 1e3) / 1e9,
+           "computed_cells": st["stencil_cells"],
            "failed": int((~ok).sum()),
-           "max_rel_fft64_vs_stencil": float(np.max(np.abs(p_ref[ok] - ps[ok]) / np.abs(ps[ok]))) if ok.any() else None,
+           "max_rel_fft64_vs_stencil": max_rel_floor(p_ref, ps, ok, reqs),
+           "max_abs_fft64_vs_stencil_over_K": (float(np.max(np.abs(p_ref[ok] - ps[ok]) / np.array([r.K for r in reqs])[ok]))
+                                               if ok.any() else None),
            "energy_how": how}
     if joules is not None:
         out["joules_per_option"] = joules / len(sarr)
-    if reqs is not None:
-        fl = stencil_flops(reqs)
-        ach = fl / (ms / 1e3) / 1e12
-        if m == aop.STENCIL_FP64:
-            peak, src = MEASURED_ALU["fp64"], "FP64 FMA rate measured live by aop_measure_fma_peak (of measured)"
-        else:
-            peak, src = MEASURED_ALU["fp32"], ("FP32 FMA rate measured live by aop_measure_fma_peak (of measured); "
-                                               "a doubled-FP32 cell costs about 25 FP32 instructions for its "
-                                               "3-5 algorithmic flops")
-        out["roofline"] = {"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
-                           "flops": fl, "peak_source": src}
+    kind = "fp64" if m == aop.STENCIL_FP64 else "df32"
+    instr = sum(lattice_cells(r) * STENCIL_INSTR[kind][2 if r.model in (0, 3) else 3] for r in reqs)
+    ach = instr / (ms / 1e3) / 1e12
+    # the measured FMA rate in flop/s counts two per FMA instruction
+    peak = MEASURED_ALU[kind if kind == "fp64" else "fp32"] / 2
+    out["roofline"] = {"bound": "alu", "achieved": ach, "peak": peak, "unit": "Tinstr/s", "frac": ach / peak,
+                       "instructions": instr,
+                       "peak_source": ("%s FMA instruction rate measured live by aop_measure_fma_peak (of measured)"
+                                       % ("FP64" if kind == "fp64" else "FP32")),
+                       "count": ("instructions per lattice cell on the bounding pipe: %s"
+                                 % json.dumps(STENCIL_INSTR[kind]))}
     return out
 
 
@@ -485,7 +504,7 @@ def main():
     ap.add_argument("--serve-stencil-prefix", type=int, default=128,
                     help="requests of the stream's prefix also served by the plain FP64 stencil")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--stencil-sample", type=int, default=4)
+    ap.add_argument("--stencil-sample", type=int, default=16)
     ap.add_argument("--small", action="store_true",
                     help="reduced book (T=2^15, 304 options: two per SM) for profiler captures")
     ap.add_argument("--configs", action="store_true",

@@ -73,7 +73,8 @@ constexpr int kSpecLg = 22;                // log2 g and log2 N of directly inde
 constexpr int kLeftoverCall = 48;          // rows solved naively at the root
 constexpr double kDfLogRange = 80.0;       // largest log price ratio of a doubled-FP32 base case
 constexpr int kRegCells = 256;             // widest base-case window: 8 registers per lane
-constexpr int kNaiveCap = 512;             // widest base-case window (cells) and exercise table
+constexpr int kNaiveCap = 640;             // exercise table of a base case: a 256-cell binomial
+                                           // window over 64 rows spans 2 x 256 + 64 + 4 exponents
 constexpr uint64_t kWaitNs = 30ull * 1000000000ull;   // bound of every spin-wait (30 s)
 constexpr uint64_t kStallNs = 20000000ull;             // the bound under AOP_FLAG_TEST_STALL (20 ms)
 
@@ -1155,16 +1156,18 @@ struct Walker {
         }
         return r;
     }
-    // Row values live in registers: lane l holds cells x = c0 + l + 32 r,
+    // Row values live in registers: lane l holds cells t = x - c0 = l + 32 r,
     // r < R, updated in place (ascending r, so the right neighbours a lane
-    // reads by shuffle are still the previous row's).  The D cells right of
-    // the divider hold their exercise values, so every red cell is the same
-    // D+1-point stencil.  Row i needs exercise values at cells bp .. bp + D
-    // (bp the divider of row i+1); they lie in bp' - 1 .. bp' + D (bp' the
-    // divider one row up, the divider moving <= 1 cell per row), one cell per
-    // lane, so each lane loads its one value a row ahead and the per-row chain
-    // is shuffle -> stencil -> test.  A is the arithmetic (FP64, or doubled
-    // FP32 on the FP32 pipe).
+    // reads by shuffle are still the previous row's).  Every cell of the window
+    // takes max(continuation, exercise) (Def. 2.1) from lane-local operands:
+    // its exercise value comes from the base case's table at an address that
+    // does not depend on the values, so no value waits for the divider.  The cells right of the top row's divider
+    // tb stay green in every row below (Cor. 2.7) and hold their exercise
+    // values, which closes the window on the right.  A row's divider (the last
+    // real cell whose continuation is at least its exercise value) comes from
+    // one ballot per register: a row costs one shuffle, one stencil sum, one
+    // max and the ballots (lattice cells past a row's end, D i, get values
+    // that only such cells read).  A is the arithmetic (FP64, or doubled FP32 on the FP32 pipe).
     template <int R, int D, class A>
     __device__ int64_t call_rows(int64_t i0, int64_t c0, int64_t b, int64_t h, const Buf &in, const Buf &out,
                                  int64_t klo, int64_t khi) {
@@ -1174,87 +1177,66 @@ struct Walker {
         // 32-bit arithmetic relative to (i0, c0) inside the base case: column
         // t = x - c0, row offset k = i0 - i.  The exercise value of (k, t)
         // sits at slot sbase + alpha t + k of the table, clamped into it (the
-        // columns past a row's end that can reach the clamp are never read).
+        // cells that can reach the clamp are past the window or the rows).
         const int alpha = (P.model == AOP_BINOMIAL_CALL) ? 2 : 1;
         const int sbase = (int)(alpha * c0 - i0 + P.T - klo);
         const int kmax = (int)(khi - klo);
         const int clip0 = (int)((int64_t)D * i0 - c0);   // row i0 - k ends at column clip0 - D k
         const int hh = (int)h;
+        const int tb = (int)(b - c0);
         int32_t *const rec = (lane == 0 && bnd) ? bnd + i0 : nullptr;   // rec[-k] = row i0 - k
         auto slot = [&](int k, int t) { return min(max(sbase + alpha * t + k, 0), kmax); };
-        int bb = (int)(b - c0);
         T val[R];
 #pragma unroll
         for (int r = 0; r < R; r++) {
             const int t = lane + 32 * r;
             val[r] = A::zero();
-            if (t <= bb) val[r] = A::template load<MODE>(in, c0 + t);
-            else if (t <= bb + D) val[r] = ext[slot(0, t)];
+            if (t <= tb) val[r] = A::template load<MODE>(in, c0 + t);
+            else if (t <= tb + D) val[r] = ext[slot(0, t)];
         }
-        // this lane's column among bb - 1 .. bb + D, or -1
-        auto cand = [&](int bq) -> int {
-            const int d = bq - 1;
-            const int t = d + ((lane - d) & 31);
-            return (t >= 0 && t <= d + D + 1) ? t : -1;
-        };
-        int pt = cand(bb);
-        T pre = (pt >= 0) ? ext[slot(1, pt)] : A::zero();
-        int cells = 0;
+        int bn = tb;
+        long long cells = 0;
         const long long lc0 = clock64();
-        int k = 1;
-        for (; k <= hh; k++) {
-            const int bp = bb;
-            if (bp < 0) break;
-            const T ex1 = pre;           // exercise value of row k at column t1
-            const int t1 = pt;
-            pt = cand(bp);               // and of row k + 1 for the next row
-            pre = (pt >= 0) ? ext[slot(k + 1, pt)] : A::zero();
+        for (int k = 1; k <= hh; k++) {
+            const int lim = min(tb, clip0 - D * k);   // last real cell of the window in this row
+            const int bprev = bn;
+            int nbn = -1;
             // straight-line over the registers (R fits the window), so that
-            // their shuffles and sums overlap
+            // their shuffles, sums and maxima overlap
 #pragma unroll
             for (int r = 0; r < R; r++) {
+                const int t = lane + 32 * r;
+                const T ex = ext[slot(k, t)];      // independent of the values: issued early
                 const T nx = (r + 1 < R) ? val[(r + 1) % R] : A::zero();
                 const T n1 = A::shfl(lane == 0 ? nx : val[r], (lane + 1) & 31);
+                T cont;
                 if (D == 2) {
                     const T n2 = A::shfl(lane <= 1 ? nx : val[r], (lane + 2) & 31);
-                    val[r] = A::dot3(w, val[r], n1, n2);
+                    cont = A::dot3(w, val[r], n1, n2);
                 } else {
-                    val[r] = A::dot2(w, val[r], n1);
+                    cont = A::dot2(w, val[r], n1);
                 }
+                const bool red = A::cont_ge(cont, ex);
+                val[r] = (red && t <= tb) ? cont : ex;
+                // bit l: cell l + 32 r is a red cell of the row
+                const unsigned bl = __ballot_sync(0xffffffffu, red && t <= lim);
+                if (bl) nbn = 32 * r + 31 - __clz(bl);
             }
-            const int last = clip0 - D * k;          // last column of this row
-            int bn;
-            if (bp - 1 >= last) {
-                bn = last;                           // the row ends inside the window: all red
-            } else {
-                // value-versus-payoff test at the previous divider (Cor. 2.7),
-                // taken by the lane that holds it (its ex1 is that cell's)
-                T tv = A::zero();
-#pragma unroll
-                for (int r = 0; r < R; r++)
-                    if (r == (bp >> 5)) tv = val[r];
-                const bool ge = __shfl_sync(0xffffffffu, A::cont_ge(tv, ex1), bp & 31);
-                bn = ge ? bp : bp - 1;
-            }
-            cells += min(bp, last) + 1;
-            bb = bn;
-            if (rec) rec[-k] = (int32_t)(c0 + max(bb, -1));
-            // cells right of the new divider take their exercise values
-            if (t1 > bb) {
-#pragma unroll
-                for (int r = 0; r < R; r++)
-                    if (r == (t1 >> 5)) val[r] = ex1;
-            }
+            // the previous row's divider is stored now, after this row's
+            // shuffles, so that the store does not hold them back
+            if (k > 1 && rec) rec[-(k - 1)] = (int32_t)(c0 + bprev);
+            bn = nbn;
+            cells += max(lim + 1, 0);
         }
+        if (hh >= 1 && rec) rec[-hh] = (int32_t)(c0 + bn);
         if (lane == 0) cnt.loop_cyc += clock64() - lc0;
-        if (k <= hh) record_range(i0 - h, i0 - k, (int32_t)(c0 - 1));
 #pragma unroll
         for (int r = 0; r < R; r++) {
             const int t = lane + 32 * r;
-            if (t <= bb) A::template store<MODE>(out, c0 + t, val[r]);
+            if (t <= bn) A::template store<MODE>(out, c0 + t, val[r]);
         }
         if (lane == 0) cnt.base_cells += cells;
-        return c0 + bb;
+        return c0 + bn;
     }
 
     template <class A>
@@ -1281,7 +1263,7 @@ struct Walker {
         const int64_t need = b - c0 + 1 + D;
         // exercise values the base case can touch (the divider moves <= 1 cell
         // per row): one table of exponent indices, filled once
-        const int64_t klo = max((int64_t)0, ex_index(P, i0, b) - h - 2);
+        const int64_t klo = max((int64_t)0, ex_index(P, i0, c0) - 2);
         const int64_t khi = min(2 * P.T, ex_index(P, i0 - h, b + D) + 2);
         if (need > kRegCells || khi - klo + 1 > kNaiveCap) {   // never expected
             if (lane == 0) atomicCAS((int *)&S.err, 0, AOP_EINTERNAL);
@@ -1311,91 +1293,64 @@ struct Walker {
     // Put rows in registers (lane l holds cells x = lo + l + 32 r), updated
     // in place in ascending r (each lane keeps its old value of the register
     // below for the left neighbour of lane 0).  The window shrinks by one cell
-    // per side per row.  Cells left of the divider hold the exercise value,
-    // which for the put does not depend on the time step (table exw, one per
-    // window); they stay green, so only the divider cell can turn red.
+    // per side per row.  Every cell takes max(continuation, exercise)
+    // (Def. 2.1 for the put) from lane-local operands; the put's exercise
+    // value does not depend on the time step, so each lane holds its cells'
+    // values for the whole base case.  A row's divider (the last cell of the
+    // row whose exercise value exceeds its continuation) comes from one ballot
+    // per register.
     template <int R, class A>
     __device__ int64_t put_rows(int64_t n, int64_t lo, int64_t hi, int64_t f, int64_t h, const Buf &in,
                                 const Buf &out) {
         using T = typename A::T;
         const typename A::Wts w = A::weights(S);
         const T *ext = (const T *)exw;
-        T val[R];
+        const int span = (int)(hi - lo);          // window cells 0 .. span
+        const int fl = (int)(f - lo);             // divider of row n, relative to lo
+        T val[R], ex[R];
 #pragma unroll
         for (int r = 0; r < R; r++) {
-            const int64_t x = lo + lane + 32 * r;
+            const int t = lane + 32 * r;
+            ex[r] = ext[min(t, span)];
             val[r] = A::zero();
-            if (x <= hi) val[r] = (x <= f) ? ext[x - lo] : A::template load<MODE>(in, x);
+            if (t <= span) val[r] = (t <= fl) ? ex[r] : A::template load<MODE>(in, lo + t);
         }
-        long long cells = 0;
         int32_t *const rec = (lane == 0) ? bnd : nullptr;
-        const int64_t span = hi - lo;
-        auto ld = [&](int64_t x) { return ext[min(max(x - lo, (int64_t)0), span)]; };
-        // exercise values at the cells the next test may take: f, f - 1 and
-        // the row's right end (loaded a row ahead)
-        T p0 = ld(f), p1 = ld(f - 1), p2 = ld(hi);
-        int64_t pf = f;
-        int64_t L = lo, Rr = hi;
-        for (int64_t k = 1; k <= h; k++) {
-            const int64_t nl = L + 1, nr = Rr - 1;
-            const int64_t fp = f;
-            const bool test = (fp >= nl && fp <= nr);
-            const T te = (fp == pf) ? p0 : ((fp == pf - 1) ? p1 : p2);
-            pf = fp;
-            p0 = ld(fp);
-            p1 = ld(fp - 1);
-            p2 = ld(nr);
+        const int hh = (int)h;
+        int fn = fl;
+        long long cells = 0;
+        for (int k = 1; k <= hh; k++) {
+            const int fprev = fn;
+            int nfn = k - 1;                      // none: left of this row's window
             T prev = A::zero();
-            // only registers that hold the test cell fp or red cells (fp .. nr)
-            // are stepped: cells left of fp are green and keep their exercise
-            // values, cells right of nr are outside the row
-            const int r_lo = (int)((fp - lo) >> 5), r_hi = (int)((nr - lo) >> 5);
 #pragma unroll
             for (int r = 0; r < R; r++) {
-                if (r < r_lo || r > r_hi) {
-                    prev = val[r];
-                    continue;
-                }
-                const int64_t x = lo + lane + 32 * r;
+                const int t = lane + 32 * r;
                 const T nx = (r + 1 < R) ? val[(r + 1) % R] : A::zero();
                 const T vl = A::shfl(lane == 31 ? prev : val[r], (lane + 31) & 31);
                 const T vr = A::shfl(lane == 0 ? nx : val[r], (lane + 1) & 31);
                 const T cv = A::dot3(w, vl, val[r], vr);
                 prev = val[r];
-                if (x >= fp) val[r] = cv;
+                const bool green = A::ex_gt(ex[r], cv);
+                val[r] = green ? ex[r] : cv;
+                // bit l: cell l + 32 r is a green cell of the row
+                const unsigned bl = __ballot_sync(0xffffffffu, green && t >= k && t <= span - k);
+                if (bl) nfn = 32 * r + 31 - __clz(bl);
             }
-            cells += nr - nl + 1;
-            int64_t fn;
-            if (fp >= nr + 1) fn = nr;
-            else if (fp < nl) fn = fp;
-            else {
-                // exercise > continuation, taken by the lane that holds the
-                // previous divider
-                const int64_t d = fp - lo;
-                T tv = A::zero();
-#pragma unroll
-                for (int r = 0; r < R; r++)
-                    if (r == (int)(d >> 5)) tv = val[r];
-                const bool green = __shfl_sync(0xffffffffu, A::ex_gt(te, tv), (int)(d & 31));
-                fn = green ? fp : fp - 1;
-                if (green && lane == (int)(d & 31)) {
-#pragma unroll
-                    for (int r = 0; r < R; r++)
-                        if (r == (int)(d >> 5)) val[r] = te;
-                }
-            }
-            f = fn;
-            if (rec) rec[n + k] = (f >= nl) ? (int32_t)f : (int32_t)AOP_BOUNDARY_NONE_PUT;
-            L = nl;
-            Rr = nr;
+            // the previous row's divider is stored after this row's shuffles
+            if (k > 1 && rec)
+                rec[n + k - 1] = (fprev >= k - 1) ? (int32_t)(lo + fprev) : (int32_t)AOP_BOUNDARY_NONE_PUT;
+            fn = nfn;
+            cells += span - 2 * k + 1;
         }
+        if (hh >= 1 && rec) rec[n + hh] = (fn >= hh) ? (int32_t)(lo + fn) : (int32_t)AOP_BOUNDARY_NONE_PUT;
 #pragma unroll
         for (int r = 0; r < R; r++) {
-            const int64_t x = lo + lane + 32 * r;
-            if (x >= max(L, f + 1) && x <= Rr) A::template store<MODE>(out, x, val[r]);
+            const int t = lane + 32 * r;
+            if (t >= max(hh, fn + 1) && t <= span - hh) A::template store<MODE>(out, lo + t, val[r]);
         }
         if (lane == 0) cnt.base_cells += cells;
-        return f;
+        return lo + fn;
     }
 
     template <class A>

@@ -6,11 +6,11 @@
 // Layout: per option an exercise table ex[k'] (k' in [0, 2T]) and two row
 // buffers (ping-pong) of D T + 1 (calls) or 2T + 1 (put) doubles, at a uniform
 // stride.  One launch advances every option of the batch by up to kRows rows:
-// a CTA owns an output segment of kSeg cells, loads the input row segment plus
-// the halo its dependency cone needs (kRows*D cells to the right for the calls,
-// kRows on each side for the put) into shared memory, and steps kRows rows
-// there (overlapped tiling: the halo is recomputed by the neighbour tile).
-// The per-row divider is reduced per tile and merged with atomicMax.
+// each warp owns a tile of contiguous cells held in registers (kLC per lane),
+// steps the rows there with shuffles between neighbouring lanes, and reads the
+// exercise values from its slice of the table in shared memory (overlapped
+// tiling: the cells a tile's rows cut off are recomputed by the neighbour
+// tile).  The per-row divider is reduced per warp and merged with atomicMax.
 //
 // Two arithmetics (template flag DF): FP64, and doubled FP32 (a cell is an
 // unevaluated pair hi + lo of FP32 numbers in the same 8-byte slot, ~48-bit
@@ -38,10 +38,22 @@ namespace aop {
 
 namespace {
 
-constexpr int kRows = 128;      // rows per temporal block (one launch)
-constexpr int kSeg = 2048;      // output cells per tile
-constexpr int kThreads = 256;
-constexpr int kBuf = kSeg + 2 * kRows + 8;
+constexpr int kRows = 64;       // rows per temporal block (one launch)
+constexpr int kLC = 16;         // cells per lane: a warp tile holds 32 x kLC contiguous cells
+constexpr int kTile = 32 * kLC;
+constexpr int kWarps = 4;       // warp tiles per CTA
+
+// Each warp keeps a slice of the option's exercise table in shared memory,
+// one segment per lane: lane l's segment holds the entries its cells read over
+// the block's rows, at offsets alpha c + beta (k - 1) (cell c of the lane, row
+// k of the block; alpha = 2 on the binomial lattice, 1 else; beta = 1 for the
+// calls, whose exercise value moves one exponent per row, 0 for the put).  The
+// segment length is odd, so the 32 lanes' reads fall in distinct banks, and a
+// cell's address is a per-row base plus a constant.
+__host__ __device__ constexpr int seg_vmax(int alpha, int beta) { return alpha * (kLC - 1) + beta * (kRows - 1); }
+__host__ __device__ constexpr int seg_stride(int alpha, int beta) { return (seg_vmax(alpha, beta) + 1) | 1; }
+constexpr int kSegMax = seg_stride(2, 1) > seg_stride(1, 1) ? seg_stride(2, 1) : seg_stride(1, 1);
+constexpr size_t kWarpTab = (size_t)32 * kSegMax * sizeof(double);
 
 struct StencilOpt {
     int64_t W;        // row buffer length (doubles)
@@ -53,11 +65,6 @@ __host__ __device__ inline StencilOpt stencil_layout(int64_t T_max) {
     L.W = 2 * T_max + 1;                   // enough for every model
     L.stride = ((3 * L.W + 31) / 32) * 32; // ex table + two rows
     return L;
-}
-
-__device__ inline int64_t remaining_after(int64_t T, int64_t launch) {
-    int64_t r = T - launch * (int64_t)kRows;
-    return r < 0 ? 0 : r;
 }
 
 constexpr double kDfClamp = 1e30;
@@ -122,158 +129,216 @@ __global__ void stencil_init_kernel(const Params *params, int64_t n, int64_t T_m
     }
 }
 
-// One temporal block of up to kRows rows for every option.  grid-stride over
-// tiles; tile -> (option, segment) through per-option tile counts computed in
-// shared memory.
-template <bool DF>
-__global__ void __launch_bounds__(kThreads)
-stencil_block_kernel(const Params *params, int64_t n, int64_t T_max, int64_t launch,
-                     double *ws, int32_t *bnd, const int64_t *bnd_off, long long *cells)
+// One temporal block of up to kRows rows of every option (grid.y walks the
+// options, grid.x x kWarps the warp tiles of an option's output row).  A warp
+// loads its input window of kTile cells (lane l: cells x0 + kLC l .. + kLC-1),
+// steps the rows in registers -- the D cells right of a lane's last cell (and
+// for the put the one left of its first) come from the neighbouring lanes by
+// shuffle -- and stores the cells it owns.  The window's valid part shrinks by
+// D cells per row on the right (calls) or one on each side (put); neighbouring
+// tiles overlap by that much and compute the overlap identically.  Every cell
+// takes max(continuation, exercise) (Def. 2.1); with BND each row's divider
+// (calls: last red cell; put: last green cell) is reduced per warp and merged
+// with atomicMax.
+template <class C> struct Cell;
+template <> struct Cell<double> {
+    __device__ static double zero() { return 0.0; }
+    __device__ static double shfl_dn(double v) { return __shfl_down_sync(0xffffffffu, v, 1); }
+    __device__ static double shfl_up(double v) { return __shfl_up_sync(0xffffffffu, v, 1); }
+    __device__ static double dot2(double w0, double w1, float2, float2, double a, double b) { return w0 * a + w1 * b; }
+    __device__ static double dot3(double w0, double w1, double w2, float2, float2, float2, double a, double b,
+                                  double c) { return w0 * a + w1 * b + w2 * c; }
+    __device__ static bool ge(double a, double b) { return a >= b; }
+    __device__ static bool clamped(double) { return false; }
+};
+template <> struct Cell<float2> {
+    __device__ static float2 zero() { return make_float2(0.f, 0.f); }
+    __device__ static float2 shfl_dn(float2 v) {
+        return make_float2(__shfl_down_sync(0xffffffffu, v.x, 1), __shfl_down_sync(0xffffffffu, v.y, 1));
+    }
+    __device__ static float2 shfl_up(float2 v) {
+        return make_float2(__shfl_up_sync(0xffffffffu, v.x, 1), __shfl_up_sync(0xffffffffu, v.y, 1));
+    }
+    __device__ static float2 dot2(double, double, float2 v0, float2 v1, float2 a, float2 b) {
+        return fft::df_dot2(v0, v1, a, b);
+    }
+    __device__ static float2 dot3(double, double, double, float2 v0, float2 v1, float2 v2, float2 a, float2 b,
+                                  float2 c) { return fft::df_dot3(v0, v1, v2, a, b, c); }
+    __device__ static bool ge(float2 a, float2 b) { return fft::df_ge(a, b); }
+    __device__ static bool clamped(float2 e) { return e.x >= (float)kDfClamp; }
+};
+
+struct TileJob {
+    int64_t T, R;        // steps of the option, rows left before this block
+    int Kp;              // rows of this block
+    int64_t x0;          // first input cell of the warp's window
+    int64_t own_lo, own_hi;
+};
+
+// the warp's table segments: lane l's entry v = table index kp_lo + alpha kLC l + v
+template <class C>
+__device__ void fill_tab(C *tab, const C *ex, int64_t kp_lo, int64_t T, int alpha, int vmax, int stride, int lane) {
+    for (int l = 0; l < 32; l++) {
+        const int64_t b = kp_lo + (int64_t)alpha * kLC * l;
+        for (int v = lane; v <= vmax; v += 32) {
+            const int64_t kp = min(max(b + v, (int64_t)0), 2 * T);
+            tab[l * stride + v] = ex[kp];
+        }
+    }
+    __syncwarp();
+}
+
+// Calls: input row R (columns 0 .. D R), rows R-1 .. R-Kp.
+template <class C, int D, bool BND>
+__device__ long long call_tile(const Params &P, const TileJob &J, const C *src, C *dst, const C *ex, C *tab,
+                               int32_t *b, int lane) {
+    using A = Cell<C>;
+    const int alpha = (D == 1) ? 2 : 1;
+    const int stride = seg_stride(alpha, 1);
+    const int64_t R = J.R, x0 = J.x0;
+    const int64_t xl = x0 + (int64_t)kLC * lane;              // the lane's first cell
+    fill_tab(tab, ex, ex_index(P, R - 1, x0), J.T, alpha, seg_vmax(alpha, 1), stride, lane);
+    C v[kLC + 2];
+#pragma unroll
+    for (int c = 0; c < kLC; c++) {
+        const int64_t x = xl + c;
+        v[c] = (x >= 0 && x <= (int64_t)D * R) ? src[x] : A::zero();
+    }
+    const double w0 = P.w[0], w1 = P.w[1], w2 = P.w[2];
+    const float2 f0 = fft::df_from(w0), f1 = fft::df_from(w1), f2 = fft::df_from(w2);
+    const C *tl = tab + lane * stride;
+    long long cells = 0;
+    for (int k = 1; k <= J.Kp; k++) {
+        v[kLC] = A::shfl_dn(v[0]);
+        if (D == 2) v[kLC + 1] = A::shfl_dn(v[1]);
+        const C *tk = tl + (k - 1);
+        const int64_t hi = min(x0 + kTile - 1 - (int64_t)D * k, (int64_t)D * (R - k));   // last valid cell
+        const int lim = (int)max(min(hi - xl, (int64_t)kLC - 1), (int64_t)-1);
+        int last = -1;
+#pragma unroll
+        for (int c = 0; c < kLC; c++) {
+            const C cont = (D == 2) ? A::dot3(w0, w1, w2, f0, f1, f2, v[c], v[c + 1], v[c + 2])
+                                    : A::dot2(w0, w1, f0, f1, v[c], v[c + 1]);
+            const C e = tk[alpha * c];
+            const bool red = A::ge(cont, e) && !A::clamped(e);
+            v[c] = red ? cont : e;
+            if (BND && red && c <= lim) last = c;
+        }
+        if (BND) {
+            int best = (last >= 0) ? (int)(xl + last) : INT32_MIN;
+            best = __reduce_max_sync(0xffffffffu, best);
+            if (lane == 0 && best != INT32_MIN) atomicMax(&b[R - k], best);
+        }
+        cells += max(hi - x0 + 1, (int64_t)0);
+    }
+#pragma unroll
+    for (int c = 0; c < kLC; c++) {
+        const int64_t x = xl + c;
+        if (x >= J.own_lo && x <= J.own_hi) dst[x] = v[c];
+    }
+    return cells;
+}
+
+// BSM put: input row n0 = T - R (k in [-R, R], stored at k + T), rows n0+1 ..
+// n0+Kp; weights b, c, a on k-1, k, k+1; the exercise value does not depend on
+// the row.
+template <class C, bool BND>
+__device__ long long put_tile(const Params &P, const TileJob &J, const C *src, C *dst, const C *ex, C *tab,
+                              int32_t *b, int lane) {
+    using A = Cell<C>;
+    const int stride = seg_stride(1, 0);
+    const int64_t R = J.R, x0 = J.x0, T = J.T;
+    const int64_t xl = x0 + (int64_t)kLC * lane;
+    fill_tab(tab, ex, x0 + T, T, 1, seg_vmax(1, 0), stride, lane);
+    C v[kLC];
+#pragma unroll
+    for (int c = 0; c < kLC; c++) {
+        const int64_t x = xl + c;
+        v[c] = (x >= -R && x <= R) ? src[x + T] : A::zero();
+    }
+    const double w0 = P.w[0], w1 = P.w[1], w2 = P.w[2];
+    const float2 f0 = fft::df_from(w0), f1 = fft::df_from(w1), f2 = fft::df_from(w2);
+    const C *tl = tab + lane * stride;
+    const int64_t n0 = T - R;
+    long long cells = 0;
+    for (int k = 1; k <= J.Kp; k++) {
+        const C left = A::shfl_up(v[kLC - 1]);
+        const C right = A::shfl_dn(v[0]);
+        const int64_t lo = max(x0 + k, -(R - k)), hi = min(x0 + kTile - 1 - k, R - k);   // valid cells
+        const int clo = (int)max(min(lo - xl, (int64_t)kLC), (int64_t)0);
+        const int chi = (int)max(min(hi - xl, (int64_t)kLC - 1), (int64_t)-1);
+        int last = -1;
+        C prev = left;
+#pragma unroll
+        for (int c = 0; c < kLC; c++) {
+            const C nxt = (c + 1 < kLC) ? v[(c + 1) % kLC] : right;
+            const C cont = A::dot3(w0, w1, w2, f0, f1, f2, prev, v[c], nxt);
+            const C e = tl[c];
+            const bool green = !A::ge(cont, e);
+            prev = v[c];
+            v[c] = green ? e : cont;
+            if (BND && green && c >= clo && c <= chi) last = c;
+        }
+        if (BND) {
+            int best = (last >= 0) ? (int)(xl + last) : INT32_MIN;
+            best = __reduce_max_sync(0xffffffffu, best);
+            if (lane == 0 && best != INT32_MIN) atomicMax(&b[n0 + k], best);
+        }
+        cells += max(hi - lo + 1, (int64_t)0);
+    }
+#pragma unroll
+    for (int c = 0; c < kLC; c++) {
+        const int64_t x = xl + c;
+        if (x >= J.own_lo && x <= J.own_hi) dst[x + T] = v[c];
+    }
+    return cells;
+}
+
+// output cells a warp tile owns: the window less what its rows cut off
+__host__ __device__ inline int tile_out(int D, bool put) { return kTile - (put ? 2 : D) * kRows; }
+
+template <bool DF, bool BND>
+__global__ void __launch_bounds__(kWarps * 32)
+stencil_tile_kernel(const Params *params, int64_t n, int64_t T_max, int64_t launch, double *ws, int32_t *bnd,
+                    const int64_t *bnd_off, long long *cells)
 {
     using C = typename std::conditional<DF, float2, double>::type;   // one 8-byte cell
     static_assert(sizeof(C) == sizeof(double), "cells share the FP64 layout");
-    __shared__ double buf_raw[2][kBuf];
-    C (*buf)[kBuf] = (C (*)[kBuf])buf_raw;
-    __shared__ int s_bnd[kRows + 1];
-    __shared__ int64_t s_tiles_total;
+    extern __shared__ __align__(16) double tab_raw[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    C *tab = (C *)(tab_raw + (size_t)warp * 32 * kSegMax);
     const StencilOpt L = stencil_layout(T_max);
-
-    // count tiles of all options (n is modest for this path; every block redoes it)
-    if (threadIdx.x == 0) {
-        int64_t tot = 0;
-        for (int64_t o = 0; o < n; o++) {
-            const Params &P = params[o];
-            if (P.status != AOP_OK) continue;
-            int64_t R = remaining_after(P.T, launch);
-            if (R == 0) continue;
-            int64_t Rout = R - min((int64_t)kRows, R);
-            int64_t width = (P.model == AOP_BSM_PUT) ? 2 * Rout + 1 : (int64_t)P.D * Rout + 1;
-            tot += (width + kSeg - 1) / kSeg;
-        }
-        s_tiles_total = tot;
-    }
-    __syncthreads();
-    const int64_t total = s_tiles_total;
     long long my_cells = 0;
-
-    for (int64_t t = blockIdx.x; t < total; t += gridDim.x) {
-        // locate option and segment (linear scan; n is small for this path)
-        int64_t o = 0, seg = t;
-        for (o = 0; o < n; o++) {
-            const Params &P = params[o];
-            if (P.status != AOP_OK) continue;
-            int64_t R = remaining_after(P.T, launch);
-            if (R == 0) continue;
-            int64_t Rout = R - min((int64_t)kRows, R);
-            int64_t width = (P.model == AOP_BSM_PUT) ? 2 * Rout + 1 : (int64_t)P.D * Rout + 1;
-            int64_t nt = (width + kSeg - 1) / kSeg;
-            if (seg < nt) break;
-            seg -= nt;
-        }
-        const Params P = params[o];
-        const int64_t T = P.T;
-        const int64_t R = remaining_after(T, launch);
-        const int Kp = (int)min((int64_t)kRows, R);
-        const int64_t Rout = R - Kp;
-        const C *ex = (const C *)(ws + o * L.stride);
-        C *rowA = (C *)(ws + o * L.stride + L.W);
-        C *rowB = rowA + L.W;
-        const C *src = (launch % 2 == 0) ? rowA : rowB;
-        C *dst = (launch % 2 == 0) ? rowB : rowA;
+    for (int64_t o = blockIdx.y; o < n; o += gridDim.y) {
+        const Params &P = params[o];
+        if (P.status != AOP_OK) continue;
         const bool put = (P.model == AOP_BSM_PUT);
-        const double w0 = P.w[0], w1 = P.w[1], w2 = P.w[2];
-        const float2 v0 = fft::df_from(w0), v1 = fft::df_from(w1), v2 = fft::df_from(w2);
-        const int nw = P.nw;
-        const int64_t nseg = ((put ? 2 * Rout + 1 : (int64_t)P.D * Rout + 1) + kSeg - 1) / kSeg;
-
-        // absolute coordinates: calls use column j (row r holds [0, D r]);
-        // the put uses k (row n holds [-(T-n), T-n]) and stores at k + T.
-        int64_t a0, in_lo, in_hi;      // output segment start, input window
-        if (!put) {
-            a0 = seg * kSeg;
-            in_lo = a0;
-            in_hi = min(a0 + kSeg - 1 + (int64_t)P.D * Kp, (int64_t)P.D * R);
-        } else {
-            a0 = -Rout + seg * kSeg;
-            in_lo = max(a0 - Kp, -R);
-            in_hi = min(a0 + kSeg - 1 + Kp, R);
-        }
-        const int64_t base = in_lo;
-        const int64_t own_lo = (seg == 0) ? INT64_MIN / 2 : a0;
-        const int64_t own_hi = (seg == nseg - 1) ? INT64_MAX / 2 : a0 + kSeg - 1;
-        const int64_t store_off = put ? T : 0;
-
-        for (int64_t x = in_lo + threadIdx.x; x <= in_hi; x += blockDim.x)
-            buf[0][x - base] = src[x + store_off];
-        for (int k = threadIdx.x; k <= Kp; k += blockDim.x) s_bnd[k] = INT32_MIN;
-        __syncthreads();
-
-        int cur = 0;
-        int64_t lo = in_lo, hi = in_hi;
-        for (int k = 1; k <= Kp; k++) {
-            // row index of the new row: calls r = R - k; put n = T - R + k
-            const int64_t r = put ? (T - R + k) : (R - k);
-            int64_t nlo, nhi;
-            if (!put) { nlo = lo; nhi = min(hi - P.D, (int64_t)P.D * r); }
-            else { nlo = max(lo + 1, -(T - r)); nhi = min(hi - 1, T - r); }
-            const C *pv = buf[cur];
-            C *nv = buf[cur ^ 1];
-            int best = INT32_MIN;
-            for (int64_t x = nlo + threadIdx.x; x <= nhi; x += blockDim.x) {
-                const int64_t ix = x - base;
-                C cont;
-                if constexpr (DF) {
-                    if (!put) cont = (nw == 3) ? fft::df_dot3(v0, v1, v2, pv[ix], pv[ix + 1], pv[ix + 2])
-                                               : fft::df_dot2(v0, v1, pv[ix], pv[ix + 1]);
-                    else cont = fft::df_dot3(v0, v1, v2, pv[ix - 1], pv[ix], pv[ix + 1]);
-                } else {
-                    if (!put) {
-                        cont = w0 * pv[ix] + w1 * pv[ix + 1];
-                        if (nw == 3) cont += w2 * pv[ix + 2];
-                    } else {
-                        cont = w0 * pv[ix - 1] + w1 * pv[ix] + w2 * pv[ix + 1];
-                    }
-                }
-                const C e = ex[ex_index(P, r, x)];
-                bool ge;
-                if constexpr (DF) ge = fft::df_ge(cont, e);
-                else ge = cont >= e;
-                bool take_ex;
-                if (!put) {
-                    bool red = ge;
-                    if constexpr (DF) red = red && e.x < (float)kDfClamp;
-                    take_ex = !red;
-                    if (red && x >= own_lo && x <= own_hi) best = max(best, (int)x);
-                } else {
-                    take_ex = !ge;
-                    if (take_ex && x >= own_lo && x <= own_hi) best = max(best, (int)x);
-                }
-                nv[ix] = take_ex ? e : cont;
-                my_cells++;
-            }
-            best = __reduce_max_sync(0xffffffffu, best);
-            if ((threadIdx.x & 31) == 0 && best != INT32_MIN) atomicMax(&s_bnd[k], best);
-            lo = nlo; hi = nhi;
-            cur ^= 1;
-            __syncthreads();
-        }
-        // write the owned output segment
-        const int64_t out_hi = put ? min(a0 + kSeg - 1, Rout) : min(a0 + kSeg - 1, (int64_t)P.D * Rout);
-        for (int64_t x = a0 + threadIdx.x; x <= out_hi; x += blockDim.x)
-            dst[x + store_off] = buf[cur][x - base];
-        if (bnd) {
-            int32_t *b = bnd + bnd_off[o];
-            for (int k = 1 + threadIdx.x; k <= Kp; k += blockDim.x) {
-                const int64_t r = put ? (T - R + k) : (R - k);
-                if (s_bnd[k] != INT32_MIN) atomicMax(&b[r], s_bnd[k]);
-            }
-        }
-        __syncthreads();
+        TileJob J;
+        J.T = P.T;
+        J.R = J.T - launch * (int64_t)kRows;
+        if (J.R <= 0) continue;
+        J.Kp = (int)min((int64_t)kRows, J.R);
+        const int64_t Rout = J.R - J.Kp;
+        const int D = P.D;
+        const int64_t out_lo = put ? -Rout : 0, out_hi = put ? Rout : (int64_t)D * Rout;
+        const int outw = tile_out(D, put);
+        const int64_t ntiles = (out_hi - out_lo + outw) / outw;
+        const int64_t tile = (int64_t)blockIdx.x * kWarps + warp;
+        if (tile >= ntiles) continue;
+        J.own_lo = out_lo + tile * outw;
+        J.own_hi = min(J.own_lo + outw - 1, out_hi);
+        J.x0 = put ? J.own_lo - J.Kp : J.own_lo;
+        const C *ex = (const C *)(ws + o * L.stride);
+        const C *rowA = (const C *)(ws + o * L.stride + L.W);
+        const C *src = (launch % 2 == 0) ? rowA : rowA + L.W;
+        C *dst = (C *)((launch % 2 == 0) ? rowA + L.W : rowA);
+        int32_t *b = bnd ? bnd + bnd_off[o] : nullptr;
+        if (put) my_cells += put_tile<C, BND>(P, J, src, dst, ex, tab, b, lane);
+        else if (D == 2) my_cells += call_tile<C, 2, BND>(P, J, src, dst, ex, tab, b, lane);
+        else my_cells += call_tile<C, 1, BND>(P, J, src, dst, ex, tab, b, lane);
+        __syncwarp();
     }
-    if (cells) {
-        my_cells = __reduce_add_sync(0xffffffffu, (unsigned)my_cells);
-        if ((threadIdx.x & 31) == 0) atomicAdd((unsigned long long *)cells, (unsigned long long)my_cells);
-    }
+    if (cells && lane == 0 && my_cells) atomicAdd((unsigned long long *)cells, (unsigned long long)my_cells);
 }
 
 template <bool DF>
@@ -333,14 +398,16 @@ static cudaError_t run_stencil_t(int64_t n, const Params *d_params, int64_t T_ma
         dim3 grid(chunks, (unsigned)std::min<int64_t>(n, 65535));
         stencil_init_kernel<DF><<<grid, 256, 0, s>>>(d_params, n, T_max, w, d_bnd, d_bnd_off);
     }
-    int dev = 0, sms = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const int64_t launches = (T_max + kRows - 1) / kRows;
     long long *cells = d_stats ? (long long *)&d_stats->stencil_cells : nullptr;
-    for (int64_t l = 0; l < launches; l++) {
-        stencil_block_kernel<DF><<<sms * 4, kThreads, 0, s>>>(d_params, n, T_max, l, w, d_bnd, d_bnd_off, cells);
-    }
+    // warp tiles of the widest output row (the narrowest tile: 3-point stencils)
+    const int64_t max_tiles = (2 * T_max + 1 + tile_out(2, true) - 1) / tile_out(2, true);
+    const dim3 grid((unsigned)((max_tiles + kWarps - 1) / kWarps), (unsigned)std::min<int64_t>(n, 65535));
+    const size_t smem = kWarps * kWarpTab;
+    auto kern = d_bnd ? stencil_tile_kernel<DF, true> : stencil_tile_kernel<DF, false>;
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    for (int64_t l = 0; l < launches; l++)
+        kern<<<grid, kWarps * 32, smem, s>>>(d_params, n, T_max, l, w, d_bnd, d_bnd_off, cells);
     stencil_finish_kernel<DF><<<(unsigned)((n + 127) / 128), 128, 0, s>>>(d_params, n, T_max, w, d_prices);
     return cudaGetLastError();
 }
