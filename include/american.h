@@ -137,6 +137,8 @@ typedef struct aop_options {
     int32_t base_case;  /* D&C base-case height in rows (2 .. 64, clamped); 0 = tuned default */
     int32_t flags;      /* AOP_FLAG_* bits, 0 for none */
     int32_t ctas_per_sm; /* D&C: options in flight per SM; 0 = as many as fit */
+    int32_t lg_tile;    /* D&C: log2 of a worker's shared-memory transform tile, 9 .. 11; 0 = tuned default */
+    int32_t radix;      /* D&C: transform stages in radix-4 steps (4) or radix-2 steps (2); 0 = tuned default */
 } aop_options;
 
 /* Counters accumulated by the kernels of the last batch call (for roofline
@@ -344,16 +346,29 @@ aop_status aop_server_destroy(aop_server *srv);
 
 /* Autotuner for the divide-and-conquer methods (no counterpart in the paper,
  * which fixes its base case by hand): prices the n host requests twice per
- * schedule -- base-case height in {16, 31, 32, 47, 63, 64} x options in
- * flight per SM in {1, 2, 3, 4}, skipping counts the kernel's registers and
- * shared memory cannot hold -- timing each second run with CUDA events, and
- * keeps the fastest schedule as this context's default for `method` (used
- * where aop_options.base_case or ctas_per_sm is 0).  best_out (nullable)
- * receives it.  Costs up to 48 batch calls: pass a sample of the workload, or
+ * schedule and times each second run with CUDA events.  Stage 1 searches the
+ * base-case height in {16, 31, 32, 47, 63, 64} x options in flight per SM in
+ * {1, 2, 3, 4} (skipping counts the kernel's registers and shared memory
+ * cannot hold) with the default transforms; stage 2 searches the worker's
+ * transform tile (2^9, 2^10, 2^11 values) x the transform radix (4, 2) at
+ * the stage-1 pick.  The fastest schedule is kept in this context under the
+ * key (method, log2 of the largest T of the requests, model class: binomial
+ * only, three-point only, or both) and used by later calls whose aop_options
+ * leave a field 0: a call takes the pick of its own key, else of the same size
+ * with another model class, else of the nearest size.  best_out (nullable)
+ * receives it.  Costs up to 53 batch calls: pass a sample of the workload, or
  * the workload itself when it is priced repeatedly.  AOP_EINVAL for the plain
  * stencil or a bad method. */
 aop_status aop_ctx_autotune(aop_ctx *ctx, int64_t n, const aop_request *reqs, int32_t method,
                             aop_options *best_out);
+
+/* The D&C schedule a batch call with these n host requests and *opt would
+ * use on this context: the fields of *opt that are nonzero, the rest from the
+ * context's tuned picks (see aop_ctx_autotune) or the library defaults.
+ * ctas_per_sm 0 in *out means as many as fit.  Host-only; AOP_EINVAL for a
+ * plain stencil method. */
+aop_status aop_ctx_schedule(const aop_ctx *ctx, int64_t n, const aop_request *reqs, const aop_options *opt,
+                            aop_options *out);
 
 /* Allocation-free variant of aop_linear_advance_device (the paper has no
  * counterpart; this is a deployment convenience).

@@ -52,7 +52,8 @@ class AopError(RuntimeError):
 
 class _Options(ctypes.Structure):
     _fields_ = [("method", ctypes.c_int32), ("base_case", ctypes.c_int32),
-                ("flags", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32)]
+                ("flags", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32),
+                ("lg_tile", ctypes.c_int32), ("radix", ctypes.c_int32)]
 
 
 class _Stats(ctypes.Structure):
@@ -116,6 +117,7 @@ def load(path: Optional[str] = None):
         lib.aop_linear_advance_noalloc.argtypes = [ctypes.c_int, ctypes.c_int, vp, i64, i64, i64,
                                                    vp, vp, vp]
         lib.aop_linear_advance_noalloc.restype = ctypes.c_int
+        lib.aop_ctx_schedule.argtypes = [vp, i64, vp, ctypes.POINTER(_Options), ctypes.POINTER(_Options)]
         lib.aop_measure_fma_peak.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.POINTER(dbl)]
         lib.aop_workspace_bytes.argtypes = [ctypes.c_int, i64, ctypes.c_int, i64, ctypes.POINTER(ctypes.c_size_t)]
         for f in ("aop_ctx_get_option_times", "aop_ctx_create", "aop_ctx_destroy", "price_american", "price_american_ex",
@@ -123,7 +125,7 @@ def load(path: Optional[str] = None):
                   "aop_linear_advance_device", "aop_ctx_get_stats", "aop_ctx_autotune",
                   "aop_server_create", "aop_server_submit", "aop_server_poll", "aop_server_serve_stream",
                   "aop_server_info", "aop_server_destroy", "price_european_batch", "aop_workspace_bytes",
-                  "aop_measure_fma_peak"):
+                  "aop_measure_fma_peak", "aop_ctx_schedule"):
             getattr(lib, f).restype = ctypes.c_int
         _lib = lib
         return lib
@@ -159,8 +161,9 @@ FLAG_TEST_STALL = 16
 
 
 
-def _opts(method: int, base_case: int = 0, flags: int = 0, ctas_per_sm: int = 0) -> _Options:
-    return _Options(int(method), int(base_case), int(flags), int(ctas_per_sm))
+def _opts(method: int, base_case: int = 0, flags: int = 0, ctas_per_sm: int = 0, lg_tile: int = 0,
+          radix: int = 0) -> _Options:
+    return _Options(int(method), int(base_case), int(flags), int(ctas_per_sm), int(lg_tile), int(radix))
 
 
 def requests_array(reqs: Iterable) -> np.ndarray:
@@ -266,12 +269,12 @@ class Context:
 
     # host buffers in, host buffers out (C: price_american_batch)
     def price_batch(self, reqs, method: int = FFT_FP64, base_case: int = 0, stream: int = 0,
-                    flags: int = 0, ctas_per_sm: int = 0):
+                    flags: int = 0, ctas_per_sm: int = 0, lg_tile: int = 0, radix: int = 0):
         arr = reqs if isinstance(reqs, np.ndarray) else requests_array(reqs)
         n = len(arr)
         prices = np.empty(n, dtype=np.float64)
         status = np.empty(n, dtype=np.int32)
-        o = _opts(method, base_case, flags, ctas_per_sm)
+        o = _opts(method, base_case, flags, ctas_per_sm, lg_tile, radix)
         _check(load().price_american_batch(self._h, n, arr.ctypes.data, ctypes.byref(o),
                                            prices.ctypes.data, status.ctypes.data,
                                            ctypes.c_void_p(stream) if stream else None),
@@ -300,8 +303,8 @@ class Context:
     def price_batch_device(self, n: int, d_reqs: int, d_prices: int, d_status: int = 0,
                            d_boundary: int = 0, d_boundary_offsets: int = 0,
                            method: int = FFT_FP64, base_case: int = 0, stream: int = 0,
-                           flags: int = 0, ctas_per_sm: int = 0):
-        o = _opts(method, base_case, flags, ctas_per_sm)
+                           flags: int = 0, ctas_per_sm: int = 0, lg_tile: int = 0, radix: int = 0):
+        o = _opts(method, base_case, flags, ctas_per_sm, lg_tile, radix)
         _check(load().price_american_batch_device(
             self._h, int(n), ctypes.c_void_p(d_reqs), ctypes.byref(o), ctypes.c_void_p(d_prices),
             ctypes.c_void_p(d_status) if d_status else None,
@@ -329,14 +332,26 @@ class Context:
         return prices, status
 
     def autotune(self, reqs, method: int) -> dict:
-        """Pick this context's default D&C schedule (base-case height and
-        options in flight per SM) for `method` by timing a sample of requests
-        (C: aop_ctx_autotune)."""
+        """Pick this context's D&C schedule (base-case height, options in
+        flight per SM, transform tile and radix) for `method` and the size and
+        model class of these requests by timing them (C: aop_ctx_autotune)."""
         arr = reqs if isinstance(reqs, np.ndarray) else requests_array(reqs)
         best = _Options()
         _check(load().aop_ctx_autotune(self._h, len(arr), arr.ctypes.data, int(method), ctypes.byref(best)),
                "aop_ctx_autotune")
-        return {"base_case": int(best.base_case), "ctas_per_sm": int(best.ctas_per_sm)}
+        return {"base_case": int(best.base_case), "ctas_per_sm": int(best.ctas_per_sm),
+                "lg_tile": int(best.lg_tile), "radix": int(best.radix)}
+
+    def schedule(self, reqs, method: int) -> dict:
+        """The D&C schedule a batch of these requests would use on this
+        context (C: aop_ctx_schedule)."""
+        arr = reqs if isinstance(reqs, np.ndarray) else requests_array(reqs)
+        o = _opts(method)
+        out = _Options()
+        _check(load().aop_ctx_schedule(self._h, len(arr), arr.ctypes.data, ctypes.byref(o), ctypes.byref(out)),
+               "aop_ctx_schedule")
+        return {"base_case": int(out.base_case), "ctas_per_sm": int(out.ctas_per_sm),
+                "lg_tile": int(out.lg_tile), "radix": int(out.radix)}
 
     def option_times_ns(self, n: int) -> np.ndarray:
         out = np.empty(int(n), dtype=np.int64)

@@ -4,6 +4,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <map>
 #include <mutex>
 #include <vector>
 
@@ -37,16 +38,16 @@ struct aop_ctx {
     int64_t last_n = 0;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;   // bracket the pricing kernels
     bool timed = false;
-    // autotuned D&C schedule per method (0 = not tuned)
-    int tuned_B[4] = {0, 0, 0, 0};
-    int tuned_cap[4] = {0, 0, 0, 0};
+    // autotuned D&C schedules, keyed by (method, log2 of the batch's largest
+    // T, model class): fields 0 = not tuned
+    std::map<int, aop_options> tuned;
     bool serving = false;            // a serving session holds the workspace
 };
 
 struct aop_server {
     aop_ctx *ctx = nullptr;
     cudaStream_t stream = nullptr;   // the persistent pricing kernel's stream
-    int method = 0, B = 0, cap = 0, flags = 0, slots = 0;
+    int method = 0, B = 0, cap = 0, flags = 0, slots = 0, lg_tile = 0, radix2 = 0;
     int64_t T_max = 0, capacity = 0;
     // host memory mapped into the device: requests in, results out
     aop_request *h_reqs = nullptr;
@@ -65,6 +66,12 @@ struct aop_server {
 namespace {
 
 constexpr int kDefaultBaseCase = 63;    // the tuner's usual pick: strips fill whole registers
+
+// A D&C schedule: base-case height, options in flight per SM (0 = as many
+// as fit), log2 of a worker's transform tile, radix-2-only transform stages.
+struct Sched {
+    int B, cap, lg_tile, radix2;
+};
 
 aop_status cuda_fail(cudaError_t e) {
     return e == cudaSuccess ? AOP_OK : (e == cudaErrorMemoryAllocation ? AOP_ENOMEM : AOP_ECUDA);
@@ -113,14 +120,64 @@ aop_status ensure_twiddles(aop_ctx *c, int log2n) {
     return AOP_OK;
 }
 
-int resolve_base_case(const aop_ctx *c, const aop_options *opt) {
+// Model class of a batch for the schedule table: 0 = every option on the
+// binomial lattice (two-point stencil), 1 = every option three-point
+// (trinomial lattice, BSM grid), 2 = both, 3 = not known.
+int model_class(int64_t n, const aop_request *reqs) {
+    if (!reqs || n <= 0) return 3;
+    bool two = false, three = false;
+    for (int64_t i = 0; i < n; i++) {
+        const int m = reqs[i].model;
+        if (m == AOP_BINOMIAL_CALL || m == AOP_BINOMIAL_PUT) two = true;
+        else three = true;
+    }
+    return (two && three) ? 2 : (two ? 0 : 1);
+}
+
+int sched_key(int method, int64_t T_max, int cls) {
+    return (method * 32 + ilog2_ceil(std::max<int64_t>(T_max, 1))) * 4 + cls;
+}
+
+// The tuned schedule closest to (method, T_max, cls): the same key, else the
+// same size bucket of another class, else the nearest size bucket.
+aop_options lookup_tuned(const aop_ctx *c, int method, int64_t T_max, int cls) {
+    aop_options none{method, 0, 0, 0, 0, 0};
+    if (!c || c->tuned.empty()) return none;
+    auto it = c->tuned.find(sched_key(method, T_max, cls));
+    if (it != c->tuned.end()) return it->second;
+    for (int k : {2, 0, 1, 3}) {
+        it = c->tuned.find(sched_key(method, T_max, k));
+        if (it != c->tuned.end()) return it->second;
+    }
+    const int lg = ilog2_ceil(std::max<int64_t>(T_max, 1));
+    int best_d = 1 << 30;
+    aop_options best = none;
+    for (const auto &kv : c->tuned) {
+        if (kv.first / 128 != method) continue;
+        const int d = std::abs((kv.first / 4) % 32 - lg);
+        if (d < best_d) { best_d = d; best = kv.second; }
+    }
+    return best;
+}
+
+// The D&C schedule of a call: explicit options first, then the context's
+// tuned pick for this size and model class, then the library defaults.
+Sched resolve_sched(const aop_ctx *c, const aop_options *opt, int64_t T_max, int cls) {
     const int m = opt ? opt->method : 0;
-    int b = kDefaultBaseCase;
-    if (opt && opt->base_case > 0) b = opt->base_case;
-    else if (c && m >= 0 && m < 4 && c->tuned_B[m] > 0) b = c->tuned_B[m];
-    if (b < 2) b = 2;
-    if (b > 64) b = 64;
-    return b;
+    const aop_options t = lookup_tuned(c, m, T_max, cls);
+    Sched r;
+    r.B = (opt && opt->base_case > 0) ? opt->base_case : (t.base_case > 0 ? t.base_case : kDefaultBaseCase);
+    r.B = std::min(64, std::max(2, r.B));
+    r.cap = (opt && opt->ctas_per_sm > 0) ? opt->ctas_per_sm : t.ctas_per_sm;
+    r.lg_tile = (opt && opt->lg_tile > 0) ? opt->lg_tile : (t.lg_tile > 0 ? t.lg_tile : kDefaultLgTile);
+    r.lg_tile = std::min(11, std::max(9, r.lg_tile));
+    const int radix = (opt && opt->radix > 0) ? opt->radix : t.radix;
+    r.radix2 = (radix == 2) ? 1 : 0;
+    return r;
+}
+
+int resolve_base_case(const aop_ctx *c, const aop_options *opt) {
+    return resolve_sched(c, opt, 1, 3).B;
 }
 
 // Core of every batch: d_reqs etc. on the device, T_max known.
@@ -142,7 +199,7 @@ void longest_first(int64_t n, const aop_request *reqs, int32_t *order) {
 aop_status run_batch(aop_ctx *c, int64_t n, const aop_request *d_reqs, const aop_options *opt,
                      int64_t T_max, double *d_prices, int32_t *d_status, int32_t *d_bnd,
                      const int64_t *d_bnd_off, cudaStream_t s, Params *d_params, const int32_t *d_order,
-                     double *d_greeks = nullptr)
+                     double *d_greeks = nullptr, int cls = 3)
 {
     const int method = opt ? opt->method : AOP_FFT_FP64;
     if (method < 0 || method > 4) return AOP_EINVAL;
@@ -150,7 +207,8 @@ aop_status run_batch(aop_ctx *c, int64_t n, const aop_request *d_reqs, const aop
     if (d_greeks && stencil) return AOP_EINVAL;
     if (c->serving) return AOP_EBUSY;
     if (n == 0 || T_max < 1) return AOP_OK;
-    const int B = resolve_base_case(c, opt);
+    const Sched sc = resolve_sched(c, opt, T_max, cls);
+    const int B = sc.B;
     CK(cudaMemsetAsync(c->d_stats, 0, sizeof(aop_stats), s));
     CK(cudaMemsetAsync(c->d_err, 0, sizeof(int), s));
     if (stencil) {
@@ -168,9 +226,8 @@ aop_status run_batch(aop_ctx *c, int64_t n, const aop_request *d_reqs, const aop
         aop_status st = ensure_twiddles(c, lg);
         if (st) return st;
         int grid = 0;
-        int cap = opt ? opt->ctas_per_sm : 0;
-        if (cap <= 0) cap = c->tuned_cap[method];
-        size_t need = dnc_workspace_bytes(method, n, T_max, B, cap, &grid, c->device);
+        const int cap = sc.cap;
+        size_t need = dnc_workspace_bytes(method, n, T_max, B, cap, &grid, c->device, sc.lg_tile);
         size_t have_cap = c->cap ? c->cap : need;
         if (need > have_cap) need = have_cap;   // fewer resident CTAs
         st = ensure(&c->ws, &c->ws_size, need, c->cap);
@@ -187,7 +244,7 @@ aop_status run_batch(aop_ctx *c, int64_t n, const aop_request *d_reqs, const aop
         CK(cudaEventRecord(c->ev0, s));
         CK(run_dnc(method, n, d_params, T_max, B, c->ws, c->ws_size, tw, c->tw_log2, d_prices,
                    d_status, d_bnd, d_bnd_off, c->d_stats, c->d_err, opt_ns, opt ? opt->flags : 0,
-                   cap, c->device, s, nullptr, d_order, d_greeks));
+                   cap, c->device, s, nullptr, d_order, d_greeks, sc.lg_tile, sc.radix2));
         CK(cudaEventRecord(c->ev1, s));
     }
     // lattice puts ran as mirrored calls: map their dividers back
@@ -310,7 +367,8 @@ aop_status price_american_batch_device(aop_ctx *c, int64_t n, const aop_request 
     }
     longest_first(n, h_reqs, h_order);
     CK(cudaMemcpyAsync(d_order, h_order, (size_t)n * sizeof(int32_t), cudaMemcpyHostToDevice, s));
-    return run_batch(c, n, d_reqs, opt, T_max, d_prices, d_status, d_bnd, d_bnd_off, s, d_params, d_order);
+    return run_batch(c, n, d_reqs, opt, T_max, d_prices, d_status, d_bnd, d_bnd_off, s, d_params, d_order,
+                     nullptr, model_class(n, h_reqs));
 }
 
 // Host-array batch, with optional sensitivities (greeks: 3 doubles per option).
@@ -353,7 +411,7 @@ static aop_status host_batch(aop_ctx *c, int64_t n, const aop_request *reqs, con
     CK(launch_params(n, d_reqs, d_params, d_status, nullptr, s));
     if (d_greeks) CK(cudaMemsetAsync(d_greeks, 0xff, gb, s));     // NaN for rejected options
     st = run_batch(c, n, d_reqs, opt, T_max, d_prices, d_status, nullptr, nullptr, s, d_params, d_order,
-                   d_greeks);
+                   d_greeks, model_class(n, reqs));
     if (st) return st;
     CK(cudaMemcpyAsync(h + rb, d_prices, pb, cudaMemcpyDeviceToHost, s));
     CK(cudaMemcpyAsync(h + rb + pb, d_status, sb, cudaMemcpyDeviceToHost, s));
@@ -464,7 +522,7 @@ aop_status price_american_ex(const aop_request *req, const aop_options *opt, dou
     CK(launch_params(1, (const aop_request *)d, d_params, d_status, nullptr, s));
     int32_t *d_b = boundary_out ? (int32_t *)(d + off_b) : nullptr;
     st = run_batch(c, 1, (const aop_request *)d, opt, T, (double *)(d + off_price), d_status, d_b,
-                   (const int64_t *)(d + off_off), s, d_params, nullptr);
+                   (const int64_t *)(d + off_off), s, d_params, nullptr, nullptr, model_class(1, req));
     if (st) return st;
     CK(cudaMemcpyAsync(h + 256, d + off_price, sizeof(double), cudaMemcpyDeviceToHost, s));
     CK(cudaMemcpyAsync(h + 264, d_status, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
@@ -535,32 +593,60 @@ aop_status aop_ctx_autotune(aop_ctx *c, int64_t n, const aop_request *reqs, int3
     // (2B + 2 cells) into whole registers of 32 cells
     static const int kB[] = {16, 31, 32, 47, 63, 64};
     static const int kCap[] = {1, 2, 3, 4};
+    static const int kLgTile[] = {9, 10, 11};
+    static const int kRadix[] = {4, 2};
     int64_t T_max = 1;
     for (int64_t i = 0; i < n; i++) T_max = std::max<int64_t>(T_max, reqs[i].T);
     std::vector<double> prices((size_t)n);
     std::vector<aop_status> status((size_t)n);
     float best = -1.f;
-    int bB = 0, bCap = 0;
+    aop_options pick{method, kDefaultBaseCase, 0, 0, kDefaultLgTile, 4};
+    auto time_one = [&](const aop_options &o, float *ms) -> aop_status {
+        for (int rep = 0; rep < 2; rep++) {   // the first run sizes the workspace
+            aop_status st = price_american_batch(c, n, reqs, &o, prices.data(), status.data(), nullptr);
+            if (st) return st;
+            CK(cudaEventElapsedTime(ms, c->ev0, c->ev1));
+        }
+        return AOP_OK;
+    };
+    // stage 1: base-case height x options in flight per SM, default transforms
     for (int B : kB) {
         for (int cap : kCap) {
             if (cap > 1 && cap > dnc_max_per_sm(method, T_max, B)) continue;   // same as fewer
-            aop_options o{method, B, 0, cap};
+            aop_options o{method, B, 0, cap, kDefaultLgTile, 4};
             float ms = 0.f;
-            for (int rep = 0; rep < 2; rep++) {   // the first run sizes the workspace
-                aop_status st = price_american_batch(c, n, reqs, &o, prices.data(), status.data(), nullptr);
-                if (st) return st;
-                CK(cudaEventElapsedTime(&ms, c->ev0, c->ev1));
-            }
-            if (best < 0.f || ms < best) {
-                best = ms;
-                bB = B;
-                bCap = cap;
-            }
+            aop_status st = time_one(o, &ms);
+            if (st) return st;
+            if (best < 0.f || ms < best) { best = ms; pick = o; }
         }
     }
-    c->tuned_B[method] = bB;
-    c->tuned_cap[method] = bCap;
-    if (best_out) *best_out = aop_options{method, bB, 0, bCap};
+    // stage 2: transform tile and radix at that height and count
+    for (int lg : kLgTile) {
+        for (int radix : kRadix) {
+            if (lg == kDefaultLgTile && radix == 4) continue;   // timed in stage 1
+            if (pick.ctas_per_sm > 1 && pick.ctas_per_sm > dnc_max_per_sm(method, T_max, pick.base_case, lg))
+                continue;                                       // the tile leaves no room for the count
+            aop_options o{method, pick.base_case, 0, pick.ctas_per_sm, lg, radix};
+            float ms = 0.f;
+            aop_status st = time_one(o, &ms);
+            if (st) return st;
+            if (ms < best) { best = ms; pick = o; }
+        }
+    }
+    c->tuned[sched_key(method, T_max, model_class(n, reqs))] = pick;
+    if (best_out) *best_out = pick;
+    return AOP_OK;
+}
+
+aop_status aop_ctx_schedule(const aop_ctx *c, int64_t n, const aop_request *reqs, const aop_options *opt,
+                            aop_options *out) {
+    if (!c || !out || n <= 0 || !reqs || !opt) return AOP_EINVAL;
+    const int method = opt->method;
+    if (method < 0 || method > 3 || method == AOP_STENCIL_FP64) return AOP_EINVAL;   // D&C only
+    int64_t T_max = 1;
+    for (int64_t i = 0; i < n; i++) T_max = std::max<int64_t>(T_max, reqs[i].T);
+    const Sched sc = resolve_sched(c, opt, T_max, model_class(n, reqs));
+    *out = aop_options{method, sc.B, opt->flags, sc.cap, sc.lg_tile, sc.radix2 ? 2 : 4};
     return AOP_OK;
 }
 
@@ -577,7 +663,7 @@ aop_status server_launch(aop_server *s) {
     const void *tw = (s->method == AOP_FFT_FP64) ? c->tw64 : c->tw32;
     CK(run_dnc(s->method, s->capacity, nullptr, s->T_max, s->B, c->ws, c->ws_size, tw, c->tw_log2, nullptr,
                nullptr, nullptr, nullptr, s->d_stats, s->d_err, nullptr, s->flags, s->cap, c->device, s->stream,
-               &s->sess));
+               &s->sess, nullptr, nullptr, s->lg_tile, s->radix2));
     return AOP_OK;
 }
 
@@ -609,8 +695,11 @@ aop_status aop_server_create(aop_ctx *c, int64_t capacity, int64_t T_max, const 
     aop_server *s = new aop_server;
     s->ctx = c;
     s->method = method;
-    s->B = resolve_base_case(c, opt);
-    s->cap = (opt && opt->ctas_per_sm > 0) ? opt->ctas_per_sm : c->tuned_cap[method];
+    const Sched sc = resolve_sched(c, opt, T_max, 2);
+    s->B = sc.B;
+    s->cap = sc.cap;
+    s->lg_tile = sc.lg_tile;
+    s->radix2 = sc.radix2;
     s->flags = opt ? (opt->flags & ~AOP_FLAG_OPTION_TIMES) : 0;
     s->T_max = T_max;
     s->capacity = capacity;
@@ -623,7 +712,7 @@ aop_status aop_server_create(aop_ctx *c, int64_t capacity, int64_t T_max, const 
     if (lg < 13) lg = 13;
     if ((st = ensure_twiddles(c, lg))) return fail(st);
     int grid = 0;
-    size_t need = dnc_workspace_bytes(method, capacity, T_max, s->B, s->cap, &grid, c->device);
+    size_t need = dnc_workspace_bytes(method, capacity, T_max, s->B, s->cap, &grid, c->device, s->lg_tile);
     if (c->cap && need > c->cap) need = c->cap;     // admission: the slots the cap holds
     if ((st = ensure(&c->ws, &c->ws_size, need, c->cap))) return fail(st);
     // the slots the workspace holds (the launch clips its grid the same way)

@@ -150,6 +150,7 @@ struct DncArgs {
     int64_t n;
     int B;                 // base-case height (2 .. 64 rows)
     int lg_tile;           // log2 of a worker's shared-memory transform tile
+    int radix2;            // 1: transform stages as radix-2 steps only (else radix 4)
     int lg_block;          // log2 of the block-level tile (linear advance entry points)
     int64_t W_max;         // widest row (doubles)
     char *ws;
@@ -803,8 +804,13 @@ struct Cta {
                     stage_scratch<G>(tile, count, idx, scr);
                 }
                 const fft::Cols cl{lgQ, s_lo, q0};
-                if (DIF) fft::dif_cols<MODE, G>(tile, L, L - 1, 0, cl, T);
-                else fft::dit_cols<MODE, G>(tile, L, 0, L - 1, cl, T);
+                if (a.radix2) {
+                    if (DIF) fft::dif_cols_r2<MODE, G>(tile, L, L - 1, 0, cl, T);
+                    else fft::dit_cols_r2<MODE, G>(tile, L, 0, L - 1, cl, T);
+                } else {
+                    if (DIF) fft::dif_cols<MODE, G>(tile, L, L - 1, 0, cl, T);
+                    else fft::dit_cols<MODE, G>(tile, L, 0, L - 1, cl, T);
+                }
                 for (int s = G::rank(); s < count; s += G::size()) {
                     const int e = idx(s);
                     if (last) {
@@ -866,10 +872,10 @@ struct Cta {
                 const long long q1 = clock64();
                 stage_packed<G, ST>(tile, (int)N / 2, [](int s) { return s; }, in, x_lo, W);
                 const long long q2 = clock64();
-                fft::dif_all<MODE, G>(tile, lgN - 1, T);
+                fft::dif_all<MODE, G>(tile, lgN - 1, T, a.radix2);
                 real_pairs<G>(tile, false, 0, lgN - 1, lgN - 1, sp, mc, g);
                 const long long q3 = clock64();
-                fft::dit_all<MODE, G>(tile, lgN - 1, T);
+                fft::dit_all<MODE, G>(tile, lgN - 1, T, a.radix2);
                 const long long q4 = clock64();
                 for (int64_t t = G::rank(); t < nout; t += G::size()) {
                     const int64_t p = off + t;            // odd cells in the imaginary part
@@ -891,10 +897,10 @@ struct Cta {
             const long long q1 = clock64();
             stage_input<G, ST>(tile, (int)N, [](int s) { return s; }, in, x_lo, W);
             const long long q2 = clock64();
-            fft::dif_all<MODE, G>(tile, lgN, T);
+            fft::dif_all<MODE, G>(tile, lgN, T, a.radix2);
             product<G>(tile, (int)N, 0u, lgN, sp, mc, g);
             const long long q3 = clock64();
-            fft::dit_all<MODE, G>(tile, lgN, T);
+            fft::dit_all<MODE, G>(tile, lgN, T, a.radix2);
             const long long q4 = clock64();
             for (int64_t t = G::rank(); t < nout; t += G::size())
                 store<ST>(out, y_lo + t, untilt<ST>(ST::from_v(tile[off + t], cs), W - 1 - t, cs));
@@ -941,11 +947,11 @@ struct Cta {
                     fft::cp_async<(int)sizeof(V)>(&tile[s], s < Bs ? &blk1[s] : &blk2[s - Bs], (int)sizeof(V));
                 fft::cp_async_wait();
                 G::sync();
-                fft::dif_all<MODE, G>(tile, lti, T);
-                if (two) fft::dif_all<MODE, G>(tile + Bs, lti, T);
+                fft::dif_all<MODE, G>(tile, lti, T, a.radix2);
+                if (two) fft::dif_all<MODE, G>(tile + Bs, lti, T, a.radix2);
                 real_pairs<G>(tile, two, rb, lgM, lti, sp, mc, g);
-                fft::dit_all<MODE, G>(tile, lti, T);
-                if (two) fft::dit_all<MODE, G>(tile + Bs, lti, T);
+                fft::dit_all<MODE, G>(tile, lti, T, a.radix2);
+                if (two) fft::dit_all<MODE, G>(tile + Bs, lti, T, a.radix2);
                 for (int s = G::rank(); s < cnt2; s += G::size()) {
                     if (s < Bs) blk1[s] = tile[s];
                     else blk2[s - Bs] = tile[s];
@@ -979,9 +985,9 @@ struct Cta {
         for (int b = 0; b < (int)(N / N2); b++) {
             V *blk = scr + (int64_t)b * N2;
             stage_scratch<G>(tile, N2, [](int s) { return s; }, blk);
-            fft::dif_all<MODE, G>(tile, lg_tile, T);
+            fft::dif_all<MODE, G>(tile, lg_tile, T, a.radix2);
             product<G>(tile, N2, (uint32_t)(b * N2), lgN, sp, mc, g);
-            fft::dit_all<MODE, G>(tile, lg_tile, T);
+            fft::dit_all<MODE, G>(tile, lg_tile, T, a.radix2);
             for (int s = G::rank(); s < N2; s += G::size()) blk[s] = tile[s];
             G::sync();
         }
@@ -1239,9 +1245,102 @@ struct Walker {
         return c0 + bn;
     }
 
+    // Doubled-FP32 rows with each lane holding R contiguous cells t = R l + c:
+    // a row needs only the D cells right of a lane's last cell, from the next
+    // lane (D shuffles of a pair); each cell carries its node price, multiplied
+    // by u once per row (moving down a row raises the price exponent by one),
+    // and its exercise value is that price less K; the divider is one maximum
+    // over the lanes.  The cells and their values are those of call_rows: every
+    // cell takes max(continuation, exercise) (Def. 2.1), the cells right of
+    // the top row's divider stay green (Cor. 2.7).  The price recurrence adds
+    // at most a few units of 2^-48 relative a row over the <= 64 rows of a
+    // base case.
+    template <int R, int D>
+    __device__ int64_t call_rows_df(int64_t i0, int64_t c0, int64_t b, int64_t h, const Buf &in, const Buf &out,
+                                    int64_t klo) {
+        using A = ArithDF;
+        const A::Wts w = A::weights(S);
+        const int alpha = (P.model == AOP_BINOMIAL_CALL) ? 2 : 1;
+        const int sbase = (int)(alpha * c0 - i0 + P.T - klo);   // u-table slot of cell (0, t): sbase + alpha t
+        const int clip0 = (int)((int64_t)D * i0 - c0);         // row i0 - k ends at column clip0 - D k
+        const int hh = (int)h;
+        const int tb = (int)(b - c0);
+        int32_t *const rec = (lane == 0 && bnd) ? bnd + i0 : nullptr;   // rec[-k] = row i0 - k
+        const float2 an = to_df(exp_from_tables(E, klo));      // node price of exponent index klo
+        const float2 u = S.updf[1];
+        const float2 K = S.kdf;
+        float2 val[R], px[R];
+#pragma unroll
+        for (int c = 0; c < R; c++) {
+            const int t = R * lane + c;
+            const float2 g = S.updf[min(max(sbase + alpha * t, 0), kNaiveCap - 1)];
+            fft::df_mul(an.x, an.y, g.x, g.y, px[c].x, px[c].y);
+            float2 e0;
+            fft::df_add(px[c].x, px[c].y, -K.x, -K.y, e0.x, e0.y);
+            val[c] = A::zero();
+            if (t <= tb) val[c] = A::template load<MODE>(in, c0 + t);
+            else if (t <= tb + D) val[c] = e0;
+        }
+        int bn = tb;
+        long long cells = 0;
+        const long long lc0 = clock64();
+        for (int k = 1; k <= hh; k++) {
+            const int lim = min(tb, clip0 - D * k);   // last real cell of the window in this row
+            const int bprev = bn;
+            const float2 s1 = A::shfl(val[0], (lane + 1) & 31);
+            float2 s2 = A::zero();
+            if (D == 2) s2 = (R == 1) ? A::shfl(val[0], (lane + 2) & 31) : A::shfl(val[R > 1 ? 1 : 0], (lane + 1) & 31);
+            int last = -1;
+#pragma unroll
+            for (int c = 0; c < R; c++) {
+                const int t = R * lane + c;
+                const float2 a1 = (c + 1 < R) ? val[(c + 1) % R] : s1;
+                float2 cont;
+                if (D == 2) {
+                    const float2 a2 = (c + 2 < R) ? val[(c + 2) % R] : ((c + 2 == R) ? s1 : s2);
+                    cont = A::dot3(w, val[c], a1, a2);
+                } else {
+                    cont = A::dot2(w, val[c], a1);
+                }
+                fft::df_mul(px[c].x, px[c].y, u.x, u.y, px[c].x, px[c].y);
+                float2 ex;
+                fft::df_add(px[c].x, px[c].y, -K.x, -K.y, ex.x, ex.y);
+                const bool red = A::cont_ge(cont, ex);
+                val[c] = (red && t <= tb) ? cont : ex;
+                if (red && t <= lim) last = t;
+            }
+            const int nbn = __reduce_max_sync(0xffffffffu, last);
+            // the previous row's divider is stored after this row's shuffles
+            if (k > 1 && rec) rec[-(k - 1)] = (int32_t)(c0 + bprev);
+            bn = nbn;
+            cells += max(lim + 1, 0);
+        }
+        if (hh >= 1 && rec) rec[-hh] = (int32_t)(c0 + bn);
+        if (lane == 0) cnt.loop_cyc += clock64() - lc0;
+#pragma unroll
+        for (int c = 0; c < R; c++) {
+            const int t = R * lane + c;
+            if (t <= bn) A::template store<MODE>(out, c0 + t, val[c]);
+        }
+        if (lane == 0) cnt.base_cells += cells;
+        return c0 + bn;
+    }
+
     template <class A>
     __device__ int64_t call_dispatch(int64_t need, int64_t i0, int64_t c0, int64_t b, int64_t h, const Buf &in,
                                      const Buf &out, int64_t klo, int64_t khi) {
+        if (std::is_same<A, ArithDF>::value) {   // no table: prices carried in registers
+            if (P.D == 1) {
+                if (need <= 32) return call_rows_df<1, 1>(i0, c0, b, h, in, out, klo);
+                if (need <= 64) return call_rows_df<2, 1>(i0, c0, b, h, in, out, klo);
+                if (need <= 128) return call_rows_df<4, 1>(i0, c0, b, h, in, out, klo);
+                return call_rows_df<8, 1>(i0, c0, b, h, in, out, klo);
+            }
+            if (need <= 32) return call_rows_df<1, 2>(i0, c0, b, h, in, out, klo);
+            if (need <= 64) return call_rows_df<2, 2>(i0, c0, b, h, in, out, klo);
+            if (need <= 128) return call_rows_df<4, 2>(i0, c0, b, h, in, out, klo);
+            return call_rows_df<8, 2>(i0, c0, b, h, in, out, klo);
+        }
         const long long fc0 = clock64();
         A::fill(S, (typename A::T *)exw, klo, khi, lane);
         __syncwarp();
@@ -2005,12 +2104,12 @@ int value_bytes(int method) {
     return method == AOP_FFT_FP32SPLIT ? 8 : 16;
 }
 
-Layout make_layout(int method, int64_t T_max, int B, int scratch_units) {
+Layout make_layout(int method, int64_t T_max, int B, int scratch_units, int lg_tile) {
     Layout L;
     L.vsz = value_bytes(method);
     L.W_max = 2 * T_max + 1;
     L.N_max = (int64_t)1 << ilog2_ceil(L.W_max);
-    L.lg_tile = 10;                           // 8 KiB (FP32 split) or 16 KiB per worker tile
+    L.lg_tile = lg_tile;                      // 2^10: 8 KiB (FP32 split) or 16 KiB per worker tile
     L.lg_block = (L.vsz == 8) ? 12 : 11;     // 32 KiB block tile (linear advance entry points)
     L.tw_log2 = std::max(ilog2_ceil(L.N_max), L.lg_block + 1);
     L.spec_cap = std::max<int64_t>(1 << 17, L.N_max / 2 + 2);
@@ -2114,8 +2213,8 @@ int dnc_per_sm(int method, int64_t n, size_t smem, int cap, int device) {
 
 // Options in flight per SM that the pricing kernel's registers and shared
 // memory allow (the autotuner tries no more).
-int dnc_max_per_sm(int method, int64_t T_max, int base_case) {
-    Layout L = make_layout(method, T_max, base_case, shape_big(method));
+int dnc_max_per_sm(int method, int64_t T_max, int base_case, int lg_tile) {
+    Layout L = make_layout(method, T_max, base_case, shape_big(method), lg_tile);
     return ctas_per_sm(method, L.smem);
 }
 
@@ -2126,12 +2225,13 @@ int64_t dnc_grid(int method, int64_t n, size_t smem, int cap, int device) {
 
 size_t dnc_slot_bytes(int method, int64_t T_max, int base_case)
 {
-    return (size_t)make_layout(method, T_max, base_case, shape_big(method)).stride;
+    return (size_t)make_layout(method, T_max, base_case, shape_big(method), kDefaultLgTile).stride;   // independent of the tile
 }
 
-size_t dnc_workspace_bytes(int method, int64_t n, int64_t T_max, int base_case, int cap, int *grid_out, int device)
+size_t dnc_workspace_bytes(int method, int64_t n, int64_t T_max, int base_case, int cap, int *grid_out, int device,
+                           int lg_tile)
 {
-    Layout L = make_layout(method, T_max, base_case, shape_big(method));
+    Layout L = make_layout(method, T_max, base_case, shape_big(method), lg_tile);
     int64_t grid = dnc_grid(method, n, L.smem, cap, device);
     if (grid < 1) grid = 1;
     if (grid_out) *grid_out = (int)grid;
@@ -2142,11 +2242,13 @@ cudaError_t run_dnc(int method, int64_t n, const Params *d_params, int64_t T_max
                     void *ws, size_t ws_bytes, const void *d_tw, int tw_log2, double *d_prices,
                     int32_t *d_status, int32_t *d_bnd, const int64_t *d_bnd_off,
                     aop_stats *d_stats, int *d_err, int64_t *d_opt_ns, int flags, int cap, int device,
-                    cudaStream_t s, const ServeSession *srv, const int32_t *d_order, double *d_greeks)
+                    cudaStream_t s, const ServeSession *srv, const int32_t *d_order, double *d_greeks,
+                    int lg_tile, int radix2)
 {
     if (srv) n = srv->capacity;
     if (n == 0) return cudaSuccess;
-    Layout L = make_layout(method, T_max, base_case, shape_big(method));
+    if (lg_tile < 9 || lg_tile > 11) return cudaErrorInvalidValue;
+    Layout L = make_layout(method, T_max, base_case, shape_big(method), lg_tile);
     if (tw_log2 < L.tw_log2) return cudaErrorInvalidValue;
     int64_t grid = dnc_grid(method, n, L.smem, cap, device);
     const size_t need = (size_t)(grid * L.stride) + 8192;
@@ -2164,6 +2266,7 @@ cudaError_t run_dnc(int method, int64_t n, const Params *d_params, int64_t T_max
     a.n = n;
     a.B = base_case;
     a.lg_tile = L.lg_tile;
+    a.radix2 = radix2 ? 1 : 0;
     a.lg_block = L.lg_block;
     a.W_max = L.W_max;
     a.ws = base;
@@ -2355,7 +2458,7 @@ Params advance_params(int nw, const double *w) {
 size_t linear_advance_workspace_bytes(int method, int64_t W, int64_t h)
 {
     (void)h;
-    Layout L = make_layout(method, (W + 1) / 2 + 1, 16, 1);
+    Layout L = make_layout(method, (W + 1) / 2 + 1, 16, 1, kDefaultLgTile);
     return (size_t)(L.stride * 64 + 4096);
 }
 
@@ -2363,7 +2466,7 @@ cudaError_t run_linear_advance(int method, int nw, const double *w, int64_t coun
                                const double *d_in, double *d_out, const void *d_tw, int tw_log2,
                                void *ws, size_t ws_bytes, int *d_err, cudaStream_t s)
 {
-    Layout L = make_layout(method, (W + 1) / 2 + 1, 16, 1);
+    Layout L = make_layout(method, (W + 1) / 2 + 1, 16, 1, kDefaultLgTile);
     int64_t grid = std::min<int64_t>(count, 64);
     if ((size_t)(grid * L.stride) > ws_bytes) grid = (int64_t)(ws_bytes / L.stride);
     if (grid < 1) return cudaErrorMemoryAllocation;
@@ -2390,7 +2493,7 @@ cudaError_t run_linear_advance(int method, int nw, const double *w, int64_t coun
 
 size_t european_workspace_bytes(int64_t n, int64_t T_max, int *grid_out, int device)
 {
-    Layout L = make_layout(AOP_FFT_FP64, T_max, 16, 1);
+    Layout L = make_layout(AOP_FFT_FP64, T_max, 16, 1, kDefaultLgTile);
     const int64_t grid = std::max<int64_t>(1, std::min<int64_t>(n, (int64_t)sm_count(device) * 2));
     if (grid_out) *grid_out = (int)grid;
     return (size_t)(grid * L.stride);
@@ -2401,7 +2504,7 @@ cudaError_t run_european(int64_t n, const Params *d_params, int64_t T_max, void 
                          cudaStream_t s)
 {
     if (n == 0) return cudaSuccess;
-    Layout L = make_layout(AOP_FFT_FP64, T_max, 16, 1);
+    Layout L = make_layout(AOP_FFT_FP64, T_max, 16, 1, kDefaultLgTile);
     if (tw_log2 < L.tw_log2) return cudaErrorInvalidValue;
     int64_t grid = std::max<int64_t>(1, std::min<int64_t>(n, (int64_t)sm_count(device) * 2));
     if ((size_t)(grid * L.stride) > ws_bytes) grid = (int64_t)(ws_bytes / L.stride);

@@ -383,14 +383,34 @@ __device__ __noinline__ void dit_cols(V *x, int lgR, int lgMlo, int lgMhi, Cols 
         G::sync();
     }
 }
-// Whole transforms of a plain tile of 2^lgN points.
+// The same stage ranges as radix-2 steps only: a transform schedule the
+// autotuner may pick.  Separate out-of-line copies, so that the radix-4 code
+// the default schedule runs is unchanged (the pricing kernel is sensitive to
+// the size of its hot code).
 template <int MODE, class G, class V>
-__device__ void dif_all(V *x, int lgN, const typename Cx<MODE>::Tw *tw) {
-    dif_cols<MODE, G>(x, lgN, lgN - 1, 0, Cols{0, 0, 0}, tw);
+__device__ __noinline__ void dif_cols_r2(V *x, int lgR, int lgMhi, int lgMlo, Cols c, const typename Cx<MODE>::Tw *tw) {
+    for (int lg = lgMhi; lg >= lgMlo; lg--) {
+        dif2c<MODE, G>(x, 1 << (lgR + c.lgQ - 1), lg, c, tw);
+        G::sync();
+    }
 }
 template <int MODE, class G, class V>
-__device__ void dit_all(V *x, int lgN, const typename Cx<MODE>::Tw *tw) {
-    dit_cols<MODE, G>(x, lgN, 0, lgN - 1, Cols{0, 0, 0}, tw);
+__device__ __noinline__ void dit_cols_r2(V *x, int lgR, int lgMlo, int lgMhi, Cols c, const typename Cx<MODE>::Tw *tw) {
+    for (int lg = lgMlo; lg <= lgMhi; lg++) {
+        dit2c<MODE, G>(x, 1 << (lgR + c.lgQ - 1), lg, c, tw);
+        G::sync();
+    }
+}
+// Whole transforms of a plain tile of 2^lgN points (r2: radix-2 steps only).
+template <int MODE, class G, class V>
+__device__ void dif_all(V *x, int lgN, const typename Cx<MODE>::Tw *tw, int r2 = 0) {
+    if (r2) dif_cols_r2<MODE, G>(x, lgN, lgN - 1, 0, Cols{0, 0, 0}, tw);
+    else dif_cols<MODE, G>(x, lgN, lgN - 1, 0, Cols{0, 0, 0}, tw);
+}
+template <int MODE, class G, class V>
+__device__ void dit_all(V *x, int lgN, const typename Cx<MODE>::Tw *tw, int r2 = 0) {
+    if (r2) dit_cols_r2<MODE, G>(x, lgN, 0, lgN - 1, Cols{0, 0, 0}, tw);
+    else dit_cols<MODE, G>(x, lgN, 0, lgN - 1, Cols{0, 0, 0}, tw);
 }
 
 // ------------------------------------------------- value conversions by mode

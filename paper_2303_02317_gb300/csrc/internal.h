@@ -49,12 +49,14 @@ cudaError_t run_stencil(int64_t n, const Params *d_params, int64_t T_max, void *
                         const int64_t *d_bnd_off, aop_stats *d_stats, cudaStream_t s, bool df);
 
 // dnc.cu -- trapezoidal divide-and-conquer pricer
-int dnc_max_per_sm(int method, int64_t T_max, int base_case);
+// log2 of a worker's transform tile unless a schedule says otherwise
+constexpr int kDefaultLgTile = 10;
+int dnc_max_per_sm(int method, int64_t T_max, int base_case, int lg_tile = kDefaultLgTile);
 // per-option workspace of the pricing kernel (one slot), without the
 // launch's 8 KiB of queue words
 size_t dnc_slot_bytes(int method, int64_t T_max, int base_case);
 size_t dnc_workspace_bytes(int method, int64_t n, int64_t T_max, int base_case, int cap, int *grid_out,
-                           int device);
+                           int device, int lg_tile = kDefaultLgTile);
 // A serving session's host-shared state (see aop_server_* in the header):
 // requests and results live in mapped host memory, the claim counter on the
 // device.  run_dnc with a session prices the published requests in order of
@@ -75,7 +77,7 @@ cudaError_t run_dnc(int method, int64_t n, const Params *d_params, int64_t T_max
                     int32_t *d_status, int32_t *d_bnd, const int64_t *d_bnd_off,
                     aop_stats *d_stats, int *d_err, int64_t *d_opt_ns, int flags, int cap, int device,
                     cudaStream_t s, const ServeSession *srv = nullptr, const int32_t *d_order = nullptr,
-                    double *d_greeks = nullptr);
+                    double *d_greeks = nullptr, int lg_tile = kDefaultLgTile, int radix2 = 0);
 cudaError_t run_linear_advance(int method, int nw, const double *w, int64_t count, int64_t W,
                                int64_t h, const double *d_in, double *d_out, const void *d_tw,
                                int tw_log2, void *ws, size_t ws_bytes, int *d_err,

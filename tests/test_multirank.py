@@ -65,12 +65,18 @@ def test_captured_traffic_only_for_the_captured_sources(monkeypatch):
     assert bench.captured_traffic("df32") is None
 
 
-def test_stencil_flops_counts_the_lattice_cells():
-    """(D+1) products and D sums per cell: T(T+1)/2 binomial cells, T^2
-    trinomial or BSM cells."""
+def test_lattice_cells_and_stencil_floor():
+    """The plain stencil's cell count: T(T+1)/2 binomial cells, T^2 trinomial
+    or BSM cells; its relative distance skips near-zero prices (below 1e-3 K)."""
+    import numpy as np
     import bench
     from paper_2303_02317_gb300 import workloads as wl
     T = 100
-    assert bench.stencil_flops([wl.fixed_call(0, T)]) == 3.0 * T * (T + 1) / 2
-    assert bench.stencil_flops([wl.fixed_call(1, T)]) == 5.0 * T * T
-    assert bench.stencil_flops([wl.fixed_bsm_put(T)]) == 5.0 * T * T
+    assert bench.lattice_cells(wl.fixed_call(0, T)) == T * (T + 1) / 2
+    assert bench.lattice_cells(wl.fixed_call(1, T)) == T * T
+    assert bench.lattice_cells(wl.fixed_bsm_put(T)) == T * T
+    reqs = [wl.fixed_call(0, T), wl.fixed_call(1, T)]
+    ref = np.array([10.0, 1e-9])
+    got = np.array([10.0 * (1 + 1e-9), 2e-9])
+    ok = np.array([True, True])
+    assert abs(bench.max_rel_floor(ref, got, ok, reqs) - 1e-9) < 1e-15
