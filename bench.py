@@ -384,6 +384,42 @@ def serve_stream(ctx, aop, wl, method, args, stencil_method=None):
     return out
 
 
+def run_profile_case(args):
+    """One small invocation of one kernel, three times after one warm-up, for
+    profiler captures (the bench's own workload is too large for a full-set
+    capture):
+      stencil_df32 / stencil_fp64 -- the plain stencil on 4 options of the
+          precision-sweep mix at T = 8192 (2 binomial, 2 trinomial);
+      european -- 64 European counterparts of that mix at T = 2^15;
+      dnc_small -- the doubled-FP32 D&C on the reduced book (152 binomial +
+          152 trinomial calls at T = 2^15, two per SM, base case 63).
+    Prints the kernel time of each run (CUDA events on the launch stream)."""
+    import paper_2303_02317_gb300 as aop
+    from paper_2303_02317_gb300 import workloads as wl
+    ctx = aop.Context(0)
+    case = args.profile_case
+    out = []
+    for k in range(4):
+        if case in ("stencil_df32", "stencil_fp64"):
+            reqs = wl.precision_sweep(T=8192, n_binomial=2, n_trinomial=2)
+            m = aop.STENCIL_DF32 if case == "stencil_df32" else aop.STENCIL_FP64
+            p, st = ctx.price_batch(reqs, method=m)
+        elif case == "european":
+            reqs = wl.precision_sweep(T=1 << 15, n_binomial=32, n_trinomial=32)
+            p, st = ctx.price_european(reqs)
+        elif case == "dnc_small":
+            reqs = wl.precision_sweep(T=1 << 15, n_binomial=152, n_trinomial=152)
+            p, st = ctx.price_batch(reqs, method=aop.FFT_DF32, base_case=63, ctas_per_sm=2)
+        else:
+            raise SystemExit("unknown --profile-case %s" % case)
+        if (np.asarray(st) != 0).any():
+            raise SystemExit("profile case %s: status %s" % (case, np.unique(st)))
+        if k:
+            out.append(ctx.stats()["kernel_ms"] if case != "european" else None)
+    print(json.dumps({"profile_case": case, "kernel_ms": out, "stats": ctx.stats()}))
+    ctx.close()
+
+
 def run_configs(args):
     """Single-option latency of the fixed configurations on one GPU: C1 (binomial
     call, T = 2048, with its boundary checked against the oracle), C2 (binomial
@@ -510,9 +546,14 @@ def main():
     ap.add_argument("--configs", action="store_true",
                     help="single-option latency tables of the fixed configurations (C1-C3) instead of the book")
     ap.add_argument("--config-runs", type=int, default=10)
+    ap.add_argument("--profile-case", default=None,
+                    choices=["stencil_df32", "stencil_fp64", "european", "dnc_small"],
+                    help="one small invocation of one kernel (for profiler captures) instead of the bench")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.profile_case:
+        return run_profile_case(args)
     if args.configs:
         return run_configs(args)
     args.warmup = max(args.warmup, 3)
