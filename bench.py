@@ -388,11 +388,17 @@ def run_profile_case(args):
     """One small invocation of one kernel, three times after one warm-up, for
     profiler captures (the bench's own workload is too large for a full-set
     capture):
-      stencil_df32 / stencil_fp64 -- the plain stencil on 4 options of the
-          precision-sweep mix at T = 8192 (2 binomial, 2 trinomial);
+      stencil_df32 / stencil_fp64 -- the plain stencil on 16 options of the
+          precision-sweep mix at T = 2^15 (8 binomial, 8 trinomial: about 1 950
+          warp tiles in the first launches, enough to fill the GPU);
       european -- 64 European counterparts of that mix at T = 2^15;
       dnc_small -- the doubled-FP32 D&C on the reduced book (152 binomial +
-          152 trinomial calls at T = 2^15, two per SM, base case 63).
+          152 trinomial calls at T = 2^15, two per SM, base case 63);
+      dnc_part -- the doubled-FP32 D&C on 76 options of the book itself
+          (the first 38 binomial and 38 trinomial calls at T = 2^17, base case
+          63): its DRAM traffic per option stands for the book's, whose
+          per-option scratch (35 MB) far exceeds L2 whatever the options in
+          flight.
     Prints the kernel time of each run (CUDA events on the launch stream)."""
     import paper_2303_02317_gb300 as aop
     from paper_2303_02317_gb300 import workloads as wl
@@ -401,12 +407,16 @@ def run_profile_case(args):
     out = []
     for k in range(4):
         if case in ("stencil_df32", "stencil_fp64"):
-            reqs = wl.precision_sweep(T=8192, n_binomial=2, n_trinomial=2)
+            reqs = wl.precision_sweep(T=1 << 15, n_binomial=8, n_trinomial=8)
             m = aop.STENCIL_DF32 if case == "stencil_df32" else aop.STENCIL_FP64
             p, st = ctx.price_batch(reqs, method=m)
         elif case == "european":
             reqs = wl.precision_sweep(T=1 << 15, n_binomial=32, n_trinomial=32)
             p, st = ctx.price_european(reqs)
+        elif case == "dnc_part":
+            book = wl.precision_sweep(T=T_BENCH, n_binomial=N_BINOMIAL, n_trinomial=N_TRINOMIAL)
+            reqs = book[:38] + book[N_BINOMIAL:N_BINOMIAL + 38]
+            p, st = ctx.price_batch(reqs, method=aop.FFT_DF32, base_case=63, ctas_per_sm=2)
         elif case == "dnc_small":
             reqs = wl.precision_sweep(T=1 << 15, n_binomial=152, n_trinomial=152)
             p, st = ctx.price_batch(reqs, method=aop.FFT_DF32, base_case=63, ctas_per_sm=2)
@@ -547,7 +557,7 @@ def main():
                     help="single-option latency tables of the fixed configurations (C1-C3) instead of the book")
     ap.add_argument("--config-runs", type=int, default=10)
     ap.add_argument("--profile-case", default=None,
-                    choices=["stencil_df32", "stencil_fp64", "european", "dnc_small"],
+                    choices=["stencil_df32", "stencil_fp64", "european", "dnc_small", "dnc_part"],
                     help="one small invocation of one kernel (for profiler captures) instead of the bench")
     args = ap.parse_args()
     if args.impl == "reference":
