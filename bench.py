@@ -48,15 +48,15 @@ MEASURED_ALU = {}
 WORKLOAD = "precision_sweep_T131072_256binomial_256trinomial"
 
 # DRAM traffic of one launch of the pricing kernel on this book, from one
-# ncu capture (dram__bytes_read.sum + dram__bytes_write.sum, one-pass launch
-# list of `bench.py --steps 2 --warmup 3 --schedule 63:2 --no-cpu-baseline
-# --stencil-sample 0 --serve-n 0`, summarised with the launch list under
-# profiles/).  It holds for the kernel
-# sources whose SHA-256 is recorded with it; any other source reports null.
+# ncu capture (dram__bytes_read.sum + dram__bytes_write.sum, one pass, of the
+# fourth launch of `bench.py --steps 1 --warmup 3 --schedule 63:2 --serve-n 0
+# --stencil-sample 0 --no-cpu-baseline --no-fp32`, summarised under profiles/).
+# It holds for the kernel sources whose SHA-256 is recorded with it; any other
+# source reports null.
 KERNEL_SOURCES = ("paper_2303_02317_gb300/csrc/dnc.cu", "paper_2303_02317_gb300/csrc/fft.cuh",
                   "paper_2303_02317_gb300/csrc/common.cuh")
-TRAFFIC_CAPTURE = {"sources_sha256": "f53730896269e4cc6925b7428147243892d92bacafc0c5fa053ef9ba7361ad9f",
-                   "bytes_per_launch": {"df32": 29993e6, "fft32": 37773e6, "fft64": 32194e6}}
+TRAFFIC_CAPTURE = {"sources_sha256": "f603c72036a9efd82cb98974fc55bde12ee7f148da3bbed5865d604fb850934b",
+                   "bytes_per_launch": {"df32": 13230298112 + 17697210624}}
 
 
 def kernel_sources_sha256() -> str:
@@ -542,8 +542,9 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--method", default="df32", choices=["fft32", "fft64", "df32"])
     ap.add_argument("--no-tune", action="store_true", help="library default schedule, no autotuning")
-    ap.add_argument("--schedule", default=None, metavar="B:CAP",
-                    help="base-case height and options in flight per SM of the priced method, no autotuning")
+    ap.add_argument("--schedule", default=None, metavar="B:CAP[:LG[:RADIX]]",
+                    help="base-case height, options in flight per SM[, log2 transform tile[, radix]] of the "
+                         "priced method, no autotuning")
     ap.add_argument("--no-fp32", action="store_true", help="skip the split-FP32 side measurement")
     ap.add_argument("--serve-n", type=int, default=65536,
                     help="requests of the serving stream (Poisson 20k/s, mixed models, T in [2^10, 2^18]); 0 = skip")
@@ -602,8 +603,8 @@ def main():
     tuned = {}
     fixed = {}
     if args.schedule:
-        b, cap = (int(v) for v in args.schedule.split(":"))
-        fixed = {"base_case": b, "ctas_per_sm": cap}
+        parts = [int(v) for v in args.schedule.split(":")]
+        fixed = dict(zip(("base_case", "ctas_per_sm", "lg_tile", "radix"), parts))
         tuned = {"method": dict(fixed)}
     elif not args.no_tune:
         tuned = {"method": ctx.autotune(arr, method)}
@@ -814,6 +815,7 @@ def main():
         "data": "synthetic",
         "config": {"workload": WORKLOAD, "T": T_BENCH, "options_per_step": n,
                    "method": args.method, "schedule": tuned or "library default",
+                   "schedule_in_use": ctx.schedule(arr, method) if not fixed else dict(fixed),
                    "l2": "512 MB buffer written between timed steps",
                    "parallelism": "independent options per rank"},
         "e2e": {"value": whole_job_rate(n, world, e2e_ms), "unit": "options/s",

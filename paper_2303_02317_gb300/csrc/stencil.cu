@@ -38,7 +38,7 @@ namespace aop {
 
 namespace {
 
-constexpr int kRows = 64;       // rows per temporal block (one launch)
+constexpr int kRows = 32;       // rows per temporal block (one launch): 16 KB of exercise slices a warp, three CTAs per SM
 constexpr int kLC = 16;         // cells per lane: a warp tile holds 32 x kLC contiguous cells
 constexpr int kTile = 32 * kLC;
 constexpr int kWarps = 4;       // warp tiles per CTA
