@@ -1452,11 +1452,78 @@ struct Walker {
         return lo + fn;
     }
 
+    // Doubled-FP32 put rows with each lane holding R contiguous cells
+    // t = R l + c of the window (t = x - lo): a row needs the cell left of a
+    // lane's first cell and the one right of its last, from the neighbouring
+    // lanes (two shuffles of a pair); the exercise values (which for the put
+    // do not depend on the time step) stay in registers; every cell takes
+    // max(continuation, exercise) (Def. 2.1 for the put) and the divider -- the
+    // last cell of the row whose exercise value exceeds its continuation -- is
+    // one maximum over the lanes.  The cells and values are those of put_rows.
+    template <int R>
+    __device__ int64_t put_rows_df(int64_t n, int64_t lo, int64_t hi, int64_t f, int64_t h, const Buf &in,
+                                   const Buf &out) {
+        using A = ArithDF;
+        const A::Wts w = A::weights(S);
+        const float2 *ext = (const float2 *)exw;
+        const int span = (int)(hi - lo);          // window cells 0 .. span
+        const int fl = (int)(f - lo);             // divider of row n, relative to lo
+        float2 val[R], ex[R];
+#pragma unroll
+        for (int c = 0; c < R; c++) {
+            const int t = R * lane + c;
+            ex[c] = ext[min(t, span)];
+            val[c] = A::zero();
+            if (t <= span) val[c] = (t <= fl) ? ex[c] : A::template load<MODE>(in, lo + t);
+        }
+        int32_t *const rec = (lane == 0) ? bnd : nullptr;
+        const int hh = (int)h;
+        int fn = fl;
+        long long cells = 0;
+        for (int k = 1; k <= hh; k++) {
+            const int fprev = fn;
+            const float2 left = A::shfl(val[R - 1], (lane + 31) & 31);
+            const float2 right = A::shfl(val[0], (lane + 1) & 31);
+            float2 prev = left;
+            int last = -1;
+#pragma unroll
+            for (int c = 0; c < R; c++) {
+                const int t = R * lane + c;
+                const float2 nxt = (c + 1 < R) ? val[(c + 1) % R] : right;
+                const float2 cv = A::dot3(w, prev, val[c], nxt);
+                prev = val[c];
+                const bool green = A::ex_gt(ex[c], cv);
+                val[c] = green ? ex[c] : cv;
+                if (green && t >= k && t <= span - k) last = t;
+            }
+            const int m = __reduce_max_sync(0xffffffffu, last);
+            // the previous row's divider is stored after this row's shuffles
+            if (k > 1 && rec)
+                rec[n + k - 1] = (fprev >= k - 1) ? (int32_t)(lo + fprev) : (int32_t)AOP_BOUNDARY_NONE_PUT;
+            fn = (m >= k) ? m : k - 1;            // none: left of this row's window
+            cells += span - 2 * k + 1;
+        }
+        if (hh >= 1 && rec) rec[n + hh] = (fn >= hh) ? (int32_t)(lo + fn) : (int32_t)AOP_BOUNDARY_NONE_PUT;
+#pragma unroll
+        for (int c = 0; c < R; c++) {
+            const int t = R * lane + c;
+            if (t >= max(hh, fn + 1) && t <= span - hh) A::template store<MODE>(out, lo + t, val[c]);
+        }
+        if (lane == 0) cnt.base_cells += cells;
+        return lo + fn;
+    }
+
     template <class A>
     __device__ int64_t put_dispatch(int64_t w, int64_t n, int64_t lo, int64_t hi, int64_t f, int64_t h,
                                     const Buf &in, const Buf &out) {
         A::fill(S, (typename A::T *)exw, ex_index(P, n, lo), ex_index(P, n, hi), lane);
         __syncwarp();
+        if (std::is_same<A, ArithDF>::value) {
+            if (w <= 32) return put_rows_df<1>(n, lo, hi, f, h, in, out);
+            if (w <= 64) return put_rows_df<2>(n, lo, hi, f, h, in, out);
+            if (w <= 128) return put_rows_df<4>(n, lo, hi, f, h, in, out);
+            return put_rows_df<8>(n, lo, hi, f, h, in, out);
+        }
         if (w <= 32) return put_rows<1, A>(n, lo, hi, f, h, in, out);
         if (w <= 64) return put_rows<2, A>(n, lo, hi, f, h, in, out);
         if (w <= 128) return put_rows<4, A>(n, lo, hi, f, h, in, out);
