@@ -134,7 +134,9 @@ typedef struct aop_request {
 
 typedef struct aop_options {
     int32_t method;     /* aop_method */
-    int32_t base_case;  /* D&C base-case height in rows (2 .. 64, clamped); 0 = tuned default */
+    int32_t base_case;  /* D&C base-case height in rows (2 .. 64, clamped) for every option of the call;
+                           0 = the context's tuned pick, else 63 for the lattices and 31 for the
+                           BSM put (whose base-case windows are four heights wide) */
     int32_t flags;      /* AOP_FLAG_* bits, 0 for none */
     int32_t ctas_per_sm; /* D&C: options in flight per SM; 0 = as many as fit */
     int32_t lg_tile;    /* D&C: log2 of a worker's shared-memory transform tile, 9 .. 11; 0 = tuned default */

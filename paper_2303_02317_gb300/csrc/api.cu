@@ -47,7 +47,7 @@ struct aop_ctx {
 struct aop_server {
     aop_ctx *ctx = nullptr;
     cudaStream_t stream = nullptr;   // the persistent pricing kernel's stream
-    int method = 0, B = 0, cap = 0, flags = 0, slots = 0, lg_tile = 0, radix2 = 0;
+    int method = 0, B = 0, cap = 0, flags = 0, slots = 0, lg_tile = 0, radix2 = 0, Bput = 0;
     int64_t T_max = 0, capacity = 0;
     // host memory mapped into the device: requests in, results out
     aop_request *h_reqs = nullptr;
@@ -71,7 +71,9 @@ constexpr int kDefaultBaseCase = 63;    // the tuner's usual pick: strips fill w
 // as fit), log2 of a worker's transform tile, radix-2-only transform stages.
 struct Sched {
     int B, cap, lg_tile, radix2;
+    int Bput;          // base-case height of BSM puts (their windows are four heights wide)
 };
+constexpr int kDefaultPutBaseCase = 31;   // a put strip of 4B + 1 cells fills four registers
 
 aop_status cuda_fail(cudaError_t e) {
     return e == cudaSuccess ? AOP_OK : (e == cudaErrorMemoryAllocation ? AOP_ENOMEM : AOP_ECUDA);
@@ -168,6 +170,8 @@ Sched resolve_sched(const aop_ctx *c, const aop_options *opt, int64_t T_max, int
     Sched r;
     r.B = (opt && opt->base_case > 0) ? opt->base_case : (t.base_case > 0 ? t.base_case : kDefaultBaseCase);
     r.B = std::min(64, std::max(2, r.B));
+    // puts: an explicit or tuned height applies to them too; untuned, their own default
+    r.Bput = (opt && opt->base_case > 0) ? r.B : (t.base_case > 0 ? r.B : kDefaultPutBaseCase);
     r.cap = (opt && opt->ctas_per_sm > 0) ? opt->ctas_per_sm : t.ctas_per_sm;
     r.lg_tile = (opt && opt->lg_tile > 0) ? opt->lg_tile : (t.lg_tile > 0 ? t.lg_tile : kDefaultLgTile);
     r.lg_tile = std::min(11, std::max(9, r.lg_tile));
@@ -227,7 +231,8 @@ aop_status run_batch(aop_ctx *c, int64_t n, const aop_request *d_reqs, const aop
         if (st) return st;
         int grid = 0;
         const int cap = sc.cap;
-        size_t need = dnc_workspace_bytes(method, n, T_max, B, cap, &grid, c->device, sc.lg_tile);
+        size_t need = dnc_workspace_bytes(method, n, T_max, std::max(B, sc.Bput), cap, &grid, c->device,
+                                          sc.lg_tile);
         size_t have_cap = c->cap ? c->cap : need;
         if (need > have_cap) need = have_cap;   // fewer resident CTAs
         st = ensure(&c->ws, &c->ws_size, need, c->cap);
@@ -244,7 +249,7 @@ aop_status run_batch(aop_ctx *c, int64_t n, const aop_request *d_reqs, const aop
         CK(cudaEventRecord(c->ev0, s));
         CK(run_dnc(method, n, d_params, T_max, B, c->ws, c->ws_size, tw, c->tw_log2, d_prices,
                    d_status, d_bnd, d_bnd_off, c->d_stats, c->d_err, opt_ns, opt ? opt->flags : 0,
-                   cap, c->device, s, nullptr, d_order, d_greeks, sc.lg_tile, sc.radix2));
+                   cap, c->device, s, nullptr, d_order, d_greeks, sc.lg_tile, sc.radix2, sc.Bput));
         CK(cudaEventRecord(c->ev1, s));
     }
     // lattice puts ran as mirrored calls: map their dividers back
@@ -663,7 +668,7 @@ aop_status server_launch(aop_server *s) {
     const void *tw = (s->method == AOP_FFT_FP64) ? c->tw64 : c->tw32;
     CK(run_dnc(s->method, s->capacity, nullptr, s->T_max, s->B, c->ws, c->ws_size, tw, c->tw_log2, nullptr,
                nullptr, nullptr, nullptr, s->d_stats, s->d_err, nullptr, s->flags, s->cap, c->device, s->stream,
-               &s->sess, nullptr, nullptr, s->lg_tile, s->radix2));
+               &s->sess, nullptr, nullptr, s->lg_tile, s->radix2, s->Bput));
     return AOP_OK;
 }
 
@@ -697,6 +702,7 @@ aop_status aop_server_create(aop_ctx *c, int64_t capacity, int64_t T_max, const 
     s->method = method;
     const Sched sc = resolve_sched(c, opt, T_max, 2);
     s->B = sc.B;
+    s->Bput = sc.Bput;
     s->cap = sc.cap;
     s->lg_tile = sc.lg_tile;
     s->radix2 = sc.radix2;
@@ -712,11 +718,12 @@ aop_status aop_server_create(aop_ctx *c, int64_t capacity, int64_t T_max, const 
     if (lg < 13) lg = 13;
     if ((st = ensure_twiddles(c, lg))) return fail(st);
     int grid = 0;
-    size_t need = dnc_workspace_bytes(method, capacity, T_max, s->B, s->cap, &grid, c->device, s->lg_tile);
+    size_t need = dnc_workspace_bytes(method, capacity, T_max, std::max(s->B, s->Bput), s->cap, &grid, c->device,
+                                      s->lg_tile);
     if (c->cap && need > c->cap) need = c->cap;     // admission: the slots the cap holds
     if ((st = ensure(&c->ws, &c->ws_size, need, c->cap))) return fail(st);
     // the slots the workspace holds (the launch clips its grid the same way)
-    const size_t stride = dnc_slot_bytes(method, T_max, s->B);
+    const size_t stride = dnc_slot_bytes(method, T_max, std::max(s->B, s->Bput));
     if (c->ws_size < stride + 8192) return fail(AOP_ENOMEM);
     s->slots = (int)std::min<int64_t>(grid, (int64_t)((c->ws_size - 8192) / stride));
     const size_t per = sizeof(aop_request) + sizeof(double) + 2 * sizeof(int32_t);
@@ -830,7 +837,7 @@ aop_status aop_workspace_bytes(int method, int64_t T_max, int base_case, int64_t
     if (method < 0 || method > 3 || method == AOP_STENCIL_FP64) return AOP_EINVAL;   // D&C only
     aop_options o{method, base_case, 0, 0};
     const int B = resolve_base_case(nullptr, &o);
-    *bytes_out = dnc_slot_bytes(method, T_max, B) * (size_t)options_in_flight + 8192;
+    *bytes_out = dnc_slot_bytes(method, T_max, std::max(B, kDefaultPutBaseCase)) * (size_t)options_in_flight + 8192;
     return AOP_OK;
 }
 

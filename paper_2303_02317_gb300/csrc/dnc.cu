@@ -149,6 +149,7 @@ struct DncArgs {
     const Params *params;
     int64_t n;
     int B;                 // base-case height (2 .. 64 rows)
+    int Bput;              // base-case height of the BSM put (its windows are four heights wide)
     int lg_tile;           // log2 of a worker's shared-memory transform tile
     int radix2;            // 1: transform stages as radix-2 steps only (else radix 4)
     int lg_block;          // log2 of the block-level tile (linear advance entry points)
@@ -398,6 +399,8 @@ struct Cta {
     long long cnt_spec_ns = 0, cnt_spec_bins = 0;   // spectrum builds by this thread's group
 
     __device__ Cta(const DncArgs &a_, Shared &S_, char *slot_) : a(a_), S(S_), slot(slot_) {}
+    // base-case height of the current option
+    __device__ int bcase() const { return S.P.model == AOP_BSM_PUT ? a.Bput : a.B; }
 
     // e^{+kappa n} (0 past the float range) and e^{-kappa n} from the
     // tables, in doubled FP32
@@ -473,7 +476,8 @@ struct Cta {
         // The recursion's heights are the base-case height times powers of
         // two, so g = Bodd * 2^lgg with Bodd the odd part of B.
         const int lgg = g > 0 ? __ffsll((long long)g) - 1 : 0;
-        const bool direct = g > 0 && a.B > 0 && (g >> lgg) == (a.B >> (__ffs(a.B) - 1)) && lgN < kSpecLg &&
+        const int bc = bcase();
+        const bool direct = g > 0 && bc > 0 && (g >> lgg) == (bc >> (__ffs(bc) - 1)) && lgN < kSpecLg &&
                             lgg < kSpecLg;
         if (direct) {
             const int v = S.spec_map[lgg][lgN];
@@ -1763,7 +1767,7 @@ struct Walker {
                     sp--;
                     continue;
                 }
-                if ((F.h <= c.a.B && F.hi - F.lo + 1 <= kRegCells) || F.h < 2 || F.depth + 1 >= kMaxDepth) {
+                if ((F.h <= c.a.Bput && F.hi - F.lo + 1 <= kRegCells) || F.h < 2 || F.depth + 1 >= kMaxDepth) {
                     ret = naive_put(F.n, F.lo, F.hi, F.f, F.h, F.in, F.out);
                     sp--;
                     continue;
@@ -1820,12 +1824,12 @@ struct Walker {
                 if (gk) return finish_put_greeks(T, row);
                 return P.out_scale * exercise(P, E, ex_index(P, T, 0));
             }
-            if (R < 2 * c.a.B) {
+            if (R < 2 * c.a.Bput) {
                 f = naive_put(n, -R, R, f, R - stop, row, row);
                 n = T - stop;
                 break;
             }
-            int64_t h = c.a.B;
+            int64_t h = c.a.Bput;
             while (2 * h <= R / 2) h *= 2;
             f = solve_put(n, -R, R, f, h, row);
             n += h;
@@ -2310,12 +2314,12 @@ cudaError_t run_dnc(int method, int64_t n, const Params *d_params, int64_t T_max
                     int32_t *d_status, int32_t *d_bnd, const int64_t *d_bnd_off,
                     aop_stats *d_stats, int *d_err, int64_t *d_opt_ns, int flags, int cap, int device,
                     cudaStream_t s, const ServeSession *srv, const int32_t *d_order, double *d_greeks,
-                    int lg_tile, int radix2)
+                    int lg_tile, int radix2, int base_case_put)
 {
     if (srv) n = srv->capacity;
     if (n == 0) return cudaSuccess;
     if (lg_tile < 9 || lg_tile > 11) return cudaErrorInvalidValue;
-    Layout L = make_layout(method, T_max, base_case, shape_big(method), lg_tile);
+    Layout L = make_layout(method, T_max, std::max(base_case, base_case_put), shape_big(method), lg_tile);
     if (tw_log2 < L.tw_log2) return cudaErrorInvalidValue;
     int64_t grid = dnc_grid(method, n, L.smem, cap, device);
     const size_t need = (size_t)(grid * L.stride) + 8192;
@@ -2332,6 +2336,7 @@ cudaError_t run_dnc(int method, int64_t n, const Params *d_params, int64_t T_max
     a.params = d_params;
     a.n = n;
     a.B = base_case;
+    a.Bput = base_case_put > 0 ? base_case_put : base_case;
     a.lg_tile = L.lg_tile;
     a.radix2 = radix2 ? 1 : 0;
     a.lg_block = L.lg_block;
@@ -2542,6 +2547,7 @@ cudaError_t run_linear_advance(int method, int nw, const double *w, int64_t coun
     DncArgs a;
     memset(&a, 0, sizeof(a));
     a.B = 16;
+    a.Bput = 16;
     a.lg_tile = L.lg_tile;
     a.lg_block = L.lg_block;
     a.W_max = L.W_max;
@@ -2581,6 +2587,7 @@ cudaError_t run_european(int64_t n, const Params *d_params, int64_t T_max, void 
     a.params = d_params;
     a.n = n;
     a.B = 16;
+    a.Bput = 16;
     a.lg_tile = L.lg_tile;
     a.lg_block = L.lg_block;
     a.W_max = L.W_max;
@@ -2705,6 +2712,7 @@ extern "C" aop_status aop_linear_advance_noalloc(int method, int nw, const doubl
     DncArgs a;
     memset(&a, 0, sizeof(a));
     a.B = 16;
+    a.Bput = 16;
     a.lg_block = (method == AOP_FFT_FP64) ? 11 : 12;
     a.lg_tile = a.lg_block;
     a.W_max = kNoAllocMaxW;

@@ -77,7 +77,8 @@ cudaError_t run_dnc(int method, int64_t n, const Params *d_params, int64_t T_max
                     int32_t *d_status, int32_t *d_bnd, const int64_t *d_bnd_off,
                     aop_stats *d_stats, int *d_err, int64_t *d_opt_ns, int flags, int cap, int device,
                     cudaStream_t s, const ServeSession *srv = nullptr, const int32_t *d_order = nullptr,
-                    double *d_greeks = nullptr, int lg_tile = kDefaultLgTile, int radix2 = 0);
+                    double *d_greeks = nullptr, int lg_tile = kDefaultLgTile, int radix2 = 0,
+                    int base_case_put = 0);
 cudaError_t run_linear_advance(int method, int nw, const double *w, int64_t count, int64_t W,
                                int64_t h, const double *d_in, double *d_out, const void *d_tw,
                                int tw_log2, void *ws, size_t ws_bytes, int *d_err,
