@@ -332,6 +332,14 @@ def serve_stream(ctx, aop, wl, method, args, stencil_method=None):
     T_MAX = 1 << 18
     reqs, arrivals = wl.request_stream(n=args.serve_n, rate=20000.0, seed=2317)
     arr = aop.requests_array(reqs)
+    # the session takes the context's schedule for its size and model mix:
+    # tune it on a sample of requests drawn like the stream's (its own seed),
+    # large enough (about seven a slot) that a batch's time follows throughput
+    # rather than its longest option
+    tuned = None
+    if not args.schedule and not args.no_tune:
+        sample, _ = wl.request_stream(n=2048, rate=20000.0, seed=2319)
+        tuned = ctx.autotune(aop.requests_array(sample), method)
     t0 = time.perf_counter()
     with aop.Server(ctx, capacity=len(reqs), T_max=T_MAX, method=method) as srv:
         slots = srv.info()["slots"]
@@ -346,6 +354,7 @@ def serve_stream(ctx, aop, wl, method, args, stencil_method=None):
            "latency_ms": {"p50": float(np.percentile(lat, 50) * 1e3), "p99": float(np.percentile(lat, 99) * 1e3),
                           "max": float(lat.max() * 1e3), "mean": float(lat.mean() * 1e3)},
            "slots": slots, "T_max": T_MAX,
+           "schedule": tuned or "the book's (nearest size)",
            "stream": "Poisson 20k req/s, 40% binomial call, 40% trinomial call, 20% BSM put, "
                      "T=round(2^U[10,18]), seed 2317"}
     m = args.serve_stencil_prefix

@@ -374,10 +374,10 @@ class Server:
     persistent pricing kernel takes requests as they are published."""
 
     def __init__(self, ctx: "Context", capacity: int, T_max: int, method: int = FFT_FP64,
-                 base_case: int = 0, flags: int = 0, ctas_per_sm: int = 0):
+                 base_case: int = 0, flags: int = 0, ctas_per_sm: int = 0, lg_tile: int = 0, radix: int = 0):
         self.ctx = ctx
         h = ctypes.c_void_p()
-        o = _opts(method, base_case, flags, ctas_per_sm)
+        o = _opts(method, base_case, flags, ctas_per_sm, lg_tile, radix)
         _check(load().aop_server_create(ctx._h, int(capacity), int(T_max), ctypes.byref(o), ctypes.byref(h)),
                "aop_server_create")
         self._h = h
