@@ -638,6 +638,23 @@ aop_status aop_ctx_autotune(aop_ctx *c, int64_t n, const aop_request *reqs, int3
             if (ms < best) { best = ms; pick = o; }
         }
     }
+    // stage 3: when stage 2 moved the tile or the radix, the height and count
+    // again at the new transforms (the kernel's code size and the workers'
+    // speed shift the balance between walker and workers)
+    if (pick.lg_tile != kDefaultLgTile || pick.radix != 4) {
+        const aop_options at = pick;
+        for (int B : kB) {
+            for (int cap : kCap) {
+                if (B == at.base_case && cap == at.ctas_per_sm) continue;
+                if (cap > 1 && cap > dnc_max_per_sm(method, T_max, B, at.lg_tile)) continue;
+                aop_options o{method, B, 0, cap, at.lg_tile, at.radix};
+                float ms = 0.f;
+                aop_status st = time_one(o, &ms);
+                if (st) return st;
+                if (ms < best) { best = ms; pick = o; }
+            }
+        }
+    }
     c->tuned[sched_key(method, T_max, model_class(n, reqs))] = pick;
     if (best_out) *best_out = pick;
     return AOP_OK;
