@@ -351,15 +351,15 @@ aop_status aop_server_destroy(aop_server *srv);
  * schedule and times each second run with CUDA events.  Stage 1 searches the
  * base-case height in {16, 31, 32, 47, 63, 64} x options in flight per SM in
  * {1, 2, 3, 4} (skipping counts the kernel's registers and shared memory
- * cannot hold) with the default transforms; stage 2 searches the worker's
- * transform tile (2^9, 2^10, 2^11 values) x the transform radix (4, 2) at
- * the stage-1 pick; when that moved the tile or the radix, stage 3 searches
- * the height x count again at the new transforms.  The fastest schedule is kept in this context under the
- * key (method, log2 of the largest T of the requests, model class: binomial
+ * cannot hold) x the transform radix (4, 2) at the default 2^10-value tile;
+ * stage 2 tries tiles of 2^9 and 2^11 values at the stage-1 pick; when that
+ * moved the tile, stage 3 searches the height x count again at it.  The
+ * fastest schedule is kept in this context under the key (method, log2 of
+ * the largest T of the requests, model class: binomial
  * only, three-point only, or both) and used by later calls whose aop_options
  * leave a field 0: a call takes the pick of its own key, else of the same size
  * with another model class, else of the nearest size.  best_out (nullable)
- * receives it.  Costs up to 104 batch calls: pass a sample of the workload, or
+ * receives it.  Costs up to 146 batch calls: pass a sample of the workload, or
  * the workload itself when it is priced repeatedly.  AOP_EINVAL for the plain
  * stencil or a bad method. */
 aop_status aop_ctx_autotune(aop_ctx *ctx, int64_t n, const aop_request *reqs, int32_t method,

@@ -614,34 +614,34 @@ aop_status aop_ctx_autotune(aop_ctx *c, int64_t n, const aop_request *reqs, int3
         }
         return AOP_OK;
     };
-    // stage 1: base-case height x options in flight per SM, default transforms
-    for (int B : kB) {
-        for (int cap : kCap) {
-            if (cap > 1 && cap > dnc_max_per_sm(method, T_max, B)) continue;   // same as fewer
-            aop_options o{method, B, 0, cap, kDefaultLgTile, 4};
-            float ms = 0.f;
-            aop_status st = time_one(o, &ms);
-            if (st) return st;
-            if (best < 0.f || ms < best) { best = ms; pick = o; }
+    // stage 1: base-case height x options in flight per SM x radix at the
+    // default tile (height, count and radix trade walker time against worker
+    // time and code size together, so they are searched jointly)
+    for (int radix : kRadix) {
+        for (int B : kB) {
+            for (int cap : kCap) {
+                if (cap > 1 && cap > dnc_max_per_sm(method, T_max, B)) continue;   // same as fewer
+                aop_options o{method, B, 0, cap, kDefaultLgTile, radix};
+                float ms = 0.f;
+                aop_status st = time_one(o, &ms);
+                if (st) return st;
+                if (best < 0.f || ms < best) { best = ms; pick = o; }
+            }
         }
     }
-    // stage 2: transform tile and radix at that height and count
+    // stage 2: the transform tile at that pick
     for (int lg : kLgTile) {
-        for (int radix : kRadix) {
-            if (lg == kDefaultLgTile && radix == 4) continue;   // timed in stage 1
-            if (pick.ctas_per_sm > 1 && pick.ctas_per_sm > dnc_max_per_sm(method, T_max, pick.base_case, lg))
-                continue;                                       // the tile leaves no room for the count
-            aop_options o{method, pick.base_case, 0, pick.ctas_per_sm, lg, radix};
-            float ms = 0.f;
-            aop_status st = time_one(o, &ms);
-            if (st) return st;
-            if (ms < best) { best = ms; pick = o; }
-        }
+        if (lg == kDefaultLgTile) continue;                     // timed in stage 1
+        if (pick.ctas_per_sm > 1 && pick.ctas_per_sm > dnc_max_per_sm(method, T_max, pick.base_case, lg))
+            continue;                                           // the tile leaves no room for the count
+        aop_options o{method, pick.base_case, 0, pick.ctas_per_sm, lg, pick.radix};
+        float ms = 0.f;
+        aop_status st = time_one(o, &ms);
+        if (st) return st;
+        if (ms < best) { best = ms; pick = o; }
     }
-    // stage 3: when stage 2 moved the tile or the radix, the height and count
-    // again at the new transforms (the kernel's code size and the workers'
-    // speed shift the balance between walker and workers)
-    if (pick.lg_tile != kDefaultLgTile || pick.radix != 4) {
+    // stage 3: when stage 2 moved the tile, the height and count again at it
+    if (pick.lg_tile != kDefaultLgTile) {
         const aop_options at = pick;
         for (int B : kB) {
             for (int cap : kCap) {
