@@ -311,7 +311,8 @@ aop_status price_european_batch(aop_ctx *ctx, int64_t n, const aop_request *reqs
  * AOP_ENOMEM, AOP_ECUDA. */
 typedef struct aop_server aop_server;
 
-/* Device workspace (bytes) that a context's cap must allow for
+/* Admission planning (a deployment helper; the paper has no counterpart).
+ * Device workspace (bytes) that a context's cap must allow for
  * options_in_flight options of up to T_max steps priced at once with a D&C
  * method (AOP_FFT_FP64, AOP_FFT_FP32SPLIT, AOP_FFT_DF32) and base-case height
  * base_case (0 = the library default): the per-option scratch of the
@@ -365,8 +366,8 @@ aop_status aop_server_destroy(aop_server *srv);
 aop_status aop_ctx_autotune(aop_ctx *ctx, int64_t n, const aop_request *reqs, int32_t method,
                             aop_options *best_out);
 
-/* The D&C schedule a batch call with these n host requests and *opt would
- * use on this context: the fields of *opt that are nonzero, the rest from the
+/* The D&C schedule (a tuning aid; the paper has no counterpart) that a batch
+ * call with these n host requests and *opt would use on this context: the fields of *opt that are nonzero, the rest from the
  * context's tuned picks (see aop_ctx_autotune) or the library defaults.
  * ctas_per_sm 0 in *out means as many as fit.  Host-only; AOP_EINVAL for a
  * plain stencil method. */
