@@ -210,7 +210,12 @@ aop_status run_batch(aop_ctx *c, int64_t n, const aop_request *d_reqs, const aop
     const bool stencil = (method == AOP_STENCIL_FP64 || method == AOP_STENCIL_DF32);
     if (d_greeks && stencil) return AOP_EINVAL;
     if (c->serving) return AOP_EBUSY;
-    if (n == 0 || T_max < 1) return AOP_OK;
+    if (n == 0) return AOP_OK;
+    if (T_max < 1) {
+        // every option was rejected (its status already says why): NaN prices
+        CK(cudaMemsetAsync(d_prices, 0xff, (size_t)n * sizeof(double), s));
+        return AOP_OK;
+    }
     const Sched sc = resolve_sched(c, opt, T_max, cls);
     const int B = sc.B;
     CK(cudaMemsetAsync(c->d_stats, 0, sizeof(aop_stats), s));
