@@ -54,7 +54,8 @@ WORKLOAD = "precision_sweep_T131072_256binomial_256trinomial"
 # book, summarised under profiles/).
 # It holds for the kernel sources whose SHA-256 is recorded with it; any other
 # source reports null.
-KERNEL_SOURCES = ("paper_2303_02317_gb300/csrc/dnc.cu", "paper_2303_02317_gb300/csrc/fft.cuh",
+KERNEL_SOURCES = ("paper_2303_02317_gb300/csrc/dnc_kernel.cuh", "paper_2303_02317_gb300/csrc/dnc.cu",
+                  "paper_2303_02317_gb300/csrc/dnc_help.cu", "paper_2303_02317_gb300/csrc/fft.cuh",
                   "paper_2303_02317_gb300/csrc/common.cuh")
 TRAFFIC_CAPTURE = {"sources_sha256": "8cd00328dcd3dc800cb560799c674f58bdbe862cd36e3c024d5627b4d068793a",
                    "bytes_per_launch": {"df32": 13511416064 + 17736364288}}
@@ -335,11 +336,12 @@ def serve_stream(ctx, aop, wl, method, args, stencil_method=None):
     # the session takes the context's schedule for its size and model mix:
     # tune it on a sample of requests drawn like the stream's (its own seed),
     # large enough (about seven a slot) that a batch's time follows throughput
-    # rather than its longest option
+    # rather than its longest option, priced without helping as the session's
+    # requests are
     tuned = None
     if not args.schedule and not args.no_tune:
         sample, _ = wl.request_stream(n=2048, rate=20000.0, seed=2319)
-        tuned = ctx.autotune(aop.requests_array(sample), method)
+        tuned = ctx.autotune(aop.requests_array(sample), method, flags=aop.FLAG_NO_HELP)
     t0 = time.perf_counter()
     with aop.Server(ctx, capacity=len(reqs), T_max=T_MAX, method=method) as srv:
         slots = srv.info()["slots"]

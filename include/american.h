@@ -131,6 +131,16 @@ typedef struct aop_request {
  * AOP_ETIMEOUT and a NaN price; the call returns and the context stays usable.
  * Nothing is faulted or hung.  Not for pricing. */
 #define AOP_FLAG_TEST_STALL 16
+/* D&C batches help by default: idle CTAs work for other options (Sec. 2.3:
+ * the linear advances of a trapezoid run in parallel with the recursion
+ * beside them).  Advances too long for one worker tile go on a board in global
+ * memory; the option's own workers take them, and so do CTAs that found no
+ * option left to start (each of their workers one advance), and, in a batch
+ * smaller than the GPU, three extra CTAs per option launched to help (all
+ * their warps on one advance).  Prices and dividers are the same to the bit
+ * either way: the same passes and stages run on another SM.  This bit turns
+ * helping off; serving sessions and the FP32-split method never help. */
+#define AOP_FLAG_NO_HELP 32
 
 typedef struct aop_options {
     int32_t method;     /* aop_method */
@@ -179,6 +189,9 @@ typedef struct aop_stats {
     int64_t advance_phase_cycles[5];     /* single-tile advances, SM cycles summed over the
                                             worker warps: spectrum lookup, input staging,
                                             forward transform + product, inverse, store */
+    int64_t helped_advances;             /* D&C: linear advances run by
+                                            CTAs working for another CTA's option */
+    int64_t helped_ns;                   /* ... and the worker time they took */
 } aop_stats;
 
 typedef struct aop_ctx aop_ctx;
@@ -365,6 +378,12 @@ aop_status aop_server_destroy(aop_server *srv);
  * stencil or a bad method. */
 aop_status aop_ctx_autotune(aop_ctx *ctx, int64_t n, const aop_request *reqs, int32_t method,
                             aop_options *best_out);
+/* aop_ctx_autotune with the candidates' batch calls made with `flags` (AOP_FLAG_*
+ * bits): AOP_FLAG_NO_HELP tunes for a use that does not help, such as a
+ * serving session, whose requests run without helping CTAs.  The pick is
+ * stored under the same key. */
+aop_status aop_ctx_autotune_flags(aop_ctx *ctx, int64_t n, const aop_request *reqs, int32_t method,
+                                  int32_t flags, aop_options *best_out);
 
 /* The D&C schedule (a tuning aid; the paper has no counterpart) that a batch
  * call with these n host requests and *opt would use on this context: the fields of *opt that are nonzero, the rest from the

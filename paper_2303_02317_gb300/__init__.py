@@ -66,7 +66,8 @@ class _Stats(ctypes.Structure):
         ("spectrum_ns", ctypes.c_int64), ("spectrum_bins", ctypes.c_int64),
         ("basecase_loop_cycles", ctypes.c_int64), ("basecase_fill_cycles", ctypes.c_int64),
         ("advance_count_by_log2n", ctypes.c_int64 * 24), ("advance_ns_by_log2n", ctypes.c_int64 * 24),
-        ("advance_phase_cycles", ctypes.c_int64 * 5)]
+        ("advance_phase_cycles", ctypes.c_int64 * 5), ("helped_advances", ctypes.c_int64),
+        ("helped_ns", ctypes.c_int64)]
 
 
 _lock = threading.Lock()
@@ -106,6 +107,7 @@ def load(path: Optional[str] = None):
         lib.aop_ctx_get_stats.argtypes = [vp, ctypes.POINTER(_Stats)]
         lib.aop_ctx_get_option_times.argtypes = [vp, i64, vp]
         lib.aop_ctx_autotune.argtypes = [vp, i64, vp, i32, ctypes.POINTER(_Options)]
+        lib.aop_ctx_autotune_flags.argtypes = [vp, i64, vp, i32, i32, ctypes.POINTER(_Options)]
         lib.price_european_batch.argtypes = [vp, i64, vp, vp, vp]
         lib.aop_server_create.argtypes = [vp, i64, i64, ctypes.POINTER(_Options), ctypes.POINTER(vp)]
         lib.aop_server_submit.argtypes = [vp, vp, ctypes.POINTER(i64)]
@@ -125,7 +127,7 @@ def load(path: Optional[str] = None):
                   "aop_linear_advance_device", "aop_ctx_get_stats", "aop_ctx_autotune",
                   "aop_server_create", "aop_server_submit", "aop_server_poll", "aop_server_serve_stream",
                   "aop_server_info", "aop_server_destroy", "price_european_batch", "aop_workspace_bytes",
-                  "aop_measure_fma_peak", "aop_ctx_schedule"):
+                  "aop_measure_fma_peak", "aop_ctx_schedule", "aop_ctx_autotune_flags"):
             getattr(lib, f).restype = ctypes.c_int
         _lib = lib
         return lib
@@ -158,6 +160,7 @@ FLAG_TILT_OFF = 2
 FLAG_TILT_ON = 4
 FLAG_SPREAD_WALKERS = 8
 FLAG_TEST_STALL = 16
+FLAG_NO_HELP = 32
 
 
 
@@ -186,13 +189,14 @@ def price_american(model: int, S0: float, K: float, r: float, q: float, sigma: f
     return out.value
 
 
-def price_american_ex(req, method: int = FFT_FP64, base_case: int = 0, boundary: bool = False):
+def price_american_ex(req, method: int = FFT_FP64, base_case: int = 0, boundary: bool = False,
+                      flags: int = 0):
     """One option with explicit method; returns price or (price, boundary[T+1])."""
     arr = requests_array([req])
     out = ctypes.c_double()
     T = int(arr["T"][0])
     b = np.empty(T + 1, dtype=np.int32) if boundary else None
-    o = _opts(method, base_case)
+    o = _opts(method, base_case, flags)
     code = load().price_american_ex(arr.ctypes.data, ctypes.byref(o), ctypes.byref(out),
                                     b.ctypes.data if b is not None else None)
     _check(code, "price_american_ex")
@@ -331,14 +335,20 @@ class Context:
                "price_european_batch")
         return prices, status
 
-    def autotune(self, reqs, method: int) -> dict:
+    def autotune(self, reqs, method: int, flags: int = 0) -> dict:
         """Pick this context's D&C schedule (base-case height, options in
         flight per SM, transform tile and radix) for `method` and the size and
-        model class of these requests by timing them (C: aop_ctx_autotune)."""
+        model class of these requests by timing them, the batch calls made
+        with `flags` (FLAG_NO_HELP for a serving session's schedule; C:
+        aop_ctx_autotune / aop_ctx_autotune_flags)."""
         arr = reqs if isinstance(reqs, np.ndarray) else requests_array(reqs)
         best = _Options()
-        _check(load().aop_ctx_autotune(self._h, len(arr), arr.ctypes.data, int(method), ctypes.byref(best)),
-               "aop_ctx_autotune")
+        if flags:
+            _check(load().aop_ctx_autotune_flags(self._h, len(arr), arr.ctypes.data, int(method), int(flags),
+                                                 ctypes.byref(best)), "aop_ctx_autotune_flags")
+        else:
+            _check(load().aop_ctx_autotune(self._h, len(arr), arr.ctypes.data, int(method), ctypes.byref(best)),
+                   "aop_ctx_autotune")
         return {"base_case": int(best.base_case), "ctas_per_sm": int(best.ctas_per_sm),
                 "lg_tile": int(best.lg_tile), "radix": int(best.radix)}
 

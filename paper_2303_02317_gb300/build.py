@@ -17,7 +17,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libamerican.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
-SOURCES = ["setup.cu", "stencil.cu", "dnc.cu", "api.cu", "peaks.cu"]
+SOURCES = ["dnc.cu", "dnc_help.cu", "setup.cu", "stencil.cu", "api.cu", "peaks.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

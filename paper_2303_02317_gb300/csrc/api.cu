@@ -237,7 +237,7 @@ aop_status run_batch(aop_ctx *c, int64_t n, const aop_request *d_reqs, const aop
         int grid = 0;
         const int cap = sc.cap;
         size_t need = dnc_workspace_bytes(method, n, T_max, std::max(B, sc.Bput), cap, &grid, c->device,
-                                          sc.lg_tile);
+                                          sc.lg_tile, !(opt && (opt->flags & AOP_FLAG_NO_HELP)));
         size_t have_cap = c->cap ? c->cap : need;
         if (need > have_cap) need = have_cap;   // fewer resident CTAs
         st = ensure(&c->ws, &c->ws_size, need, c->cap);
@@ -598,6 +598,11 @@ aop_status aop_ctx_get_option_times(aop_ctx *c, int64_t n, int64_t *ns_out) {
 
 aop_status aop_ctx_autotune(aop_ctx *c, int64_t n, const aop_request *reqs, int32_t method,
                             aop_options *best_out) {
+    return aop_ctx_autotune_flags(c, n, reqs, method, 0, best_out);
+}
+
+aop_status aop_ctx_autotune_flags(aop_ctx *c, int64_t n, const aop_request *reqs, int32_t method, int32_t flags,
+                                  aop_options *best_out) {
     if (!c || n <= 0 || !reqs || method < 0 || method > 3 || method == AOP_STENCIL_FP64) return AOP_EINVAL;   // D&C only
     // heights 2^k - 1 fit a binomial strip (B + 1 cells) or a trinomial one
     // (2B + 2 cells) into whole registers of 32 cells
@@ -626,7 +631,7 @@ aop_status aop_ctx_autotune(aop_ctx *c, int64_t n, const aop_request *reqs, int3
         for (int B : kB) {
             for (int cap : kCap) {
                 if (cap > 1 && cap > dnc_max_per_sm(method, T_max, B)) continue;   // same as fewer
-                aop_options o{method, B, 0, cap, kDefaultLgTile, radix};
+                aop_options o{method, B, flags, cap, kDefaultLgTile, radix};
                 float ms = 0.f;
                 aop_status st = time_one(o, &ms);
                 if (st) return st;
@@ -639,7 +644,7 @@ aop_status aop_ctx_autotune(aop_ctx *c, int64_t n, const aop_request *reqs, int3
         if (lg == kDefaultLgTile) continue;                     // timed in stage 1
         if (pick.ctas_per_sm > 1 && pick.ctas_per_sm > dnc_max_per_sm(method, T_max, pick.base_case, lg))
             continue;                                           // the tile leaves no room for the count
-        aop_options o{method, pick.base_case, 0, pick.ctas_per_sm, lg, pick.radix};
+        aop_options o{method, pick.base_case, flags, pick.ctas_per_sm, lg, pick.radix};
         float ms = 0.f;
         aop_status st = time_one(o, &ms);
         if (st) return st;
@@ -652,7 +657,7 @@ aop_status aop_ctx_autotune(aop_ctx *c, int64_t n, const aop_request *reqs, int3
             for (int cap : kCap) {
                 if (B == at.base_case && cap == at.ctas_per_sm) continue;
                 if (cap > 1 && cap > dnc_max_per_sm(method, T_max, B, at.lg_tile)) continue;
-                aop_options o{method, B, 0, cap, at.lg_tile, at.radix};
+                aop_options o{method, B, flags, cap, at.lg_tile, at.radix};
                 float ms = 0.f;
                 aop_status st = time_one(o, &ms);
                 if (st) return st;
@@ -660,6 +665,7 @@ aop_status aop_ctx_autotune(aop_ctx *c, int64_t n, const aop_request *reqs, int3
             }
         }
     }
+    pick.flags = 0;
     c->tuned[sched_key(method, T_max, model_class(n, reqs))] = pick;
     if (best_out) *best_out = pick;
     return AOP_OK;

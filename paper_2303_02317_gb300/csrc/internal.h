@@ -51,12 +51,13 @@ cudaError_t run_stencil(int64_t n, const Params *d_params, int64_t T_max, void *
 // dnc.cu -- trapezoidal divide-and-conquer pricer
 // log2 of a worker's transform tile unless a schedule says otherwise
 constexpr int kDefaultLgTile = 10;
+constexpr int kHelpers = 3;     // helping: extra CTAs per option of a batch smaller than the GPU
 int dnc_max_per_sm(int method, int64_t T_max, int base_case, int lg_tile = kDefaultLgTile);
 // per-option workspace of the pricing kernel (one slot), without the
 // launch's 8 KiB of queue words
 size_t dnc_slot_bytes(int method, int64_t T_max, int base_case);
 size_t dnc_workspace_bytes(int method, int64_t n, int64_t T_max, int base_case, int cap, int *grid_out,
-                           int device, int lg_tile = kDefaultLgTile);
+                           int device, int lg_tile = kDefaultLgTile, bool help = false);
 // A serving session's host-shared state (see aop_server_* in the header):
 // requests and results live in mapped host memory, the claim counter on the
 // device.  run_dnc with a session prices the published requests in order of
