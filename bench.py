@@ -57,8 +57,8 @@ WORKLOAD = "precision_sweep_T131072_256binomial_256trinomial"
 KERNEL_SOURCES = ("paper_2303_02317_gb300/csrc/dnc_kernel.cuh", "paper_2303_02317_gb300/csrc/dnc.cu",
                   "paper_2303_02317_gb300/csrc/dnc_help.cu", "paper_2303_02317_gb300/csrc/fft.cuh",
                   "paper_2303_02317_gb300/csrc/common.cuh")
-TRAFFIC_CAPTURE = {"sources_sha256": "8cd00328dcd3dc800cb560799c674f58bdbe862cd36e3c024d5627b4d068793a",
-                   "bytes_per_launch": {"df32": 13511416064 + 17736364288}}
+TRAFFIC_CAPTURE = {"sources_sha256": "d9d60662fef916195be0862bc7ef15a232b7a14a5e8c45b01a8e4a5ed1fba8fa",
+                   "bytes_per_launch": {"df32": 13512423680 + 17762582272}}
 
 
 def kernel_sources_sha256() -> str:

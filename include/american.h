@@ -131,15 +131,17 @@ typedef struct aop_request {
  * AOP_ETIMEOUT and a NaN price; the call returns and the context stays usable.
  * Nothing is faulted or hung.  Not for pricing. */
 #define AOP_FLAG_TEST_STALL 16
-/* D&C batches help by default: idle CTAs work for other options (Sec. 2.3:
- * the linear advances of a trapezoid run in parallel with the recursion
- * beside them).  Advances too long for one worker tile go on a board in global
- * memory; the option's own workers take them, and so do CTAs that found no
- * option left to start (each of their workers one advance), and, in a batch
- * smaller than the GPU, three extra CTAs per option launched to help (all
- * their warps on one advance).  Prices and dividers are the same to the bit
- * either way: the same passes and stages run on another SM.  This bit turns
- * helping off; serving sessions and the FP32-split method never help. */
+/* Small D&C batches help by default: spare SMs work for the options in
+ * flight (Sec. 2.3: the linear advances of a trapezoid run in parallel with
+ * the recursion beside them).  A batch of n options, when the GPU has at least
+ * 2n SMs, gets min(3, (SMs - n) / n) helping CTAs per option, every CTA on an
+ * SM of its own.  Advances too long for one worker tile go on a board in
+ * global memory, where the option's own workers and the helping CTAs (all
+ * warps on one advance) take them; CTAs whose options are done help too.
+ * Prices and dividers are the same to the bit either way: the same passes and
+ * stages run on another SM.  Larger batches, serving sessions and the
+ * FP32-split method never help (a helper that shares an SM with an option's
+ * recursion slows it more than it saves); this bit turns helping off. */
 #define AOP_FLAG_NO_HELP 32
 
 typedef struct aop_options {

@@ -237,7 +237,7 @@ aop_status run_batch(aop_ctx *c, int64_t n, const aop_request *d_reqs, const aop
         int grid = 0;
         const int cap = sc.cap;
         size_t need = dnc_workspace_bytes(method, n, T_max, std::max(B, sc.Bput), cap, &grid, c->device,
-                                          sc.lg_tile, !(opt && (opt->flags & AOP_FLAG_NO_HELP)));
+                                          sc.lg_tile, !(opt && (opt->flags & AOP_FLAG_NO_HELP)) && method != AOP_FFT_FP32SPLIT);
         size_t have_cap = c->cap ? c->cap : need;
         if (need > have_cap) need = have_cap;   // fewer resident CTAs
         st = ensure(&c->ws, &c->ws_size, need, c->cap);

@@ -136,11 +136,21 @@ int dnc_max_per_sm(int method, int64_t T_max, int base_case, int lg_tile) {
     return ctas_per_sm(method, L.smem);
 }
 
-// One CTA per option in flight, at most n; with helping, a batch smaller
-// than the GPU also gets kHelpers CTAs per option, which work for the
-// options' boards from the start.
+// Helping CTAs per option of a batch of n: as many (up to kHelpers) as the
+// SMs the options leave idle hold, one CTA an SM.  A helper sharing an SM
+// with an option's walker slows that walker more than it saves (measured:
+// 152 options of the book at T = 2^17, one owner and one helper an SM, 96-103
+// against 91 ms), so batches of more than half as many options as SMs get none.
+int dnc_helpers(int64_t n, int device) {
+    const int64_t sms = sm_count(device);
+    if (n < 1 || n >= sms) return 0;
+    return (int)std::min<int64_t>(kHelpers, (sms - n) / n);
+}
+
+// One CTA per option in flight, at most n; with helping, dnc_helpers(n) more
+// CTAs per option, which work for the options' boards from the start.
 int64_t dnc_grid(int method, int64_t n, size_t smem, int cap, int device, bool help) {
-    const int64_t m = help ? n * (1 + kHelpers) : n;
+    const int64_t m = help ? n * (1 + dnc_helpers(n, device)) : n;
     return std::min<int64_t>(m, (int64_t)sm_count(device) * dnc_per_sm(method, m, smem, cap, device));
 }
 
@@ -171,7 +181,8 @@ cudaError_t run_dnc(int method, int64_t n, const Params *d_params, int64_t T_max
     if (lg_tile < 9 || lg_tile > 11) return cudaErrorInvalidValue;
     Layout L = make_layout(method, T_max, std::max(base_case, base_case_put), shape_big(method), lg_tile);
     if (tw_log2 < L.tw_log2) return cudaErrorInvalidValue;
-    const bool help = !srv && !(flags & AOP_FLAG_NO_HELP) && method != AOP_FFT_FP32SPLIT;
+    const bool help = !srv && !(flags & AOP_FLAG_NO_HELP) && method != AOP_FFT_FP32SPLIT &&
+                      dnc_helpers(n, device) > 0;
     int64_t grid = dnc_grid(method, n, L.smem, cap, device, help);
     const size_t need = (size_t)(grid * L.stride) + 8192;
     if (ws_bytes < need) {

@@ -51,7 +51,7 @@ cudaError_t run_stencil(int64_t n, const Params *d_params, int64_t T_max, void *
 // dnc.cu -- trapezoidal divide-and-conquer pricer
 // log2 of a worker's transform tile unless a schedule says otherwise
 constexpr int kDefaultLgTile = 10;
-constexpr int kHelpers = 3;     // helping: extra CTAs per option of a batch smaller than the GPU
+constexpr int kHelpers = 3;     // helping: at most this many extra CTAs per option of a small batch
 int dnc_max_per_sm(int method, int64_t T_max, int base_case, int lg_tile = kDefaultLgTile);
 // per-option workspace of the pricing kernel (one slot), without the
 // launch's 8 KiB of queue words

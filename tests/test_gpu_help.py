@@ -71,25 +71,40 @@ def test_single_dividers_bit_equal(ctx):
     assert abs(p[0] - ref) <= parity.price_tol(aop.FFT_DF32, ref, r.K)
 
 
+def _sms():
+    import torch
+    return torch.cuda.get_device_properties(0).multi_processor_count
+
+
 @pytest.mark.parametrize("method", [aop.FFT_DF32, aop.FFT_FP64], ids=["df32", "fft64"])
-def test_batch_with_a_tail_bit_equal(ctx, method):
-    """More options than resident CTAs, of mixed sizes and models: CTAs that
-    find the queue empty help the options still in flight.  Every price is
-    bit-equal to the launch without helping."""
+def test_small_batch_bit_equal(ctx, method):
+    """A batch of a quarter as many options as SMs, of mixed sizes and models:
+    three helping CTAs per option, and CTAs whose options finish early help
+    the rest.  Every price is bit-equal to the launch without helping, and a
+    second launch on the same workspace (whose boards, left by the last
+    launch, must be skipped) gives the same prices again."""
     rng = np.random.default_rng(2303)
-    reqs = wl.random_small(420, seed=7, T_range=(1500, 12000), models=(0, 1, 2))
+    reqs = wl.random_small(_sms() // 4, seed=7, T_range=(1500, 12000), models=(0, 1, 2))
     p0, s0 = ctx.price_batch(reqs, method=method, flags=OFF)
     p1, s1 = ctx.price_batch(reqs, method=method)
     st = ctx.stats()
     assert (s0 == 0).all() and (s1 == 0).all()
     assert np.array_equal(p0, p1), np.nonzero(p0 != p1)[0][:8]
     assert st["helped_advances"] > 0
-    # a second helped launch on the same workspace (boards of the last launch
-    # are stale and must be skipped) gives the same prices again
     order = rng.permutation(len(reqs))
     p2, s2 = ctx.price_batch([reqs[i] for i in order], method=method)
     assert (s2 == 0).all()
     assert np.array_equal(p2, p0[order])
+
+
+def test_large_batch_does_not_help(ctx):
+    """More options than SMs: no helping CTA (they would share SMs with the
+    options' recursions), the same prices."""
+    reqs = wl.random_small(_sms() + 10, seed=8, T_range=(1500, 6000), models=(0, 1, 2))
+    p0, s0 = ctx.price_batch(reqs, method=aop.FFT_DF32, flags=OFF)
+    p1, s1 = ctx.price_batch(reqs, method=aop.FFT_DF32)
+    assert (s0 == 0).all() and (s1 == 0).all() and np.array_equal(p0, p1)
+    assert ctx.stats()["helped_advances"] == 0
 
 
 def test_stall_with_helping_times_out_and_recovers(ctx):
