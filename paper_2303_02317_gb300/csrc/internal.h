@@ -48,7 +48,7 @@ cudaError_t run_stencil(int64_t n, const Params *d_params, int64_t T_max, void *
                         double *d_prices, int32_t *d_status, int32_t *d_bnd,
                         const int64_t *d_bnd_off, aop_stats *d_stats, cudaStream_t s, bool df);
 
-// dnc.cu -- trapezoidal divide-and-conquer pricer
+// dnc.cu / dnc_help.cu -- trapezoidal divide-and-conquer pricer
 // log2 of a worker's transform tile unless a schedule says otherwise
 constexpr int kDefaultLgTile = 10;
 constexpr int kHelpers = 3;     // helping: at most this many extra CTAs per option of a small batch
