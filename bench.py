@@ -406,6 +406,8 @@ def run_profile_case(args):
       european -- 64 European counterparts of that mix at T = 2^15;
       dnc_small -- the doubled-FP32 D&C on the reduced book (152 binomial +
           152 trinomial calls at T = 2^15, two per SM, base case 63);
+      dnc_single_put -- one BSM put at T = 2^16 in doubled FP32 with its three
+          helping CTAs (the helping kernel);
       dnc_part -- the doubled-FP32 D&C on 76 options of the book itself
           (the first 38 binomial and 38 trinomial calls at T = 2^17, base case
           63): its DRAM traffic per option stands for the book's, whose
@@ -429,6 +431,9 @@ def run_profile_case(args):
             book = wl.precision_sweep(T=T_BENCH, n_binomial=N_BINOMIAL, n_trinomial=N_TRINOMIAL)
             reqs = book[:38] + book[N_BINOMIAL:N_BINOMIAL + 38]
             p, st = ctx.price_batch(reqs, method=aop.FFT_DF32, base_case=63, ctas_per_sm=2)
+        elif case == "dnc_single_put":
+            reqs = [wl.fixed_bsm_put(1 << 16)]
+            p, st = ctx.price_batch(reqs, method=aop.FFT_DF32)
         elif case == "dnc_small":
             reqs = wl.precision_sweep(T=1 << 15, n_binomial=152, n_trinomial=152)
             p, st = ctx.price_batch(reqs, method=aop.FFT_DF32, base_case=63, ctas_per_sm=2)
@@ -570,7 +575,7 @@ def main():
                     help="single-option latency tables of the fixed configurations (C1-C3) instead of the book")
     ap.add_argument("--config-runs", type=int, default=10)
     ap.add_argument("--profile-case", default=None,
-                    choices=["stencil_df32", "stencil_fp64", "european", "dnc_small", "dnc_part"],
+                    choices=["stencil_df32", "stencil_fp64", "european", "dnc_small", "dnc_part", "dnc_single_put"],
                     help="one small invocation of one kernel (for profiler captures) instead of the bench")
     args = ap.parse_args()
     if args.impl == "reference":

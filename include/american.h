@@ -148,7 +148,9 @@ typedef struct aop_options {
     int32_t method;     /* aop_method */
     int32_t base_case;  /* D&C base-case height in rows (2 .. 64, clamped) for every option of the call;
                            0 = the context's tuned pick, else 63 for the lattices and 31 for the
-                           BSM put (whose base-case windows are four heights wide) */
+                           BSM put (whose base-case windows are four heights wide); 31 for a
+                           batch of three-point lattices only that is small enough to help
+                           (AOP_FLAG_NO_HELP) */
     int32_t flags;      /* AOP_FLAG_* bits, 0 for none */
     int32_t ctas_per_sm; /* D&C: options in flight per SM; 0 = as many as fit */
     int32_t lg_tile;    /* D&C: log2 of a worker's shared-memory transform tile, 9 .. 11; 0 = tuned default */

@@ -74,6 +74,12 @@ struct Sched {
     int Bput;          // base-case height of BSM puts (their windows are four heights wide)
 };
 constexpr int kDefaultPutBaseCase = 31;   // a put strip of 4B + 1 cells fills four registers
+// Untuned height of a batch of three-point lattices only, when the batch is
+// small enough to be helped: the spare SMs absorb the extra advances of the
+// lower height, and the shorter rows shorten each option's chain (measured,
+// one trinomial call at T = 2^17: 54.8 ms against 63.3 at height 63; one
+// binomial call stays fastest at 63).
+constexpr int kHelpedTriBaseCase = 31;
 
 aop_status cuda_fail(cudaError_t e) {
     return e == cudaSuccess ? AOP_OK : (e == cudaErrorMemoryAllocation ? AOP_ENOMEM : AOP_ECUDA);
@@ -164,11 +170,14 @@ aop_options lookup_tuned(const aop_ctx *c, int method, int64_t T_max, int cls) {
 
 // The D&C schedule of a call: explicit options first, then the context's
 // tuned pick for this size and model class, then the library defaults.
-Sched resolve_sched(const aop_ctx *c, const aop_options *opt, int64_t T_max, int cls) {
+Sched resolve_sched(const aop_ctx *c, const aop_options *opt, int64_t T_max, int cls, int64_t n = 0) {
     const int m = opt ? opt->method : 0;
     const aop_options t = lookup_tuned(c, m, T_max, cls);
+    const bool helped = c && n > 0 && m != AOP_FFT_FP32SPLIT && !(opt && (opt->flags & AOP_FLAG_NO_HELP)) &&
+                        dnc_helpers(n, c->device) > 0;
+    const int B0 = (cls == 1 && helped) ? kHelpedTriBaseCase : kDefaultBaseCase;
     Sched r;
-    r.B = (opt && opt->base_case > 0) ? opt->base_case : (t.base_case > 0 ? t.base_case : kDefaultBaseCase);
+    r.B = (opt && opt->base_case > 0) ? opt->base_case : (t.base_case > 0 ? t.base_case : B0);
     r.B = std::min(64, std::max(2, r.B));
     // puts: an explicit or tuned height applies to them too; untuned, their own default
     r.Bput = (opt && opt->base_case > 0) ? r.B : (t.base_case > 0 ? r.B : kDefaultPutBaseCase);
@@ -216,7 +225,7 @@ aop_status run_batch(aop_ctx *c, int64_t n, const aop_request *d_reqs, const aop
         CK(cudaMemsetAsync(d_prices, 0xff, (size_t)n * sizeof(double), s));
         return AOP_OK;
     }
-    const Sched sc = resolve_sched(c, opt, T_max, cls);
+    const Sched sc = resolve_sched(c, opt, T_max, cls, n);
     const int B = sc.B;
     CK(cudaMemsetAsync(c->d_stats, 0, sizeof(aop_stats), s));
     CK(cudaMemsetAsync(c->d_err, 0, sizeof(int), s));
@@ -678,7 +687,7 @@ aop_status aop_ctx_schedule(const aop_ctx *c, int64_t n, const aop_request *reqs
     if (method < 0 || method > 3 || method == AOP_STENCIL_FP64) return AOP_EINVAL;   // D&C only
     int64_t T_max = 1;
     for (int64_t i = 0; i < n; i++) T_max = std::max<int64_t>(T_max, reqs[i].T);
-    const Sched sc = resolve_sched(c, opt, T_max, model_class(n, reqs));
+    const Sched sc = resolve_sched(c, opt, T_max, model_class(n, reqs), n);
     *out = aop_options{method, sc.B, opt->flags, sc.cap, sc.lg_tile, sc.radix2 ? 2 : 4};
     return AOP_OK;
 }

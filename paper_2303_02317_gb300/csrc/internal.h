@@ -53,6 +53,8 @@ cudaError_t run_stencil(int64_t n, const Params *d_params, int64_t T_max, void *
 constexpr int kDefaultLgTile = 10;
 constexpr int kHelpers = 3;     // helping: at most this many extra CTAs per option of a small batch
 int dnc_max_per_sm(int method, int64_t T_max, int base_case, int lg_tile = kDefaultLgTile);
+// Helping CTAs per option that a batch of n options gets on this device (0: none)
+int dnc_helpers(int64_t n, int device);
 // per-option workspace of the pricing kernel (one slot), without the
 // launch's 8 KiB of queue words
 size_t dnc_slot_bytes(int method, int64_t T_max, int base_case);

@@ -48,8 +48,9 @@ def test_single_options_bit_equal(ctx, method):
     FP32-split mode, which does not help)."""
     helped = 0
     for r in SINGLES:
-        p0, s0 = ctx.price_batch([r], method=method, flags=OFF)
-        p1, s1 = ctx.price_batch([r], method=method)
+        # the same height both ways (untuned, a helped trinomial takes 31)
+        p0, s0 = ctx.price_batch([r], method=method, base_case=63, flags=OFF)
+        p1, s1 = ctx.price_batch([r], method=method, base_case=63)
         helped += ctx.stats()["helped_advances"]
         assert s0[0] == 0 and s1[0] == 0, (r, s0, s1)
         assert p1[0] == p0[0], (r, p0[0], p1[0])
@@ -61,8 +62,8 @@ def test_single_dividers_bit_equal(ctx):
     the parity tolerance of the oracle."""
     for r in SINGLES[:4]:
         d = r.as_dict()
-        p0, b0 = aop.price_american_ex(d, method=aop.FFT_DF32, boundary=True, flags=OFF)
-        p1, b1 = aop.price_american_ex(d, method=aop.FFT_DF32, boundary=True)
+        p0, b0 = aop.price_american_ex(d, method=aop.FFT_DF32, base_case=63, boundary=True, flags=OFF)
+        p1, b1 = aop.price_american_ex(d, method=aop.FFT_DF32, base_case=63, boundary=True)
         assert p1 == p0
         assert np.array_equal(b0, b1)
     r = SINGLES[1]
@@ -117,3 +118,21 @@ def test_stall_with_helping_times_out_and_recovers(ctx):
     p0, s0 = ctx.price_batch(reqs, method=aop.FFT_DF32, flags=OFF)
     p1, s1 = ctx.price_batch(reqs, method=aop.FFT_DF32)
     assert (s0 == 0).all() and (s1 == 0).all() and np.array_equal(p0, p1)
+
+
+def test_small_three_point_batches_default_to_height_31():
+    """Untuned, a batch of three-point lattices only that is small enough to
+    help takes base case 31 (the spare SMs absorb the extra advances); a
+    binomial batch, a large batch and the FP32-split method keep 63."""
+    c = aop.Context(0)
+    try:
+        tri = [wl.fixed_call(1, 1 << 13)]
+        assert c.schedule(tri, aop.FFT_DF32)["base_case"] == 31
+        assert c.schedule(tri, aop.FFT_FP32SPLIT)["base_case"] == 63
+        assert c.schedule([wl.fixed_call(0, 1 << 13)], aop.FFT_DF32)["base_case"] == 63
+        assert c.schedule(tri * _sms(), aop.FFT_DF32)["base_case"] == 63
+        p, s = c.price_batch(tri, method=aop.FFT_DF32)
+        ref = oracle.price_american(tri[0].as_dict(), nthreads=0)
+        assert s[0] == 0 and abs(p[0] - ref) <= parity.price_tol(aop.FFT_DF32, ref, tri[0].K)
+    finally:
+        c.close()
