@@ -65,3 +65,15 @@ def test_workspace_bytes_is_host_arithmetic(lib):
         aop.workspace_bytes(aop.STENCIL_FP64, 1 << 13, 1)
     with pytest.raises(aop.AopError):
         aop.workspace_bytes(aop.FFT_FP64, 0, 1)
+
+
+def test_autotune_entry_points_check_arguments_on_the_host(lib):
+    """Both tuner entry points refuse a null context, an empty sample and the
+    plain stencil (which has no D&C schedule) before touching a device."""
+    arr = aop.requests_array([dict(model=0, S0=100.0, K=100.0, r=0.05, q=0.03, sigma=0.2, expiry=1.0, T=64)])
+    best = aop._Options()
+    for args in ((None, 1, arr.ctypes.data, aop.FFT_DF32),
+                 (None, 0, arr.ctypes.data, aop.FFT_DF32),
+                 (None, 1, arr.ctypes.data, aop.STENCIL_FP64)):
+        assert lib.aop_ctx_autotune(*args, ctypes.byref(best)) == 1                          # AOP_EINVAL
+        assert lib.aop_ctx_autotune_flags(*args, aop.FLAG_NO_HELP, ctypes.byref(best)) == 1
